@@ -1,0 +1,259 @@
+/*
+ * lcmg.h -- C ABI of liblcmg.so: multigrid-preconditioned CG for the
+ * regularized least-squares problems of Bolten, MacLachlan and Kilmer,
+ * "Multigrid preconditioning for regularized least-squares problems".
+ *
+ * The library solves, for a list of regularization parameters lambda_i and
+ * right-hand sides b, the regularized normal equations
+ *
+ *     (A^T A + lambda^2 L^T D^2 L) x = A^T b                 (Sec. 3.2, eq. (normal))
+ *
+ * where A is the forward operator (a CSR matrix, e.g. a CT ray-length
+ * matrix, or a blur PSF applied with zero boundary), L the discrete gradient
+ * of an n_v x n_h image (Sec. 2, eq. (gradient)) and D = diag(d) the edge
+ * weights of the outer iteration (Sec. 2, eq. (g)).  Each system is solved
+ * by preconditioned CG; the preconditioner is one symmetric multigrid
+ * V-cycle (Algorithm 1) on lambda^2 L^T D^2 L + diag(A^T A) with Galerkin
+ * coarse operators (Sec. 3.1).  The outer loop of Algorithm 2 (L-curve
+ * corner, weight update, lambda trimming, stopping rule) is exposed both
+ * as separate calls and end to end.
+ *
+ * Conventions
+ *  - Images are n_v x n_h, vectorised column-major: pixel (i, j) -> i + j*n_v.
+ *  - Edge vectors (d, D L x) hold the n_h*(n_v-1) vertical differences
+ *    first, then the (n_h-1)*n_v horizontal ones, each column-major (the
+ *    row order of L in eq. (gradient)).
+ *  - Lambda lists are strictly increasing (Sec. 3.4 indexes them that way);
+ *    index arguments are 1-based like the paper's i.
+ *  - Every call returns an lcmg_status; nothing throws across the ABI.
+ *    lcmg_last_error() returns a message for the calling thread's most
+ *    recent failure.
+ *  - Ownership: the caller owns every buffer it passes.  Host-pointer calls
+ *    copy inputs into device memory the context owns (freed by
+ *    lcmg_destroy) and copy results back before returning.  *_dev calls
+ *    take device pointers valid on the context's device, read and write them
+ *    in stream order on the context's stream, never free them, and return
+ *    without synchronising unless stated.
+ *  - Device pointers and streams are passed as void* (a cudaStream_t).
+ *  - A context is not thread safe; use one per host thread.
+ */
+#ifndef LCMG_H
+#define LCMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------- */
+typedef enum {
+  LCMG_OK = 0,
+  LCMG_ERR_INVALID_ARG = 1,  /* bad size, pointer, order, or inconsistent state  */
+  LCMG_ERR_NOMEM = 2,        /* device allocation failed or over the HBM budget  */
+  LCMG_ERR_CUDA = 3,         /* a CUDA runtime call failed                        */
+  LCMG_ERR_NOT_READY = 4,    /* server: result not available yet                 */
+  LCMG_ERR_CANCELLED = 5,    /* server: request cancelled or timed out            */
+  LCMG_ERR_STATE = 6         /* call made before the state it needs was set       */
+} lcmg_status;
+
+/* per-system outcome written to status[] by the solve calls */
+typedef enum {
+  LCMG_CONVERGED = 0,        /* ||A^T b - K x||_2 <= tol ||A^T b||_2 (true residual) */
+  LCMG_MAXIT = 1,            /* iteration limit reached                              */
+  LCMG_BREAKDOWN = 2,        /* p^T K p <= 0 or r^T z <= 0                           */
+  LCMG_NONFINITE = 3         /* NaN or Inf met                                       */
+} lcmg_solve_status;
+
+typedef enum { LCMG_SMOOTH_L1_JACOBI = 0, LCMG_SMOOTH_JACOBI = 1 } lcmg_smoother;
+typedef enum {
+  LCMG_PREC_FP64 = 0,        /* all vectors, operators and reductions in FP64       */
+  LCMG_PREC_MIXED = 1        /* FP32 SpMV/stencils/V-cycle, FP64 dots, alpha/beta,
+                                true residuals (reliable updates) and coarse solve  */
+} lcmg_precision;
+typedef enum {
+  LCMG_MODE_BATCHED = 0,     /* all (lambda, rhs) columns advanced together          */
+  LCMG_MODE_SEQUENTIAL = 1   /* one lambda at a time, largest first, each warm-started
+                                from the previous lambda's solution (Sec. 3.3)        */
+} lcmg_mode;
+
+/* ---- parameters ------------------------------------------------------ */
+typedef struct {
+  int32_t levels;       /* multigrid levels incl. the finest; 0 = coarsen by 2 while
+                           both sides are even and one exceeds coarse_max            */
+  int32_t coarse_max;   /* side limit of the coarsest grid for levels = 0 (default 16) */
+  int32_t nu;           /* pre- = post-smoothing sweeps (default 2; equal counts keep
+                           the V-cycle symmetric so CG applies)                      */
+  int32_t smoother;     /* lcmg_smoother (default l1-Jacobi)                         */
+  double omega;         /* damping of LCMG_SMOOTH_JACOBI (default 2/3)               */
+  double q;             /* exponent of eq. (g) (default 2)                           */
+  double d_min;         /* lower clamp of d in eq. (g) (default 1e-3)                */
+  double tol;           /* relative normal-equations residual (default 1e-6)         */
+  int32_t maxit;        /* PCG iteration limit per system (default 10000)            */
+  int32_t precision;    /* lcmg_precision (default FP64)                             */
+  int32_t mode;         /* lcmg_mode (default batched)                               */
+  int32_t check_every;  /* device iterations between host convergence polls (16)     */
+  int32_t graphs;       /* 1 = replay each block of check_every iterations as one CUDA
+                           graph (default), 0 = launch kernels one by one            */
+} lcmg_params;
+
+typedef struct lcmg_ctx lcmg_ctx;
+
+/* Fill *p with the defaults listed above. */
+void lcmg_default_params(lcmg_params* p);
+
+/* Message of the calling thread's last failure ("" if none).  The string is
+ * owned by the library and valid until the thread's next lcmg call. */
+const char* lcmg_last_error(void);
+
+/* Library version string. */
+const char* lcmg_version(void);
+
+/* Create a context on CUDA device `device` that launches on `stream` (a
+ * cudaStream_t).  With stream = NULL the context creates a blocking stream
+ * of its own (ordered with the legacy default stream, and capturable into
+ * CUDA graphs, which the legacy stream is not).  p may be NULL (defaults).
+ * Errors: INVALID_ARG (bad device or parameters), CUDA. */
+int lcmg_create(lcmg_ctx** ctx, int device, void* stream, const lcmg_params* p);
+
+/* Free every device buffer the context owns.  Accepts NULL. */
+int lcmg_destroy(lcmg_ctx* ctx);
+
+/* Replace the parameters (takes effect at the next set_weights / solve). */
+int lcmg_set_params(lcmg_ctx* ctx, const lcmg_params* p);
+
+/* Define the image grid n_v x n_h and hence L (Sec. 2, eq. (gradient));
+ * number of edges = n_h (n_v - 1) + (n_h - 1) n_v.  Resets weights to
+ * D = I.  Errors: INVALID_ARG if n_v < 2 or n_h < 2. */
+int lcmg_set_grid(lcmg_ctx* ctx, int32_t n_v, int32_t n_h);
+
+/* Forward operator A as an m x n CSR matrix (n = n_v n_h) from host arrays:
+ * row_ptr[m+1] (int64, row_ptr[0] = 0, non-decreasing), col[nnz] (int32,
+ * 0 <= col < n), val[nnz] of dtype 0 = FP32 or 1 = FP64.  The library
+ * copies them, builds A^T as a second CSR (no atomics at apply time) and
+ * diag(A^T A) as column sums of squares (Sec. 3.2).  Requires set_grid.
+ * Errors: INVALID_ARG (sizes, monotonicity, column range), STATE, NOMEM. */
+int lcmg_set_forward_csr(lcmg_ctx* ctx, int64_t m, int64_t n, const int64_t* row_ptr,
+                         const int32_t* col, const void* val, int32_t val_dtype);
+
+/* Forward operator A as a kh x kw point-spread function (row-major, kh and
+ * kw odd) applied as a zero-boundary correlation:
+ *   (A x)(i, j) = sum_{u,v} psf[(u + kh/2) * kw + (v + kw/2)] x(i + u, j + v)
+ * over pixels inside the image (rows of A truncated at the boundary, not
+ * renormalised).  A^T uses the flipped PSF.  Requires set_grid. */
+int lcmg_set_forward_stencil(lcmg_ctx* ctx, int32_t kh, int32_t kw, const double* psf);
+
+/* Edge weights d of D = diag(d) (host array of n_edges values in (0, 1]).
+ * Rebuilds the lambda-independent multigrid hierarchy on the device
+ * (G_L^{k+1} = P^T G_L^k P, G_A^{k+1} = P^T G_A^k P, Sec. 3.1-3.2).
+ * Errors: INVALID_ARG (count, non-positive or non-finite entries), STATE. */
+int lcmg_set_weights(lcmg_ctx* ctx, const double* d, int64_t n_edges);
+int lcmg_set_weights_dev(lcmg_ctx* ctx, const double* d_dev, int64_t n_edges);
+
+/* Copy the current weights d (n_edges doubles) to a host buffer. */
+int lcmg_get_weights(lcmg_ctx* ctx, double* d_out, int64_t n_edges);
+
+/* Solve eq. (normal) for every (lambda_i, b_r) pair.
+ *   lambda[n_lambda]    strictly increasing, > 0 (host)
+ *   b[n_rhs][m]         right-hand sides, each contiguous (host)
+ *   x0                  NULL (zero initial guesses) or [n_rhs][n_lambda][n]
+ *   x[n_rhs][n_lambda][n]         solutions (host, written)
+ *   resid_norm[n_rhs][n_lambda]   rho = ||A x - b||_2        (may be NULL)
+ *   seminorm[n_rhs][n_lambda]     eta = ||D L x||_2          (may be NULL)
+ *   iters, status [n_rhs][n_lambda]  PCG iterations and lcmg_solve_status
+ *                                    (may be NULL)
+ * Synchronises the stream before returning.  A system that does not
+ * converge is reported in status[], not as an error. */
+int lcmg_solve(lcmg_ctx* ctx, int32_t n_lambda, const double* lambda, int32_t n_rhs,
+               const double* b, const double* x0, double* x, double* resid_norm,
+               double* seminorm, int32_t* iters, int32_t* status);
+
+/* As lcmg_solve with device pointers (same layouts; lambda stays on the
+ * host).  x0_dev may equal x_dev (in-place warm start).  Returns once the
+ * work is enqueued and the iteration has finished (the convergence poll
+ * synchronises on the context's stream). */
+int lcmg_solve_dev(lcmg_ctx* ctx, int32_t n_lambda, const double* lambda, int32_t n_rhs,
+                   const double* b_dev, const double* x0_dev, double* x_dev,
+                   double* resid_norm_dev, double* seminorm_dev, int32_t* iters_dev,
+                   int32_t* status_dev);
+
+/* L-curve corner (Sec. 1): index (0-based) of the point of maximum positive
+ * signed Menger curvature of (log10 rho_i, log10 eta_i), i = 0..k-1 in
+ * order of increasing lambda; ties within 1e-12 relative go to the smaller
+ * lambda; with no positive curvature the maximum over interior points;
+ * endpoints never.  Host only.  Errors: INVALID_ARG if k < 3 or a value is
+ * not positive and finite. */
+int lcmg_lcurve_corner(int32_t k, const double* rho, const double* eta, int32_t* idx);
+
+/* Weight update of eq. (g) from x_star (n values, host): v = D L x_star,
+ * g = |v| / ||v||_inf, d = max(1 - g^q, d_min), D <- diag(d) D; D unchanged
+ * if v = 0.  Rebuilds the hierarchy.  d_out (n_edges, host) may be NULL. */
+int lcmg_update_weights(lcmg_ctx* ctx, const double* x_star, double q, double d_min,
+                        double* d_out);
+int lcmg_update_weights_dev(lcmg_ctx* ctx, const double* x_star_dev, double q,
+                            double d_min);
+
+/* Lambda window of Algorithm 2 (1-based, inclusive): i_prev = 0 marks the
+ * first outer iteration (window 1..m); otherwise
+ * [max(min(i_prev-2, m-9), 1), min(max(i_prev+7, 10), m)].  Host only. */
+int lcmg_cull_lambdas(int32_t m, int32_t i_prev, int32_t* lo, int32_t* hi);
+
+/* Algorithm 2 end to end for one right-hand side b[m] (host) and m_lambda
+ * increasing lambdas: D^(1) = I; per outer iteration: window, hierarchy,
+ * solves (warm-started from the previous outer iteration's solutions; zero
+ * at the first), L-curve corner, stop after three equal selections or
+ * max_outer iterations, else weight update.
+ *   x_out[n]                 the final selected solution x^(i_l, l)
+ *   lambda_idx_history[max_outer]  selected 1-based indices per iteration
+ *   n_outer                  outer iterations run
+ *   n_solves (may be NULL)   systems solved in total (sum of window sizes)
+ *   n_converged (may be NULL) of which reached the tolerance */
+int lcmg_lcurve_run(lcmg_ctx* ctx, int32_t m_lambda, const double* lambda, const double* b,
+                    int32_t max_outer, double* x_out, int32_t* lambda_idx_history,
+                    int32_t* n_outer, int64_t* n_solves, int64_t* n_converged);
+
+/* Same with b and x_out as device pointers. */
+int lcmg_lcurve_run_dev(lcmg_ctx* ctx, int32_t m_lambda, const double* lambda,
+                        const double* b_dev, int32_t max_outer, double* x_out_dev,
+                        int32_t* lambda_idx_history, int32_t* n_outer, int64_t* n_solves,
+                        int64_t* n_converged);
+
+/* Statistics of the last solve: total PCG iterations over all systems, the
+ * number of batched iterations issued, kernel launches issued, and the
+ * milliseconds spent in the device iteration (CUDA events). */
+typedef struct {
+  int64_t column_iterations;
+  int64_t batch_iterations;
+  int64_t kernel_launches;
+  double iterate_ms;
+} lcmg_stats;
+int lcmg_get_stats(lcmg_ctx* ctx, lcmg_stats* out);
+
+/* Apply K = A^T A + lambda^2 L^T D^2 L to n_cols device vectors
+ * x_dev[n_cols][n] -> y_dev[n_cols][n] in FP64 (one lambda per column). */
+int lcmg_apply_normal_dev(lcmg_ctx* ctx, int32_t n_cols, const double* lambda,
+                          const double* x_dev, double* y_dev);
+
+/* Apply one V-cycle z = B(lambda) r to n_cols device vectors (FP64 or the
+ * context's precision), r_dev, z_dev laid out [n_cols][n]. */
+int lcmg_apply_vcycle_dev(lcmg_ctx* ctx, int32_t n_cols, const double* lambda,
+                          const double* r_dev, double* z_dev);
+
+/* Copy the Galerkin coarse operators of level k >= 1 to the host: 25
+ * coefficient arrays per part, gl[25][n_k] and ga[25][n_k], offset index
+ * (di + 2) + 5 (dj + 2) for the neighbour (i + di, j + dj).  Level 0 is the
+ * 5-point fine operator.  Returns the level's n_v, n_h. */
+int lcmg_get_level(lcmg_ctx* ctx, int32_t k, int32_t* n_v, int32_t* n_h, double* gl,
+                   double* ga);
+
+/* Number of multigrid levels of the current hierarchy. */
+int lcmg_num_levels(lcmg_ctx* ctx, int32_t* levels);
+
+/* diag(A^T A) (n doubles, host). */
+int lcmg_get_diag(lcmg_ctx* ctx, double* diag_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LCMG_H */

@@ -1,0 +1,1422 @@
+// liblcmg: host runtime and C ABI (see include/lcmg.h).
+//
+// The context owns the forward operator (CSR A and its transpose, or a
+// PSF), the edge weights, the lambda-independent Galerkin hierarchy and a
+// workspace sized for the widest batch seen.  A solve advances all
+// (lambda, right-hand side) columns of a batch together: every PCG
+// iteration is a fixed sequence of kernel launches whose per-column
+// scalars (alpha, beta, convergence) stay on the device; the host polls a
+// few counters every `check_every` iterations, and then runs the
+// true-residual check (and, on the mixed path, the reliable update) in
+// FP64.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "lcmg.h"
+
+namespace lcmg {
+
+static thread_local std::string g_err;
+
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  // grow-only allocation of at least cnt elements
+  T* need(size_t cnt) {
+    if (cnt == 0) cnt = 1;
+    if (p && n >= cnt) return p;
+    release();
+    void* q = nullptr;
+    if (cudaMalloc(&q, cnt * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      throw MemError("device allocation of " + std::to_string(cnt * sizeof(T)) + " bytes failed");
+    }
+    p = static_cast<T*>(q);
+    n = cnt;
+    return p;
+  }
+};
+
+struct Level {
+  int nv = 0, nh = 0;
+  int64_t n = 0;
+  DevBuf<double> gl, ga;   // 25 x n (levels >= 1)
+  DevBuf<float> gl32, ga32;
+};
+
+struct LevelWork {
+  DevBuf<char> rhs, z, t, res, dinv;  // T-typed, n_k x B
+};
+
+constexpr int kMaxBlocks = 2048;
+
+}  // namespace lcmg
+
+using namespace lcmg;
+
+struct lcmg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  lcmg_params prm{};
+  int sms = 0;
+  int maxblk = 0;
+  // grid
+  int nv = 0, nh = 0;
+  int64_t n = 0, ne = 0;
+  // forward operator
+  int fwd = 0;  // 0 none, 1 CSR, 2 PSF
+  int64_t m = 0, nnz = 0;
+  int vdtype = 0;  // 0 FP32 values, 1 FP64 values
+  DevBuf<int64_t> rp, rpT;
+  DevBuf<int32_t> ci, ciT;
+  DevBuf<float> v32, vT32;
+  DevBuf<double> v64, vT64;
+  int rv = 0, rh = 0;
+  DevBuf<double> psf64;
+  DevBuf<float> psf32;
+  DevBuf<double> diag;
+  DevBuf<float> diag32;
+  // weights
+  DevBuf<double> d, ws, we;
+  DevBuf<float> ws32, we32;
+  // hierarchy
+  std::vector<Level> lev;
+  bool hier_ok = false;
+  // workspace
+  int Bcap = 0;
+  DevBuf<double> x64, c64, r64, y64, bvec, cvec;
+  DevBuf<float> xlo;
+  DevBuf<char> r, z, p, q, y;
+  std::vector<LevelWork> lw;
+  DevBuf<double> lam2;
+  DevBuf<char> lam2T;
+  DevBuf<double> kinv, Mw, Ww;
+  DevBuf<double> part_pq, part_rr, part_rz, part_x;
+  DevBuf<double> s_rz, s_alpha, s_beta, s_rr, s_rmax, s_tol2cc, s_cc, s_rrtrue, s_out;
+  DevBuf<int> s_active, s_iters, s_status, s_pending, s_counters, s_info, s_flag;
+  DevBuf<double*> colptr;
+  DevBuf<int> colmap;
+  int* h_counters = nullptr;  // pinned
+  // weight-update scratch
+  DevBuf<double> absv, bmax;
+  lcmg_stats stats{};
+};
+
+namespace lcmg {
+
+static void set_err(const std::string& s) { g_err = s; }
+
+static void check_params(const lcmg_params& p) {
+  if (p.levels < 0 || p.coarse_max < 1 || p.nu < 1 || p.nu > 16) throw ArgError("invalid levels/coarse_max/nu");
+  if (p.smoother != LCMG_SMOOTH_L1_JACOBI && p.smoother != LCMG_SMOOTH_JACOBI) throw ArgError("invalid smoother");
+  if (!(p.omega > 0.0 && p.omega < 2.0)) throw ArgError("omega must lie in (0, 2)");
+  if (!(p.q > 0.0) || !(p.d_min > 0.0 && p.d_min <= 1.0)) throw ArgError("q must be > 0 and d_min in (0, 1]");
+  if (!(p.tol > 0.0 && p.tol < 1.0) || p.maxit < 1) throw ArgError("tol must lie in (0, 1) and maxit >= 1");
+  if (p.precision != LCMG_PREC_FP64 && p.precision != LCMG_PREC_MIXED) throw ArgError("invalid precision");
+  if (p.mode != LCMG_MODE_BATCHED && p.mode != LCMG_MODE_SEQUENTIAL) throw ArgError("invalid mode");
+  if (p.check_every < 1) throw ArgError("check_every must be >= 1");
+}
+
+static int sum_blocks(int nb) { return std::max(1, std::min(nb, kMaxBlocks)); }
+
+// ---------------------------------------------------------------------------
+// Hierarchy
+// ---------------------------------------------------------------------------
+static int level_count(const lcmg_ctx& c) {
+  if (c.prm.levels > 0) return c.prm.levels;
+  int lv = 1, a = c.nv, b = c.nh;
+  while ((a > c.prm.coarse_max || b > c.prm.coarse_max) && a % 2 == 0 && b % 2 == 0) {
+    a /= 2; b /= 2; ++lv;
+  }
+  return lv;
+}
+
+static void refresh_fine(lcmg_ctx& c) {
+  const int g = (int)std::min<int64_t>((c.n + kBlock - 1) / kBlock, c.maxblk);
+  k_edge_to_pixel<<<g, kBlock, 0, c.stream>>>(c.nv, c.nh, c.d.p, c.ws.need(c.n), c.we.need(c.n));
+  LCMG_LAUNCHED();
+  k_convert<double, float><<<g, kBlock, 0, c.stream>>>(c.n, c.ws.p, c.ws32.need(c.n));
+  LCMG_LAUNCHED();
+  k_convert<double, float><<<g, kBlock, 0, c.stream>>>(c.n, c.we.p, c.we32.need(c.n));
+  LCMG_LAUNCHED();
+  c.hier_ok = false;
+}
+
+static void build_hierarchy(lcmg_ctx& c) {
+  if (c.fwd == 0) throw ArgError("forward operator not set");
+  const int L = level_count(c);
+  int a = c.nv, b = c.nh;
+  for (int k = 1; k < L; ++k) {
+    if (a % 2 || b % 2) throw ArgError("grid sides must be divisible by 2^(levels-1)");
+    a /= 2; b /= 2;
+  }
+  const int64_t nc = (int64_t)a * b;
+  if (nc > 4096) throw ArgError("coarsest level has " + std::to_string(nc) + " unknowns (dense limit 4096): use more levels");
+  c.lev.resize(L);
+  c.lev[0].nv = c.nv; c.lev[0].nh = c.nh; c.lev[0].n = c.n;
+  for (int k = 1; k < L; ++k) {
+    Level& f = c.lev[k - 1];
+    Level& g = c.lev[k];
+    g.nv = f.nv / 2; g.nh = f.nh / 2; g.n = (int64_t)g.nv * g.nh;
+    double* gl = g.gl.need(kStencil * g.n);
+    double* ga = g.ga.need(kStencil * g.n);
+    RapIn in{};
+    in.nvf = f.nv; in.nhf = f.nh; in.nf = f.n;
+    if (k == 1) {
+      in.ws = c.ws.p; in.we = c.we.p; in.ga = c.diag.p;
+      in.part = 0; launch_galerkin(in, g.nv, g.nh, gl, c.maxblk, c.stream);
+      in.part = 1; launch_galerkin(in, g.nv, g.nh, ga, c.maxblk, c.stream);
+    } else {
+      in.part = 2;
+      in.g25 = f.gl.p; launch_galerkin(in, g.nv, g.nh, gl, c.maxblk, c.stream);
+      in.g25 = f.ga.p; launch_galerkin(in, g.nv, g.nh, ga, c.maxblk, c.stream);
+    }
+    const int gg = (int)std::min<int64_t>((kStencil * g.n + kBlock - 1) / kBlock, c.maxblk);
+    k_convert<double, float><<<gg, kBlock, 0, c.stream>>>(kStencil * g.n, gl, g.gl32.need(kStencil * g.n));
+    LCMG_LAUNCHED();
+    k_convert<double, float><<<gg, kBlock, 0, c.stream>>>(kStencil * g.n, ga, g.ga32.need(kStencil * g.n));
+    LCMG_LAUNCHED();
+  }
+  c.hier_ok = true;
+}
+
+static void ensure_hierarchy(lcmg_ctx& c) {
+  if (!c.hier_ok) build_hierarchy(c);
+}
+
+template <class T>
+static LevelView<T> view(const lcmg_ctx& c, int k);
+template <>
+LevelView<double> view<double>(const lcmg_ctx& c, int k) {
+  LevelView<double> v;
+  const Level& l = c.lev[k];
+  v.nv = l.nv; v.nh = l.nh; v.n = l.n;
+  if (k == 0) { v.fine = true; v.ws = c.ws.p; v.we = c.we.p; v.ga = c.diag.p; }
+  else { v.fine = false; v.gl = l.gl.p; v.ga = l.ga.p; }
+  return v;
+}
+template <>
+LevelView<float> view<float>(const lcmg_ctx& c, int k) {
+  LevelView<float> v;
+  const Level& l = c.lev[k];
+  v.nv = l.nv; v.nh = l.nh; v.n = l.n;
+  if (k == 0) { v.fine = true; v.ws = c.ws32.p; v.we = c.we32.p; v.ga = c.diag32.p; }
+  else { v.fine = false; v.gl = l.gl32.p; v.ga = l.ga32.p; }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace
+// ---------------------------------------------------------------------------
+static void ensure_work(lcmg_ctx& c, int B) {
+  const size_t nB = (size_t)c.n * B, mB = (size_t)c.m * B;
+  c.x64.need(nB); c.c64.need(nB); c.r64.need(nB); c.y64.need(std::max(mB, nB));
+  c.xlo.need(nB);
+  const size_t tb = sizeof(double);  // room for either precision
+  c.r.need(nB * tb); c.z.need(nB * tb); c.p.need(nB * tb); c.q.need(nB * tb);
+  c.y.need(std::max(mB, nB) * tb);
+  const int L = (int)c.lev.size();
+  c.lw.resize(L);
+  for (int k = 0; k < L; ++k) {
+    const size_t nk = (size_t)c.lev[k].n * B * tb;
+    c.lw[k].t.need(nk); c.lw[k].res.need(nk); c.lw[k].dinv.need(nk);
+    if (k > 0) { c.lw[k].rhs.need(nk); c.lw[k].z.need(nk); }
+  }
+  const size_t nc = (size_t)c.lev[L - 1].n;
+  c.kinv.need(nc * nc * B); c.Mw.need(nc * nc * B); c.Ww.need(nc * nc * B);
+  c.lam2.need(B); c.lam2T.need(B * tb);
+  const size_t pb = (size_t)kMaxBlocks * B;
+  c.part_pq.need(pb); c.part_rr.need(pb); c.part_rz.need(pb); c.part_x.need(pb);
+  for (auto* b : {&c.s_rz, &c.s_alpha, &c.s_beta, &c.s_rr, &c.s_rmax, &c.s_tol2cc, &c.s_cc, &c.s_rrtrue, &c.s_out})
+    b->need(B);
+  for (auto* b : {&c.s_active, &c.s_iters, &c.s_status, &c.s_pending, &c.s_info, &c.s_flag}) b->need(B);
+  c.s_counters.need(4);
+  if (!c.h_counters) LCMG_CUDA(cudaMallocHost(&c.h_counters, 4 * sizeof(int)));
+  c.Bcap = std::max(c.Bcap, B);
+}
+
+static ColState colstate(lcmg_ctx& c) {
+  ColState s;
+  s.rz = c.s_rz.p; s.alpha = c.s_alpha.p; s.beta = c.s_beta.p; s.rr = c.s_rr.p; s.rmax = c.s_rmax.p;
+  s.tol2cc = c.s_tol2cc.p; s.active = c.s_active.p; s.iters = c.s_iters.p; s.status = c.s_status.p;
+  s.pending = c.s_pending.p; s.counters = c.s_counters.p;
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Batched solver for one precision T (double: FP64 path; float: mixed)
+// ---------------------------------------------------------------------------
+template <class T>
+struct Batch {
+  lcmg_ctx& c;
+  int B;
+  cudaStream_t s;
+  int nlev;
+
+  Batch(lcmg_ctx& c_, int B_) : c(c_), B(B_), s(c_.stream), nlev((int)c_.lev.size()) {}
+
+  T* tp(DevBuf<char>& b) { return reinterpret_cast<T*>(b.p); }
+  const T* lam2T() { return reinterpret_cast<const T*>(c.lam2T.p); }
+  FineOp<T> fop() { return view<T>(c, 0).fine_op(); }
+  FineOp<double> fop64() { return view<double>(c, 0).fine_op(); }
+
+  SpmmArgs args(bool trans, int ld) {
+    SpmmArgs a{};
+    a.rows = trans ? c.n : c.m;
+    a.rp = trans ? c.rpT.p : c.rp.p;
+    a.ci = trans ? c.ciT.p : c.ci.p;
+    a.B = ld; a.c0 = 0; a.nb = ld; a.nl = 1; a.nrhs = 1;
+    return a;
+  }
+  PsfArgs psf() {
+    PsfArgs a{};
+    a.nv = c.nv; a.nh = c.nh; a.rv = c.rv; a.rh = c.rh; a.psf = c.psf64.p;
+    return a;
+  }
+  const T* psfT();
+
+  // q = K p (T precision) with partials of p.q; returns the partial count
+  int apply_K(const T* P, T* Q, double* part);
+  // r64 = c64 - K x64 in FP64 with partials of r64.r64
+  int true_residual(double* part);
+
+  // ---- V-cycle (Algorithm 1, gamma = 1, zero initial guess) ----------
+  void sweeps(int k, int m, const T* rhs, T* z, T* t, double* part, int* nb_out) {
+    // m Jacobi sweeps z <- z + D^{-1}(rhs - K z), ending in z
+    if (m <= 0) return;
+    LevelView<T> L = view<T>(c, k);
+    const T* dinv = tp(c.lw[k].dinv);
+    T* a = z;
+    T* b = t;
+    for (int i = 0; i < m; ++i) {
+      const bool last = (i == m - 1);
+      int nb = launch_smooth<T>(L, B, lam2T(), dinv, rhs, a, b, nullptr, (last && (m % 2 == 0)) ? part : nullptr,
+                                c.maxblk, s);
+      if (last && (m % 2 == 0) && nb_out) *nb_out = nb;
+      std::swap(a, b);
+    }
+    if (m % 2 == 1) {  // result is in t: copy back
+      launch_copy_cols<T>(L.n, B, nullptr, t, z, c.maxblk, s);
+      if (part) {
+        const int g = grid_for(L.n, B, c.maxblk);
+        k_col_dot<T><<<g, kBlock, 0, s>>>(L.n, B, rhs, z, part);
+        LCMG_LAUNCHED();
+        if (nb_out) *nb_out = g;
+      }
+    }
+  }
+
+  int vcycle(const T* r0, T* z0, double* part) {
+    const int nu = c.prm.nu;
+    int nb = 0;
+    if (nlev == 1) {
+      launch_coarse_solve<T>((int)c.lev[0].n, B, c.kinv.p, r0, z0, s);
+      const int g = grid_for(c.n, B, c.maxblk);
+      k_col_dot<T><<<g, kBlock, 0, s>>>(c.n, B, r0, z0, part);
+      LCMG_LAUNCHED();
+      return g;
+    }
+    std::vector<const T*> rhs(nlev);
+    std::vector<T*> zz(nlev);
+    rhs[0] = r0; zz[0] = z0;
+    for (int k = 1; k < nlev; ++k) { rhs[k] = tp(c.lw[k].rhs); zz[k] = tp(c.lw[k].z); }
+    for (int k = 0; k + 1 < nlev; ++k) {
+      LevelView<T> L = view<T>(c, k);
+      const T* dinv = tp(c.lw[k].dinv);
+      launch_smooth_zero<T>(L, B, lam2T(), dinv, rhs[k], zz[k], nu >= 2 ? 1 : 0, c.maxblk, s);
+      sweeps(k, nu - std::min(nu, 2), rhs[k], zz[k], tp(c.lw[k].t), nullptr, nullptr);
+      launch_residual<T>(L, B, lam2T(), rhs[k], zz[k], tp(c.lw[k].res), c.maxblk, s);
+      launch_restrict<T>(c.lev[k + 1].nv, c.lev[k + 1].nh, B, tp(c.lw[k].res), tp(c.lw[k + 1].rhs), c.maxblk, s);
+    }
+    launch_coarse_solve<T>((int)c.lev[nlev - 1].n, B, c.kinv.p, rhs[nlev - 1], zz[nlev - 1], s);
+    for (int k = nlev - 2; k >= 0; --k) {
+      launch_prolong_add<T>(c.lev[k + 1].nv, c.lev[k + 1].nh, B, zz[k + 1], zz[k], c.maxblk, s);
+      sweeps(k, nu, rhs[k], zz[k], tp(c.lw[k].t), k == 0 ? part : nullptr, k == 0 ? &nb : nullptr);
+    }
+    return nb;
+  }
+
+  // ---- setup of one batch --------------------------------------------
+  void setup(const std::vector<double>& lam) {
+    std::vector<double> l2(B);
+    std::vector<T> l2t(B);
+    for (int j = 0; j < B; ++j) { l2[j] = lam[j] * lam[j]; l2t[j] = (T)l2[j]; }
+    LCMG_CUDA(cudaMemcpyAsync(c.lam2.p, l2.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
+    LCMG_CUDA(cudaMemcpyAsync(c.lam2T.p, l2t.data(), sizeof(T) * B, cudaMemcpyHostToDevice, s));
+    for (int k = 0; k < nlev; ++k)
+      launch_dinv<T>(view<T>(c, k), B, c.lam2.p, c.prm.smoother, c.prm.omega, tp(c.lw[k].dinv), c.maxblk, s);
+    launch_dense_setup(view<double>(c, nlev - 1), B, c.lam2.p, c.Mw.p, c.Ww.p, c.kinv.p, c.s_info.p, c.maxblk, s);
+    // the host copy of lam2 must stay valid until the copies complete
+    LCMG_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> info(B);
+    LCMG_CUDA(cudaMemcpy(info.data(), c.s_info.p, sizeof(int) * B, cudaMemcpyDeviceToHost));
+    for (int j = 0; j < B; ++j)
+      if (info[j] != 0) throw ArgError("coarsest-level Cholesky failed (pivot " + std::to_string(info[j]) + ")");
+  }
+
+  void read_counters() {
+    LCMG_CUDA(cudaMemcpyAsync(c.h_counters, c.s_counters.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    LCMG_CUDA(cudaStreamSynchronize(s));
+  }
+
+  // one PCG iteration for all active columns
+  void iterate_once() {
+    ColState st = colstate(c);
+    T* P = tp(c.p);
+    T* Q = tp(c.q);
+    T* R = tp(c.r);
+    T* Z = tp(c.z);
+    const int nb_pq = apply_K(P, Q, c.part_pq.p);
+    k_scalar_alpha<<<1, kScalarThreads, 0, s>>>(B, nb_pq, c.part_pq.p, st);
+    LCMG_LAUNCHED();
+    int nb_rr;
+    if (std::is_same<T, double>::value)
+      nb_rr = launch_update_xr<T, T>(c.n, B, st, P, Q, reinterpret_cast<T*>(c.x64.p), R, c.part_rr.p, c.maxblk, s);
+    else
+      nb_rr = launch_update_xr<T, T>(c.n, B, st, P, Q, reinterpret_cast<T*>(c.xlo.p), R, c.part_rr.p, c.maxblk, s);
+    const int nb_rz = vcycle(R, Z, c.part_rz.p);
+    const double trig = std::is_same<T, float>::value ? 0.01 : 0.0;  // ||r|| fell 10x since the last update
+    k_scalar_beta<<<1, kScalarThreads, 0, s>>>(B, nb_rr, c.part_rr.p, nb_rz, c.part_rz.p, st, c.prm.maxit, trig);
+    LCMG_LAUNCHED();
+    launch_update_p<T>(c.n, B, st, Z, P, c.maxblk, s);
+  }
+
+  // true-residual check of pending columns; on the mixed path also the
+  // reliable update of every running column
+  void true_check(bool replace_active) {
+    ColState st = colstate(c);
+    if (!std::is_same<T, double>::value) {
+      const int g = (int)std::min<int64_t>(((int64_t)c.n * B + kBlock - 1) / kBlock, c.maxblk);
+      k_flush_x<<<g, kBlock, 0, s>>>((int64_t)c.n * B, c.xlo.p, c.x64.p);
+      LCMG_LAUNCHED();
+    }
+    const int nb = true_residual(c.part_x.p);
+    k_sum_parts<<<1, kScalarThreads, 0, s>>>(B, nb, c.part_x.p, c.s_rrtrue.p);
+    LCMG_LAUNCHED();
+    k_true_check<<<1, kBlock, 0, s>>>(B, c.s_rrtrue.p, st, replace_active ? 1 : 0, c.s_flag.p);
+    LCMG_LAUNCHED();
+    const int g = grid_for(c.n, B, c.maxblk);
+    k_take_residual<T><<<g, kBlock, 0, s>>>(c.n, B, c.s_flag.p, c.r64.p, tp(c.r));
+    LCMG_LAUNCHED();
+    read_counters();
+    if (c.h_counters[3] > 0) {  // restarted columns: z = B r, p = z, rz = r.z
+      const int nbz = vcycle(tp(c.r), tp(c.z), c.part_rz.p);
+      k_restart_finish<T><<<g, kBlock, 0, s>>>(c.n, B, nbz, c.part_rz.p, c.s_flag.p, st, tp(c.z), tp(c.p));
+      LCMG_LAUNCHED();
+    }
+  }
+
+  // Run PCG on the batch whose x64 (initial guesses) and c64 (right-hand
+  // sides A^T b) are set.  Returns the number of batch iterations.
+  int64_t run(const std::vector<double>& lam) {
+    setup(lam);
+    ColState st = colstate(c);
+    // ||c||^2 and the true initial residual
+    const int g = grid_for(c.n, B, c.maxblk);
+    k_col_dot<double><<<g, kBlock, 0, s>>>(c.n, B, c.c64.p, c.c64.p, c.part_x.p);
+    LCMG_LAUNCHED();
+    k_sum_parts<<<1, kScalarThreads, 0, s>>>(B, g, c.part_x.p, c.s_cc.p);
+    LCMG_LAUNCHED();
+    k_zero_cols<<<g, kBlock, 0, s>>>(c.n, B, c.s_cc.p, c.x64.p);
+    LCMG_LAUNCHED();
+    const int nb = true_residual(c.part_x.p);
+    k_sum_parts<<<1, kScalarThreads, 0, s>>>(B, nb, c.part_x.p, c.s_rrtrue.p);
+    LCMG_LAUNCHED();
+    k_init_state<<<1, kBlock, 0, s>>>(B, c.prm.tol, c.s_cc.p, c.s_rrtrue.p, st);
+    LCMG_LAUNCHED();
+    // r = (T) r64 for every column
+    LCMG_CUDA(cudaMemsetAsync(c.s_flag.p, 0, sizeof(int) * B, s));
+    {
+      std::vector<int> ones(B, 1);
+      LCMG_CUDA(cudaMemcpyAsync(c.s_flag.p, ones.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+      k_take_residual<T><<<g, kBlock, 0, s>>>(c.n, B, c.s_flag.p, c.r64.p, tp(c.r));
+      LCMG_LAUNCHED();
+      LCMG_CUDA(cudaStreamSynchronize(s));
+    }
+    if (!std::is_same<T, double>::value) LCMG_CUDA(cudaMemsetAsync(c.xlo.p, 0, sizeof(float) * c.n * B, s));
+    // z = B r ; p = z ; rz = r.z   (for every column; frozen ones are unaffected)
+    const int nbz = vcycle(tp(c.r), tp(c.z), c.part_rz.p);
+    k_sum_parts<<<1, kScalarThreads, 0, s>>>(B, nbz, c.part_rz.p, c.s_rz.p);
+    LCMG_LAUNCHED();
+    launch_copy_cols<T>(c.n, B, nullptr, tp(c.z), tp(c.p), c.maxblk, s);
+    int64_t batch_its = 0;
+    cudaEvent_t e0, e1;
+    LCMG_CUDA(cudaEventCreate(&e0));
+    LCMG_CUDA(cudaEventCreate(&e1));
+    LCMG_CUDA(cudaEventRecord(e0, s));
+    // counters as left by k_init_state are not set: read active directly
+    std::vector<int> act(B);
+    LCMG_CUDA(cudaMemcpyAsync(act.data(), c.s_active.p, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+    LCMG_CUDA(cudaStreamSynchronize(s));
+    int active = 0;
+    for (int v : act) active += v;
+    const int every = c.prm.check_every;
+    const bool mixed = !std::is_same<T, double>::value;
+    // one block of `every` iterations, captured once into a CUDA graph
+    cudaGraphExec_t exec = nullptr;
+    int64_t per_block = 0;  // kernels in one captured block
+    if (c.prm.graphs && active > 0) {
+      cudaGraph_t graph = nullptr;
+      const int64_t l0 = launch_counter();
+      LCMG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      try {
+        for (int i = 0; i < every; ++i) iterate_once();
+      } catch (...) {
+        cudaStreamEndCapture(s, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+      }
+      per_block = launch_counter() - l0;
+      launch_counter() = l0;  // captured, not executed
+      LCMG_CUDA(cudaStreamEndCapture(s, &graph));
+      const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      LCMG_CUDA(ie);
+    }
+    struct ExecGuard {
+      cudaGraphExec_t e;
+      ~ExecGuard() {
+        if (e) cudaGraphExecDestroy(e);
+      }
+    } guard{exec};
+    while (active > 0) {
+      if (exec) {
+        LCMG_CUDA(cudaGraphLaunch(exec, s));
+        launch_counter() += per_block;
+      } else {
+        for (int i = 0; i < every; ++i) iterate_once();
+      }
+      batch_its += every;
+      read_counters();
+      active = c.h_counters[0];
+      const int pending = c.h_counters[1];
+      const int votes = c.h_counters[2];
+      if (pending > 0 || (mixed && votes > 0) || active == 0) {
+        true_check(mixed);
+        active = c.h_counters[0];
+      }
+      if (batch_its > (int64_t)c.prm.maxit + 4LL * every + 64) break;  // safety net
+    }
+    if (!std::is_same<T, double>::value) {
+      const int gg = (int)std::min<int64_t>(((int64_t)c.n * B + kBlock - 1) / kBlock, c.maxblk);
+      k_flush_x<<<gg, kBlock, 0, s>>>((int64_t)c.n * B, c.xlo.p, c.x64.p);
+      LCMG_LAUNCHED();
+    }
+    LCMG_CUDA(cudaEventRecord(e1, s));
+    LCMG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c.stats.iterate_ms += ms;
+    c.stats.batch_iterations += batch_its;
+    return batch_its;
+  }
+};
+
+template <class T>
+const T* Batch<T>::psfT() {
+  return std::is_same<T, double>::value ? reinterpret_cast<const T*>(c.psf64.p)
+                                        : reinterpret_cast<const T*>(c.psf32.p);
+}
+
+template <class T>
+int Batch<T>::apply_K(const T* P, T* Q, double* part) {
+  T* Y = tp(c.y);
+  if (c.fwd == 1) {
+    SpmmArgs a = args(false, B);
+    SpmmArgs at = args(true, B);
+    if (std::is_same<T, float>::value) {
+      const float* va = c.vdtype == 0 ? c.v32.p : c.v32.p;
+      const float* vt = c.vdtype == 0 ? c.vT32.p : c.vT32.p;
+      launch_spmm<float, float, float, 0>(a, va, reinterpret_cast<const float*>(P), reinterpret_cast<float*>(Y),
+                                          view<float>(c, 0).fine_op(), nullptr, nullptr, nullptr, nullptr,
+                                          nullptr, c.maxblk, s);
+      return launch_spmm<float, float, float, 1>(at, vt, reinterpret_cast<const float*>(Y),
+                                                 reinterpret_cast<float*>(Q), view<float>(c, 0).fine_op(),
+                                                 reinterpret_cast<const float*>(P), nullptr, c.lam2.p, nullptr,
+                                                 part, c.maxblk, s);
+    } else {
+      const double* Pd = reinterpret_cast<const double*>(P);
+      double* Qd = reinterpret_cast<double*>(Q);
+      double* Yd = reinterpret_cast<double*>(Y);
+      if (c.vdtype == 1) {
+        launch_spmm<double, double, double, 0>(a, c.v64.p, Pd, Yd, fop64(), nullptr, nullptr, nullptr, nullptr,
+                                               nullptr, c.maxblk, s);
+        return launch_spmm<double, double, double, 1>(at, c.vT64.p, Yd, Qd, fop64(), Pd, nullptr, c.lam2.p,
+                                                      nullptr, part, c.maxblk, s);
+      }
+      launch_spmm<float, double, double, 0>(a, c.v32.p, Pd, Yd, fop64(), nullptr, nullptr, nullptr, nullptr,
+                                            nullptr, c.maxblk, s);
+      return launch_spmm<float, double, double, 1>(at, c.vT32.p, Yd, Qd, fop64(), Pd, nullptr, c.lam2.p,
+                                                   nullptr, part, c.maxblk, s);
+    }
+  }
+  // PSF operator
+  const int g = grid_for(c.n, B, c.maxblk);
+  PsfArgs pa = psf();
+  k_psf_forward<T, 0><<<g, kBlock, 0, s>>>(pa, psfT(), B, P, Y, nullptr, 1, 1, nullptr);
+  LCMG_LAUNCHED();
+  k_psf_normal<T, T, 1><<<g, kBlock, 0, s>>>(pa, psfT(), B, Y, fop(), P, nullptr, c.lam2.p, Q, part);
+  LCMG_LAUNCHED();
+  return g;
+}
+
+template <class T>
+int Batch<T>::true_residual(double* part) {
+  double* Y = c.y64.p;
+  if (c.fwd == 1) {
+    SpmmArgs a = args(false, B);
+    SpmmArgs at = args(true, B);
+    if (c.vdtype == 1) {
+      launch_spmm<double, double, double, 0>(a, c.v64.p, c.x64.p, Y, fop64(), nullptr, nullptr, nullptr, nullptr,
+                                             nullptr, c.maxblk, s);
+      return launch_spmm<double, double, double, 3>(at, c.vT64.p, Y, c.r64.p, fop64(), c.x64.p, c.c64.p,
+                                                    c.lam2.p, nullptr, part, c.maxblk, s);
+    }
+    launch_spmm<float, double, double, 0>(a, c.v32.p, c.x64.p, Y, fop64(), nullptr, nullptr, nullptr, nullptr,
+                                          nullptr, c.maxblk, s);
+    return launch_spmm<float, double, double, 3>(at, c.vT32.p, Y, c.r64.p, fop64(), c.x64.p, c.c64.p, c.lam2.p,
+                                                 nullptr, part, c.maxblk, s);
+  }
+  const int g = grid_for(c.n, B, c.maxblk);
+  PsfArgs pa = psf();
+  k_psf_forward<double, 0><<<g, kBlock, 0, s>>>(pa, c.psf64.p, B, c.x64.p, Y, nullptr, 1, 1, nullptr);
+  LCMG_LAUNCHED();
+  k_psf_normal<double, double, 3><<<g, kBlock, 0, s>>>(pa, c.psf64.p, B, Y, fop64(), c.x64.p, c.c64.p, c.lam2.p,
+                                                       c.r64.p, part);
+  LCMG_LAUNCHED();
+  return g;
+}
+
+// ---------------------------------------------------------------------------
+// Solve driver
+// ---------------------------------------------------------------------------
+// c = A^T b for the nrhs right-hand sides (b interleaved [m][nrhs] in c.bvec)
+static void compute_rhs(lcmg_ctx& c, int nrhs) {
+  double* cv = c.cvec.need((size_t)c.n * nrhs);
+  if (c.fwd == 1) {
+    SpmmArgs a{};
+    a.rows = c.n; a.rp = c.rpT.p; a.ci = c.ciT.p; a.B = nrhs; a.c0 = 0; a.nb = nrhs; a.nl = 1; a.nrhs = 1;
+    FineOp<double> f = view<double>(c, 0).fine_op();
+    if (c.vdtype == 1)
+      launch_spmm<double, double, double, 0>(a, c.vT64.p, c.bvec.p, cv, f, nullptr, nullptr, nullptr, nullptr,
+                                             nullptr, c.maxblk, c.stream);
+    else
+      launch_spmm<float, double, double, 0>(a, c.vT32.p, c.bvec.p, cv, f, nullptr, nullptr, nullptr, nullptr,
+                                            nullptr, c.maxblk, c.stream);
+  } else {
+    PsfArgs pa{};
+    pa.nv = c.nv; pa.nh = c.nh; pa.rv = c.rv; pa.rh = c.rh; pa.psf = c.psf64.p;
+    k_psf_rhs<<<grid_for(c.n, nrhs, c.maxblk), kBlock, 0, c.stream>>>(pa, nrhs, c.bvec.p, cv);
+    LCMG_LAUNCHED();
+  }
+}
+
+// Solve the columns cols (each = (lambda index li, rhs index ri)) as one
+// batch.  x0p: planar initial guesses per column (device, may be null) ;
+// outputs planar per column.
+struct ColSpec {
+  double lam;
+  int rhs;
+};
+
+static void solve_columns(lcmg_ctx& c, const std::vector<ColSpec>& cols, int nrhs,
+                          const std::vector<const double*>& x0, const std::vector<double*>& xout,
+                          double* rho, double* eta, int* iters, int* status) {
+  const int B = (int)cols.size();
+  ensure_work(c, B);
+  cudaStream_t s = c.stream;
+  // column pointer tables and the column -> right-hand-side map
+  std::vector<const double*> hptr(2 * B);
+  std::vector<int> hmap(B);
+  for (int j = 0; j < B; ++j) {
+    hptr[j] = x0[j];
+    hptr[B + j] = xout[j];
+    hmap[j] = cols[j].rhs;
+  }
+  const double** dptr = static_cast<const double**>(static_cast<void*>(c.colptr.need(2 * B)));
+  int* dmap = c.colmap.need(B);
+  LCMG_CUDA(cudaMemcpyAsync(dptr, hptr.data(), sizeof(double*) * 2 * B, cudaMemcpyHostToDevice, s));
+  LCMG_CUDA(cudaMemcpyAsync(dmap, hmap.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
+  const int gn = grid_for(c.n, B, c.maxblk);
+  k_gather_cols<<<gn, kBlock, 0, s>>>(c.n, B, dptr, c.x64.p);
+  LCMG_LAUNCHED();
+  k_gather_map<<<gn, kBlock, 0, s>>>(c.n, B, nrhs, dmap, c.cvec.p, c.c64.p);
+  LCMG_LAUNCHED();
+  LCMG_CUDA(cudaStreamSynchronize(s));  // host tables must outlive the copies
+  std::vector<double> lam(B);
+  for (int j = 0; j < B; ++j) lam[j] = cols[j].lam;
+  if (c.prm.precision == LCMG_PREC_FP64) {
+    Batch<double> b(c, B);
+    b.run(lam);
+  } else {
+    Batch<float> b(c, B);
+    b.run(lam);
+  }
+  // outputs: x (the pointer table is unchanged since the gather)
+  k_scatter_cols<<<gn, kBlock, 0, s>>>(c.n, B, c.x64.p, c.colptr.p + B);
+  LCMG_LAUNCHED();
+  // rho = ||A x - b|| per column: b of each column's right-hand side
+  double* bcol = c.y64.p;  // [m][B]
+  k_gather_map<<<grid_for(c.m, B, c.maxblk), kBlock, 0, s>>>(c.m, B, nrhs, dmap, c.bvec.p, bcol);
+  LCMG_LAUNCHED();
+  int nb;
+  if (c.fwd == 1) {
+    SpmmArgs a{};
+    a.rows = c.m; a.rp = c.rp.p; a.ci = c.ci.p; a.B = B; a.c0 = 0; a.nb = B; a.nl = 1; a.nrhs = B;
+    FineOp<double> f = view<double>(c, 0).fine_op();
+    if (c.vdtype == 1)
+      nb = launch_spmm<double, double, double, 2>(a, c.v64.p, c.x64.p, (double*)nullptr, f, nullptr, nullptr,
+                                                  nullptr, bcol, c.part_x.p, c.maxblk, s);
+    else
+      nb = launch_spmm<float, double, double, 2>(a, c.v32.p, c.x64.p, (double*)nullptr, f, nullptr, nullptr,
+                                                 nullptr, bcol, c.part_x.p, c.maxblk, s);
+  } else {
+    PsfArgs pa{};
+    pa.nv = c.nv; pa.nh = c.nh; pa.rv = c.rv; pa.rh = c.rh; pa.psf = c.psf64.p;
+    nb = grid_for(c.n, B, c.maxblk);
+    k_psf_forward<double, 2><<<nb, kBlock, 0, s>>>(pa, c.psf64.p, B, c.x64.p, nullptr, bcol, 1, B, c.part_x.p);
+    LCMG_LAUNCHED();
+  }
+  k_sum_parts<<<1, kScalarThreads, 0, s>>>(B, nb, c.part_x.p, c.s_out.p);
+  LCMG_LAUNCHED();
+  std::vector<double> hr(B), he(B);
+  LCMG_CUDA(cudaMemcpyAsync(hr.data(), c.s_out.p, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+  const int g = grid_for(c.n, B, c.maxblk);
+  k_seminorm<<<g, kBlock, 0, s>>>(c.nv, c.nh, B, c.ws.p, c.we.p, c.x64.p, c.part_x.p);
+  LCMG_LAUNCHED();
+  k_sum_parts<<<1, kScalarThreads, 0, s>>>(B, g, c.part_x.p, c.s_out.p);
+  LCMG_LAUNCHED();
+  LCMG_CUDA(cudaMemcpyAsync(he.data(), c.s_out.p, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
+  std::vector<int> hi(B), hs(B);
+  LCMG_CUDA(cudaMemcpyAsync(hi.data(), c.s_iters.p, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+  LCMG_CUDA(cudaMemcpyAsync(hs.data(), c.s_status.p, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+  LCMG_CUDA(cudaStreamSynchronize(s));
+  for (int j = 0; j < B; ++j) {
+    if (rho) rho[j] = std::sqrt(hr[j]);
+    if (eta) eta[j] = std::sqrt(he[j]);
+    if (iters) iters[j] = hi[j];
+    if (status) status[j] = hs[j] == ST_RUNNING ? ST_MAXIT : hs[j];
+    c.stats.column_iterations += hi[j];
+  }
+}
+
+static void require_ready(lcmg_ctx& c) {
+  if (c.nv == 0) throw ArgError("set_grid has not been called");
+  if (c.fwd == 0) throw ArgError("forward operator not set");
+  ensure_hierarchy(c);
+}
+
+static void check_lambdas(int nl, const double* lam) {
+  if (nl < 1 || !lam) throw ArgError("empty lambda list");
+  for (int i = 0; i < nl; ++i) {
+    if (!(lam[i] > 0.0) || !std::isfinite(lam[i])) throw ArgError("lambdas must be positive and finite");
+    if (i > 0 && !(lam[i] > lam[i - 1])) throw ArgError("lambdas must be strictly increasing");
+  }
+}
+
+// Solve for all (lambda, rhs) pairs; b_dev interleaved already in c.bvec and
+// c.cvec computed.  x0/x: device planar [nrhs][nl][n].
+static void solve_all(lcmg_ctx& c, int nl, const double* lam, int nrhs, const double* x0, double* x,
+                      double* rho, double* eta, int* iters, int* status) {
+  const int64_t n = c.n;
+  if (c.prm.mode == LCMG_MODE_BATCHED) {
+    const int total = nl * nrhs;
+    for (int start = 0; start < total; start += kMaxB) {
+      const int cnt = std::min(kMaxB, total - start);
+      std::vector<ColSpec> cols(cnt);
+      std::vector<const double*> x0s(cnt);
+      std::vector<double*> xs(cnt);
+      for (int j = 0; j < cnt; ++j) {
+        const int idx = start + j;  // idx = r * nl + li
+        cols[j].rhs = idx / nl;
+        cols[j].lam = lam[idx % nl];
+        x0s[j] = x0 ? x0 + (int64_t)idx * n : nullptr;
+        xs[j] = x + (int64_t)idx * n;
+      }
+      solve_columns(c, cols, nrhs, x0s, xs, rho ? rho + start : nullptr, eta ? eta + start : nullptr,
+                    iters ? iters + start : nullptr, status ? status + start : nullptr);
+    }
+    return;
+  }
+  // sequential: per rhs, largest lambda first, each warm-started from the
+  // previous lambda's solution (Sec. 3.3); the first from x0 (if given)
+  for (int r = 0; r < nrhs; ++r) {
+    const double* prev = nullptr;
+    for (int li = nl - 1; li >= 0; --li) {
+      const int64_t idx = (int64_t)r * nl + li;
+      std::vector<ColSpec> cols{{lam[li], r}};
+      const double* start = prev ? prev : (x0 ? x0 + idx * n : nullptr);
+      std::vector<const double*> x0s{start};
+      std::vector<double*> xs{x + idx * n};
+      solve_columns(c, cols, nrhs, x0s, xs, rho ? rho + idx : nullptr, eta ? eta + idx : nullptr,
+                    iters ? iters + idx : nullptr, status ? status + idx : nullptr);
+      prev = x + idx * n;
+    }
+  }
+}
+
+static void upload_b(lcmg_ctx& c, int nrhs, const double* b, bool dev) {
+  // b planar [nrhs][m] -> interleaved [m][nrhs]
+  double* bi = c.bvec.need((size_t)c.m * nrhs);
+  DevBuf<double> tmp;
+  const double* src = b;
+  if (!dev) {
+    tmp.need((size_t)c.m * nrhs);
+    LCMG_CUDA(cudaMemcpyAsync(tmp.p, b, sizeof(double) * c.m * nrhs, cudaMemcpyHostToDevice, c.stream));
+    src = tmp.p;
+  }
+  k_planar_to_inter<<<grid_for(c.m, nrhs, c.maxblk), kBlock, 0, c.stream>>>(c.m, nrhs, src, bi);
+  LCMG_LAUNCHED();
+  compute_rhs(c, nrhs);
+  LCMG_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+// ---------------------------------------------------------------------------
+// L-curve corner (host; reading of Sec. 1 stated in lcmg.h)
+// ---------------------------------------------------------------------------
+static int corner_host(int k, const double* rho, const double* eta) {
+  std::vector<double> u(k), v(k), kap(k, -INFINITY);
+  for (int i = 0; i < k; ++i) { u[i] = std::log10(rho[i]); v[i] = std::log10(eta[i]); }
+  for (int i = 1; i + 1 < k; ++i) {
+    const double ax = u[i] - u[i - 1], ay = v[i] - v[i - 1];
+    const double bx = u[i + 1] - u[i], by = v[i + 1] - v[i];
+    const double cx = u[i + 1] - u[i - 1], cy = v[i + 1] - v[i - 1];
+    const double cross = ax * by - ay * bx;
+    const double den = std::hypot(ax, ay) * std::hypot(bx, by) * std::hypot(cx, cy);
+    kap[i] = den > 0 ? 2.0 * cross / den : 0.0;
+  }
+  bool anypos = false;
+  for (int i = 1; i + 1 < k; ++i) anypos |= kap[i] > 0;
+  int best = -1;
+  for (int i = 1; i + 1 < k; ++i) {
+    if (anypos && !(kap[i] > 0)) continue;
+    if (best < 0 || kap[i] > kap[best] + 1e-12 * std::fabs(kap[best])) best = i;
+  }
+  return best;
+}
+
+static void window(int m, int i_prev, int* lo, int* hi) {
+  if (i_prev <= 0) { *lo = 1; *hi = m; return; }
+  *lo = std::max(std::min(i_prev - 2, m - 9), 1);
+  *hi = std::min(std::max(i_prev + 7, 10), m);
+}
+
+static void update_weights_dev(lcmg_ctx& c, const double* xs, double q, double dmin) {
+  if (!(q > 0.0) || !(dmin > 0.0 && dmin <= 1.0)) throw ArgError("q must be > 0 and d_min in (0, 1]");
+  const int g = (int)std::min<int64_t>((c.ne + kBlock - 1) / kBlock, c.maxblk);
+  double* absv = c.absv.need(c.ne);
+  double* bmax = c.bmax.need(g);
+  k_weighted_grad<<<g, kBlock, 0, c.stream>>>(c.nv, c.nh, c.d.p, xs, absv, bmax);
+  LCMG_LAUNCHED();
+  k_weight_apply<<<g, kBlock, 0, c.stream>>>(c.ne, g, bmax, absv, q, dmin, c.d.p);
+  LCMG_LAUNCHED();
+  refresh_fine(c);
+}
+
+// Statistics of one top-level call: reset at entry, launches counted at exit.
+struct StatsScope {
+  lcmg_ctx& c;
+  int64_t l0;
+  explicit StatsScope(lcmg_ctx& c_) : c(c_), l0(launch_counter()) { c.stats = lcmg_stats{}; }
+  ~StatsScope() { c.stats.kernel_launches = launch_counter() - l0; }
+};
+
+static void lcurve_run_impl(lcmg_ctx& c, int m, const double* lam, int max_outer, double* x_out_dev,
+                            int* hist, int* n_outer, int64_t* n_solves, int64_t* n_conv) {
+  check_lambdas(m, lam);
+  if (max_outer < 1) throw ArgError("max_outer must be >= 1");
+  const int64_t n = c.n;
+  DevBuf<double> xres, xstar, xwin;
+  xres.need((size_t)m * n);
+  xstar.need(n);
+  LCMG_CUDA(cudaMemsetAsync(xstar.p, 0, sizeof(double) * n, c.stream));
+  std::vector<int> solved(m, 0);
+  std::vector<int> h;
+  int64_t ns = 0, nconv = 0;
+  int ell = 0;
+  for (ell = 1; ell <= max_outer; ++ell) {
+    int lo, hi;
+    window(m, h.empty() ? 0 : h.back(), &lo, &hi);
+    const int k = hi - lo + 1;
+    ensure_hierarchy(c);
+    xwin.need((size_t)k * n);
+    std::vector<double> rho(k), eta(k);
+    std::vector<int> its(k), st(k);
+    if (c.prm.mode == LCMG_MODE_BATCHED) {
+      // each lambda starts from its own previous solution, else from x*
+      std::vector<ColSpec> cols(k);
+      std::vector<const double*> x0s(k);
+      std::vector<double*> xs(k);
+      for (int j = 0; j < k; ++j) {
+        const int i = lo + j;  // 1-based
+        cols[j] = ColSpec{lam[i - 1], 0};
+        x0s[j] = solved[i - 1] ? xres.p + (int64_t)(i - 1) * n : xstar.p;
+        xs[j] = xwin.p + (int64_t)j * n;
+      }
+      solve_columns(c, cols, 1, x0s, xs, rho.data(), eta.data(), its.data(), st.data());
+    } else {
+      // largest first, chained; the first from x*
+      const double* prev = xstar.p;
+      for (int j = k - 1; j >= 0; --j) {
+        std::vector<ColSpec> cols{{lam[lo + j - 1], 0}};
+        std::vector<const double*> x0s{prev};
+        std::vector<double*> xs{xwin.p + (int64_t)j * n};
+        solve_columns(c, cols, 1, x0s, xs, &rho[j], &eta[j], &its[j], &st[j]);
+        prev = xwin.p + (int64_t)j * n;
+      }
+    }
+    for (int j = 0; j < k; ++j) {
+      LCMG_CUDA(cudaMemcpyAsync(xres.p + (int64_t)(lo + j - 1) * n, xwin.p + (int64_t)j * n, sizeof(double) * n,
+                                cudaMemcpyDeviceToDevice, c.stream));
+      solved[lo + j - 1] = 1;
+      ns += 1;
+      nconv += st[j] == 0;
+    }
+    const int sel = lo + corner_host(k, rho.data(), eta.data());
+    h.push_back(sel);
+    LCMG_CUDA(cudaMemcpyAsync(xstar.p, xwin.p + (int64_t)(sel - lo) * n, sizeof(double) * n,
+                              cudaMemcpyDeviceToDevice, c.stream));
+    const int L = (int)h.size();
+    if (L >= 3 && h[L - 1] == h[L - 2] && h[L - 2] == h[L - 3]) break;
+    if (ell == max_outer) break;
+    update_weights_dev(c, xstar.p, c.prm.q, c.prm.d_min);
+  }
+  LCMG_CUDA(cudaMemcpyAsync(x_out_dev, xstar.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, c.stream));
+  LCMG_CUDA(cudaStreamSynchronize(c.stream));
+  for (size_t i = 0; i < h.size(); ++i) hist[i] = h[i];
+  *n_outer = (int)h.size();
+  if (n_solves) *n_solves = ns;
+  if (n_conv) *n_conv = nconv;
+}
+
+}  // namespace lcmg
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+#define API_BEGIN try {
+#define API_END                                                    \
+  }                                                                \
+  catch (const lcmg::ArgError& e) {                                \
+    lcmg::set_err(e.what());                                       \
+    return LCMG_ERR_INVALID_ARG;                                   \
+  }                                                                \
+  catch (const lcmg::MemError& e) {                                \
+    lcmg::set_err(e.what());                                       \
+    return LCMG_ERR_NOMEM;                                         \
+  }                                                                \
+  catch (const lcmg::CudaError& e) {                               \
+    lcmg::set_err(e.what());                                       \
+    return LCMG_ERR_CUDA;                                          \
+  }                                                                \
+  catch (const std::exception& e) {                                \
+    lcmg::set_err(e.what());                                       \
+    return LCMG_ERR_STATE;                                         \
+  }                                                                \
+  lcmg::g_err.clear();                                             \
+  return LCMG_OK;
+
+#define NEED_CTX() \
+  if (!ctx) throw lcmg::ArgError("null context")
+
+extern "C" {
+
+void lcmg_default_params(lcmg_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->levels = 0;
+  p->coarse_max = 16;
+  p->nu = 2;
+  p->smoother = LCMG_SMOOTH_L1_JACOBI;
+  p->omega = 2.0 / 3.0;
+  p->q = 2.0;
+  p->d_min = 1e-3;
+  p->tol = 1e-6;
+  p->maxit = 10000;
+  p->precision = LCMG_PREC_FP64;
+  p->mode = LCMG_MODE_BATCHED;
+  p->check_every = 16;
+  p->graphs = 1;
+}
+
+const char* lcmg_last_error(void) { return lcmg::g_err.c_str(); }
+const char* lcmg_version(void) { return "lcmg 0.1 (sm_103a)"; }
+
+int lcmg_create(lcmg_ctx** out, int device, void* stream, const lcmg_params* p) {
+  API_BEGIN
+  if (!out) throw lcmg::ArgError("null output pointer");
+  *out = nullptr;
+  int ndev = 0;
+  LCMG_CUDA(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) throw lcmg::ArgError("invalid device");
+  LCMG_CUDA(cudaSetDevice(device));
+  lcmg_params prm;
+  lcmg_default_params(&prm);
+  if (p) prm = *p;
+  lcmg::check_params(prm);
+  auto* c = new lcmg_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  if (!c->stream) {  // a blocking stream of our own: ordered with the legacy stream, capturable
+    LCMG_CUDA(cudaStreamCreate(&c->stream));
+    c->own_stream = true;
+  }
+  c->prm = prm;
+  cudaDeviceProp prop;
+  LCMG_CUDA(cudaGetDeviceProperties(&prop, device));
+  c->sms = prop.multiProcessorCount;
+  c->maxblk = std::min(lcmg::kMaxBlocks, c->sms * 8);
+  *out = c;
+  API_END
+}
+
+int lcmg_destroy(lcmg_ctx* ctx) {
+  API_BEGIN
+  if (!ctx) return LCMG_OK;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  API_END
+}
+
+int lcmg_set_params(lcmg_ctx* ctx, const lcmg_params* p) {
+  API_BEGIN
+  NEED_CTX();
+  if (!p) throw lcmg::ArgError("null params");
+  lcmg::check_params(*p);
+  const bool lev_change = p->levels != ctx->prm.levels || p->coarse_max != ctx->prm.coarse_max;
+  ctx->prm = *p;
+  if (lev_change) ctx->hier_ok = false;
+  API_END
+}
+
+int lcmg_set_grid(lcmg_ctx* ctx, int32_t n_v, int32_t n_h) {
+  API_BEGIN
+  NEED_CTX();
+  if (n_v < 2 || n_h < 2) throw lcmg::ArgError("grid sides must be >= 2");
+  LCMG_CUDA(cudaSetDevice(ctx->device));
+  ctx->nv = n_v;
+  ctx->nh = n_h;
+  ctx->n = (int64_t)n_v * n_h;
+  ctx->ne = (int64_t)n_h * (n_v - 1) + (int64_t)(n_h - 1) * n_v;
+  ctx->fwd = 0;
+  std::vector<double> ones(ctx->ne, 1.0);
+  LCMG_CUDA(cudaMemcpy(ctx->d.need(ctx->ne), ones.data(), sizeof(double) * ctx->ne, cudaMemcpyHostToDevice));
+  lcmg::refresh_fine(*ctx);
+  LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  API_END
+}
+
+int lcmg_set_forward_csr(lcmg_ctx* ctx, int64_t m, int64_t n, const int64_t* row_ptr, const int32_t* col,
+                         const void* val, int32_t val_dtype) {
+  API_BEGIN
+  NEED_CTX();
+  if (ctx->nv == 0) throw lcmg::ArgError("set_grid has not been called");
+  if (n != ctx->n) throw lcmg::ArgError("n must equal n_v * n_h");
+  if (m < 1 || !row_ptr || !col || !val) throw lcmg::ArgError("bad CSR arguments");
+  if (val_dtype != 0 && val_dtype != 1) throw lcmg::ArgError("val_dtype must be 0 (FP32) or 1 (FP64)");
+  if (row_ptr[0] != 0) throw lcmg::ArgError("row_ptr[0] must be 0");
+  for (int64_t i = 0; i < m; ++i)
+    if (row_ptr[i + 1] < row_ptr[i]) throw lcmg::ArgError("row_ptr must be non-decreasing");
+  const int64_t nnz = row_ptr[m];
+  std::vector<int64_t> cnt(n + 1, 0);
+  for (int64_t k = 0; k < nnz; ++k) {
+    if (col[k] < 0 || col[k] >= n) throw lcmg::ArgError("column index out of range");
+    cnt[col[k] + 1]++;
+  }
+  LCMG_CUDA(cudaSetDevice(ctx->device));
+  // transposed CSR by a stable counting sort on the column index
+  for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int64_t> rpT(cnt.begin(), cnt.end());
+  std::vector<int32_t> ciT(nnz);
+  std::vector<double> vT(nnz);
+  std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+  const float* vf = static_cast<const float*>(val);
+  const double* vd = static_cast<const double*>(val);
+  for (int64_t r = 0; r < m; ++r)
+    for (int64_t k = row_ptr[r]; k < row_ptr[r + 1]; ++k) {
+      const int64_t dst = pos[col[k]]++;
+      ciT[dst] = (int32_t)r;
+      vT[dst] = val_dtype == 0 ? (double)vf[k] : vd[k];
+    }
+  ctx->m = m;
+  ctx->nnz = nnz;
+  ctx->vdtype = val_dtype;
+  cudaStream_t s = ctx->stream;
+  LCMG_CUDA(cudaMemcpy(ctx->rp.need(m + 1), row_ptr, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice));
+  LCMG_CUDA(cudaMemcpy(ctx->ci.need(nnz), col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
+  LCMG_CUDA(cudaMemcpy(ctx->rpT.need(n + 1), rpT.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
+  LCMG_CUDA(cudaMemcpy(ctx->ciT.need(nnz), ciT.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
+  std::vector<float> tmpf(nnz);
+  if (val_dtype == 0) {
+    LCMG_CUDA(cudaMemcpy(ctx->v32.need(nnz), vf, sizeof(float) * nnz, cudaMemcpyHostToDevice));
+  } else {
+    LCMG_CUDA(cudaMemcpy(ctx->v64.need(nnz), vd, sizeof(double) * nnz, cudaMemcpyHostToDevice));
+    LCMG_CUDA(cudaMemcpy(ctx->vT64.need(nnz), vT.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
+    for (int64_t k = 0; k < nnz; ++k) tmpf[k] = (float)vd[k];
+    LCMG_CUDA(cudaMemcpy(ctx->v32.need(nnz), tmpf.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice));
+  }
+  for (int64_t k = 0; k < nnz; ++k) tmpf[k] = (float)vT[k];
+  LCMG_CUDA(cudaMemcpy(ctx->vT32.need(nnz), tmpf.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice));
+  // diag(A^T A): sums of squares along the rows of A^T
+  const int g = (int)std::min<int64_t>((n * 32 + lcmg::kBlock - 1) / lcmg::kBlock, ctx->maxblk);
+  if (val_dtype == 1)
+    lcmg::k_diag_ata<double><<<g, lcmg::kBlock, 0, s>>>(n, ctx->rpT.p, ctx->vT64.p, ctx->diag.need(n));
+  else
+    lcmg::k_diag_ata<float><<<g, lcmg::kBlock, 0, s>>>(n, ctx->rpT.p, ctx->vT32.p, ctx->diag.need(n));
+  LCMG_LAUNCHED();
+  lcmg::k_convert<double, float><<<g, lcmg::kBlock, 0, s>>>(n, ctx->diag.p, ctx->diag32.need(n));
+  LCMG_LAUNCHED();
+  LCMG_CUDA(cudaStreamSynchronize(s));
+  ctx->fwd = 1;
+  ctx->hier_ok = false;
+  API_END
+}
+
+int lcmg_set_forward_stencil(lcmg_ctx* ctx, int32_t kh, int32_t kw, const double* psf) {
+  API_BEGIN
+  NEED_CTX();
+  if (ctx->nv == 0) throw lcmg::ArgError("set_grid has not been called");
+  if (kh < 1 || kw < 1 || kh % 2 == 0 || kw % 2 == 0 || !psf) throw lcmg::ArgError("PSF sides must be odd");
+  if (kh > 2 * ctx->nv + 1 || kw > 2 * ctx->nh + 1) throw lcmg::ArgError("PSF larger than the image");
+  for (int i = 0; i < kh * kw; ++i)
+    if (!std::isfinite(psf[i])) throw lcmg::ArgError("PSF values must be finite");
+  LCMG_CUDA(cudaSetDevice(ctx->device));
+  ctx->rv = kh / 2;
+  ctx->rh = kw / 2;
+  ctx->m = ctx->n;
+  LCMG_CUDA(cudaMemcpy(ctx->psf64.need(kh * kw), psf, sizeof(double) * kh * kw, cudaMemcpyHostToDevice));
+  std::vector<float> pf(psf, psf + kh * kw);
+  LCMG_CUDA(cudaMemcpy(ctx->psf32.need(kh * kw), pf.data(), sizeof(float) * kh * kw, cudaMemcpyHostToDevice));
+  lcmg::PsfArgs pa{};
+  pa.nv = ctx->nv; pa.nh = ctx->nh; pa.rv = ctx->rv; pa.rh = ctx->rh; pa.psf = ctx->psf64.p;
+  const int g = (int)std::min<int64_t>((ctx->n + lcmg::kBlock - 1) / lcmg::kBlock, ctx->maxblk);
+  lcmg::k_psf_diag<<<g, lcmg::kBlock, 0, ctx->stream>>>(pa, ctx->diag.need(ctx->n));
+  LCMG_LAUNCHED();
+  lcmg::k_convert<double, float><<<g, lcmg::kBlock, 0, ctx->stream>>>(ctx->n, ctx->diag.p, ctx->diag32.need(ctx->n));
+  LCMG_LAUNCHED();
+  LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  ctx->fwd = 2;
+  ctx->hier_ok = false;
+  API_END
+}
+
+static void set_weights_common(lcmg_ctx* ctx, const double* d, int64_t n_edges, bool dev) {
+  if (ctx->nv == 0) throw lcmg::ArgError("set_grid has not been called");
+  if (n_edges != ctx->ne) throw lcmg::ArgError("n_edges must equal n_h (n_v - 1) + (n_h - 1) n_v");
+  if (!d) throw lcmg::ArgError("null weights");
+  LCMG_CUDA(cudaSetDevice(ctx->device));
+  if (!dev) {
+    for (int64_t e = 0; e < n_edges; ++e)
+      if (!(d[e] > 0.0) || !std::isfinite(d[e])) throw lcmg::ArgError("weights must be positive and finite");
+    LCMG_CUDA(cudaMemcpy(ctx->d.need(n_edges), d, sizeof(double) * n_edges, cudaMemcpyHostToDevice));
+  } else {
+    LCMG_CUDA(cudaMemcpyAsync(ctx->d.need(n_edges), d, sizeof(double) * n_edges, cudaMemcpyDeviceToDevice,
+                              ctx->stream));
+  }
+  lcmg::refresh_fine(*ctx);
+  if (ctx->fwd) lcmg::build_hierarchy(*ctx);
+  LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
+}
+
+int lcmg_set_weights(lcmg_ctx* ctx, const double* d, int64_t n_edges) {
+  API_BEGIN
+  NEED_CTX();
+  set_weights_common(ctx, d, n_edges, false);
+  API_END
+}
+
+int lcmg_set_weights_dev(lcmg_ctx* ctx, const double* d_dev, int64_t n_edges) {
+  API_BEGIN
+  NEED_CTX();
+  set_weights_common(ctx, d_dev, n_edges, true);
+  API_END
+}
+
+int lcmg_get_weights(lcmg_ctx* ctx, double* d_out, int64_t n_edges) {
+  API_BEGIN
+  NEED_CTX();
+  if (n_edges != ctx->ne || !d_out) throw lcmg::ArgError("bad output buffer");
+  LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  LCMG_CUDA(cudaMemcpy(d_out, ctx->d.p, sizeof(double) * n_edges, cudaMemcpyDeviceToHost));
+  API_END
+}
+
+int lcmg_solve_dev(lcmg_ctx* ctx, int32_t n_lambda, const double* lambda, int32_t n_rhs, const double* b_dev,
+                   const double* x0_dev, double* x_dev, double* resid_norm_dev, double* seminorm_dev,
+                   int32_t* iters_dev, int32_t* status_dev) {
+  API_BEGIN
+  NEED_CTX();
+  lcmg::StatsScope stats_scope(*ctx);
+  LCMG_CUDA(cudaSetDevice(ctx->device));
+  lcmg::require_ready(*ctx);
+  lcmg::check_lambdas(n_lambda, lambda);
+  if (n_rhs < 1 || !b_dev || !x_dev) throw lcmg::ArgError("bad right-hand sides or output");
+  lcmg::upload_b(*ctx, n_rhs, b_dev, true);
+  const int total = n_lambda * n_rhs;
+  std::vector<double> rho(total), eta(total);
+  std::vector<int> its(total), st(total);
+  const double* x0 = x0_dev;
+  lcmg::DevBuf<double> x0copy;
+  if (x0_dev && x0_dev == x_dev) {  // in-place warm start
+    x0copy.need((size_t)total * ctx->n);
+    LCMG_CUDA(cudaMemcpyAsync(x0copy.p, x0_dev, sizeof(double) * total * ctx->n, cudaMemcpyDeviceToDevice,
+                              ctx->stream));
+    x0 = x0copy.p;
+  }
+  lcmg::solve_all(*ctx, n_lambda, lambda, n_rhs, x0, x_dev, rho.data(), eta.data(), its.data(), st.data());
+  if (resid_norm_dev)
+    LCMG_CUDA(cudaMemcpyAsync(resid_norm_dev, rho.data(), sizeof(double) * total, cudaMemcpyHostToDevice, ctx->stream));
+  if (seminorm_dev)
+    LCMG_CUDA(cudaMemcpyAsync(seminorm_dev, eta.data(), sizeof(double) * total, cudaMemcpyHostToDevice, ctx->stream));
+  if (iters_dev)
+    LCMG_CUDA(cudaMemcpyAsync(iters_dev, its.data(), sizeof(int) * total, cudaMemcpyHostToDevice, ctx->stream));
+  if (status_dev)
+    LCMG_CUDA(cudaMemcpyAsync(status_dev, st.data(), sizeof(int) * total, cudaMemcpyHostToDevice, ctx->stream));
+  LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  API_END
+}
+
+int lcmg_solve(lcmg_ctx* ctx, int32_t n_lambda, const double* lambda, int32_t n_rhs, const double* b,
+               const double* x0, double* x, double* resid_norm, double* seminorm, int32_t* iters,
+               int32_t* status) {
+  API_BEGIN
+  NEED_CTX();
+  lcmg::StatsScope stats_scope(*ctx);
+  LCMG_CUDA(cudaSetDevice(ctx->device));
+  lcmg::require_ready(*ctx);
+  lcmg::check_lambdas(n_lambda, lambda);
+  if (n_rhs < 1 || !b || !x) throw lcmg::ArgError("bad right-hand sides or output");
+  const int total = n_lambda * n_rhs;
+  lcmg::upload_b(*ctx, n_rhs, b, false);
+  lcmg::DevBuf<double> xd, x0d;
+  xd.need((size_t)total * ctx->n);
+  if (x0) {
+    x0d.need((size_t)total * ctx->n);
+    LCMG_CUDA(cudaMemcpy(x0d.p, x0, sizeof(double) * total * ctx->n, cudaMemcpyHostToDevice));
+  }
+  lcmg::solve_all(*ctx, n_lambda, lambda, n_rhs, x0 ? x0d.p : nullptr, xd.p, resid_norm, seminorm, iters, status);
+  LCMG_CUDA(cudaMemcpyAsync(x, xd.p, sizeof(double) * total * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
+  LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  API_END
+}
+
+int lcmg_lcurve_corner(int32_t k, const double* rho, const double* eta, int32_t* idx) {
+  API_BEGIN
+  if (k < 3 || !rho || !eta || !idx) throw lcmg::ArgError("the corner needs at least three points");
+  for (int i = 0; i < k; ++i)
+    if (!(rho[i] > 0) || !(eta[i] > 0) || !std::isfinite(rho[i]) || !std::isfinite(eta[i]))
+      throw lcmg::ArgError("rho and eta must be positive and finite");
+  *idx = lcmg::corner_host(k, rho, eta);
+  API_END
+}
+
+int lcmg_cull_lambdas(int32_t m, int32_t i_prev, int32_t* lo, int32_t* hi) {
+  API_BEGIN
+  if (m < 1 || i_prev < 0 || i_prev > m || !lo || !hi) throw lcmg::ArgError("bad window arguments");
+  lcmg::window(m, i_prev, lo, hi);
+  API_END
+}
+
+int lcmg_update_weights_dev(lcmg_ctx* ctx, const double* x_star_dev, double q, double d_min) {
+  API_BEGIN
+  NEED_CTX();
+  if (ctx->nv == 0 || !x_star_dev) throw lcmg::ArgError("grid not set or null x");
+  LCMG_CUDA(cudaSetDevice(ctx->device));
+  lcmg::update_weights_dev(*ctx, x_star_dev, q, d_min);
+  if (ctx->fwd) lcmg::build_hierarchy(*ctx);
+  LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  API_END
+}
+
+int lcmg_update_weights(lcmg_ctx* ctx, const double* x_star, double q, double d_min, double* d_out) {
+  API_BEGIN
+  NEED_CTX();
+  if (ctx->nv == 0 || !x_star) throw lcmg::ArgError("grid not set or null x");
+  LCMG_CUDA(cudaSetDevice(ctx->device));
+  lcmg::DevBuf<double> xs;
+  xs.need(ctx->n);
+  LCMG_CUDA(cudaMemcpy(xs.p, x_star, sizeof(double) * ctx->n, cudaMemcpyHostToDevice));
+  lcmg::update_weights_dev(*ctx, xs.p, q, d_min);
+  if (ctx->fwd) lcmg::build_hierarchy(*ctx);
+  LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (d_out) LCMG_CUDA(cudaMemcpy(d_out, ctx->d.p, sizeof(double) * ctx->ne, cudaMemcpyDeviceToHost));
+  API_END
+}
+
+int lcmg_lcurve_run_dev(lcmg_ctx* ctx, int32_t m_lambda, const double* lambda, const double* b_dev,
+                        int32_t max_outer, double* x_out_dev, int32_t* lambda_idx_history, int32_t* n_outer,
+                        int64_t* n_solves, int64_t* n_converged) {
+  API_BEGIN
+  NEED_CTX();
+  lcmg::StatsScope stats_scope(*ctx);
+  LCMG_CUDA(cudaSetDevice(ctx->device));
+  if (!b_dev || !x_out_dev || !lambda_idx_history || !n_outer) throw lcmg::ArgError("null argument");
+  lcmg::require_ready(*ctx);
+  // Algorithm 2 starts from D = I
+  std::vector<double> ones(ctx->ne, 1.0);
+  LCMG_CUDA(cudaMemcpy(ctx->d.need(ctx->ne), ones.data(), sizeof(double) * ctx->ne, cudaMemcpyHostToDevice));
+  lcmg::refresh_fine(*ctx);
+  lcmg::build_hierarchy(*ctx);
+  lcmg::upload_b(*ctx, 1, b_dev, true);
+  lcmg::lcurve_run_impl(*ctx, m_lambda, lambda, max_outer, x_out_dev, lambda_idx_history, n_outer, n_solves,
+                        n_converged);
+  API_END
+}
+
+int lcmg_lcurve_run(lcmg_ctx* ctx, int32_t m_lambda, const double* lambda, const double* b, int32_t max_outer,
+                    double* x_out, int32_t* lambda_idx_history, int32_t* n_outer, int64_t* n_solves,
+                    int64_t* n_converged) {
+  API_BEGIN
+  NEED_CTX();
+  lcmg::StatsScope stats_scope(*ctx);
+  LCMG_CUDA(cudaSetDevice(ctx->device));
+  if (!b || !x_out || !lambda_idx_history || !n_outer) throw lcmg::ArgError("null argument");
+  lcmg::require_ready(*ctx);
+  lcmg::DevBuf<double> bd, xd;
+  bd.need(ctx->m);
+  xd.need(ctx->n);
+  LCMG_CUDA(cudaMemcpy(bd.p, b, sizeof(double) * ctx->m, cudaMemcpyHostToDevice));
+  std::vector<double> ones(ctx->ne, 1.0);
+  LCMG_CUDA(cudaMemcpy(ctx->d.need(ctx->ne), ones.data(), sizeof(double) * ctx->ne, cudaMemcpyHostToDevice));
+  lcmg::refresh_fine(*ctx);
+  lcmg::build_hierarchy(*ctx);
+  lcmg::upload_b(*ctx, 1, bd.p, true);
+  lcmg::lcurve_run_impl(*ctx, m_lambda, lambda, max_outer, xd.p, lambda_idx_history, n_outer, n_solves,
+                        n_converged);
+  LCMG_CUDA(cudaMemcpy(x_out, xd.p, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost));
+  API_END
+}
+
+int lcmg_get_stats(lcmg_ctx* ctx, lcmg_stats* out) {
+  API_BEGIN
+  NEED_CTX();
+  if (!out) throw lcmg::ArgError("null output");
+  *out = ctx->stats;
+  API_END
+}
+
+int lcmg_apply_normal_dev(lcmg_ctx* ctx, int32_t n_cols, const double* lambda, const double* x_dev,
+                          double* y_dev) {
+  API_BEGIN
+  NEED_CTX();
+  LCMG_CUDA(cudaSetDevice(ctx->device));
+  lcmg::require_ready(*ctx);
+  if (n_cols < 1 || n_cols > lcmg::kMaxB || !lambda || !x_dev || !y_dev) throw lcmg::ArgError("bad arguments");
+  const int B = n_cols;
+  lcmg::ensure_work(*ctx, B);
+  std::vector<double> l2(B);
+  for (int j = 0; j < B; ++j) l2[j] = lambda[j] * lambda[j];
+  LCMG_CUDA(cudaMemcpy(ctx->lam2.p, l2.data(), sizeof(double) * B, cudaMemcpyHostToDevice));
+  const int g = lcmg::grid_for(ctx->n, B, ctx->maxblk);
+  lcmg::k_planar_to_inter<<<g, lcmg::kBlock, 0, ctx->stream>>>(ctx->n, B, x_dev, ctx->x64.p);
+  LCMG_LAUNCHED();
+  LCMG_CUDA(cudaMemsetAsync(ctx->c64.p, 0, sizeof(double) * ctx->n * B, ctx->stream));
+  lcmg::Batch<double> b(*ctx, B);
+  b.true_residual(ctx->part_x.p);  // r64 = 0 - K x
+  const int ge = (int)std::min<int64_t>(((int64_t)ctx->n * B + lcmg::kBlock - 1) / lcmg::kBlock, ctx->maxblk);
+  lcmg::k_negate<<<ge, lcmg::kBlock, 0, ctx->stream>>>((int64_t)ctx->n * B, ctx->r64.p);
+  LCMG_LAUNCHED();
+  lcmg::k_inter_to_planar<<<g, lcmg::kBlock, 0, ctx->stream>>>(ctx->n, B, ctx->r64.p, y_dev);
+  LCMG_LAUNCHED();
+  LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  API_END
+}
+
+int lcmg_apply_vcycle_dev(lcmg_ctx* ctx, int32_t n_cols, const double* lambda, const double* r_dev,
+                          double* z_dev) {
+  API_BEGIN
+  NEED_CTX();
+  LCMG_CUDA(cudaSetDevice(ctx->device));
+  lcmg::require_ready(*ctx);
+  if (n_cols < 1 || n_cols > lcmg::kMaxB || !lambda || !r_dev || !z_dev) throw lcmg::ArgError("bad arguments");
+  const int B = n_cols;
+  lcmg::ensure_work(*ctx, B);
+  std::vector<double> lam(lambda, lambda + B);
+  const int g = lcmg::grid_for(ctx->n, B, ctx->maxblk);
+  if (ctx->prm.precision == LCMG_PREC_FP64) {
+    lcmg::Batch<double> b(*ctx, B);
+    b.setup(lam);
+    lcmg::k_planar_to_inter<<<g, lcmg::kBlock, 0, ctx->stream>>>(ctx->n, B, r_dev, reinterpret_cast<double*>(ctx->r.p));
+    LCMG_LAUNCHED();
+    b.vcycle(reinterpret_cast<double*>(ctx->r.p), reinterpret_cast<double*>(ctx->z.p), ctx->part_x.p);
+    lcmg::k_inter_to_planar<<<g, lcmg::kBlock, 0, ctx->stream>>>(ctx->n, B, reinterpret_cast<double*>(ctx->z.p), z_dev);
+    LCMG_LAUNCHED();
+  } else {
+    lcmg::Batch<float> b(*ctx, B);
+    b.setup(lam);
+    lcmg::k_planar_to_inter<<<g, lcmg::kBlock, 0, ctx->stream>>>(ctx->n, B, r_dev, ctx->r64.p);
+    LCMG_LAUNCHED();
+    lcmg::k_convert<double, float><<<g, lcmg::kBlock, 0, ctx->stream>>>((int64_t)ctx->n * B, ctx->r64.p,
+                                                                         reinterpret_cast<float*>(ctx->r.p));
+    LCMG_LAUNCHED();
+    b.vcycle(reinterpret_cast<float*>(ctx->r.p), reinterpret_cast<float*>(ctx->z.p), ctx->part_x.p);
+    lcmg::k_convert<float, double><<<g, lcmg::kBlock, 0, ctx->stream>>>((int64_t)ctx->n * B,
+                                                                         reinterpret_cast<float*>(ctx->z.p), ctx->r64.p);
+    LCMG_LAUNCHED();
+    lcmg::k_inter_to_planar<<<g, lcmg::kBlock, 0, ctx->stream>>>(ctx->n, B, ctx->r64.p, z_dev);
+    LCMG_LAUNCHED();
+  }
+  LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  API_END
+}
+
+int lcmg_get_level(lcmg_ctx* ctx, int32_t k, int32_t* n_v, int32_t* n_h, double* gl, double* ga) {
+  API_BEGIN
+  NEED_CTX();
+  lcmg::require_ready(*ctx);
+  if (k < 0 || k >= (int)ctx->lev.size()) throw lcmg::ArgError("level out of range");
+  const lcmg::Level& L = ctx->lev[k];
+  if (n_v) *n_v = L.nv;
+  if (n_h) *n_h = L.nh;
+  LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (k > 0) {
+    if (gl) LCMG_CUDA(cudaMemcpy(gl, L.gl.p, sizeof(double) * lcmg::kStencil * L.n, cudaMemcpyDeviceToHost));
+    if (ga) LCMG_CUDA(cudaMemcpy(ga, L.ga.p, sizeof(double) * lcmg::kStencil * L.n, cudaMemcpyDeviceToHost));
+  }
+  API_END
+}
+
+int lcmg_num_levels(lcmg_ctx* ctx, int32_t* levels) {
+  API_BEGIN
+  NEED_CTX();
+  lcmg::require_ready(*ctx);
+  if (!levels) throw lcmg::ArgError("null output");
+  *levels = (int)ctx->lev.size();
+  API_END
+}
+
+int lcmg_get_diag(lcmg_ctx* ctx, double* diag_out) {
+  API_BEGIN
+  NEED_CTX();
+  if (ctx->fwd == 0 || !diag_out) throw lcmg::ArgError("forward operator not set or null output");
+  LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  LCMG_CUDA(cudaMemcpy(diag_out, ctx->diag.p, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost));
+  API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// Launchers of the V-cycle level kernels, the coarsest-level dense setup,
+// the Galerkin products and the PCG vector updates.
+#include "launch.h"
+
+namespace lcmg {
+
+template <class T>
+void launch_dinv(const LevelView<T>& L, int B, const double* lam2, int smoother, double omega,
+                 T* dinv, int max_blocks, cudaStream_t s) {
+  const int g = grid_for(L.n, B, max_blocks);
+  if (L.fine)
+    k_dinv<FineOp<T>, T><<<g, kBlock, 0, s>>>(L.fine_op(), L.n, B, lam2, smoother, omega, dinv);
+  else
+    k_dinv<CoarseOp<T>, T><<<g, kBlock, 0, s>>>(L.coarse_op(), L.n, B, lam2, smoother, omega, dinv);
+  LCMG_LAUNCHED();
+}
+
+template <class T>
+void launch_smooth_zero(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const T* r,
+                        T* z, int two, int max_blocks, cudaStream_t s) {
+  const int g = grid_for(L.n, B, max_blocks);
+  if (L.fine)
+    k_smooth_zero<FineOp<T>, T><<<g, kBlock, 0, s>>>(L.fine_op(), L.n, B, lam2, dinv, r, z, two);
+  else
+    k_smooth_zero<CoarseOp<T>, T><<<g, kBlock, 0, s>>>(L.coarse_op(), L.n, B, lam2, dinv, r, z, two);
+  LCMG_LAUNCHED();
+}
+
+template <class T>
+int launch_smooth(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const T* r,
+                  const T* zin, T* zout, const int* active, double* part, int max_blocks,
+                  cudaStream_t s) {
+  const int g = grid_for(L.n, B, max_blocks);
+  if (L.fine)
+    k_smooth<FineOp<T>, T><<<g, kBlock, 0, s>>>(L.fine_op(), L.n, B, lam2, dinv, r, zin, zout, active, part);
+  else
+    k_smooth<CoarseOp<T>, T><<<g, kBlock, 0, s>>>(L.coarse_op(), L.n, B, lam2, dinv, r, zin, zout, active, part);
+  LCMG_LAUNCHED();
+  return g;
+}
+
+template <class T>
+void launch_residual(const LevelView<T>& L, int B, const T* lam2, const T* r, const T* z, T* res,
+                     int max_blocks, cudaStream_t s) {
+  const int g = grid_for(L.n, B, max_blocks);
+  if (L.fine)
+    k_residual<FineOp<T>, T><<<g, kBlock, 0, s>>>(L.fine_op(), L.n, B, lam2, r, z, res);
+  else
+    k_residual<CoarseOp<T>, T><<<g, kBlock, 0, s>>>(L.coarse_op(), L.n, B, lam2, r, z, res);
+  LCMG_LAUNCHED();
+}
+
+template <class T>
+void launch_restrict(int nvc, int nhc, int B, const T* rf, T* rc, int max_blocks, cudaStream_t s) {
+  const int g = grid_for((int64_t)nvc * nhc, B, max_blocks);
+  k_restrict<T><<<g, kBlock, 0, s>>>(nvc, nhc, B, rf, rc);
+  LCMG_LAUNCHED();
+}
+
+template <class T>
+void launch_prolong_add(int nvc, int nhc, int B, const T* ec, T* zf, int max_blocks, cudaStream_t s) {
+  const int g = grid_for((int64_t)4 * nvc * nhc, B, max_blocks);
+  k_prolong_add<T><<<g, kBlock, 0, s>>>(nvc, nhc, B, ec, zf);
+  LCMG_LAUNCHED();
+}
+
+template <class T>
+void launch_coarse_solve(int nc, int B, const double* kinv, const T* rc, T* ec, cudaStream_t s) {
+  const size_t smem = sizeof(double) * (size_t)nc;
+  dim3 grid((unsigned)((nc + kBlock / 32 - 1) / (kBlock / 32)), (unsigned)B);
+  k_coarse_solve<T><<<grid, kBlock, smem, s>>>(nc, B, kinv, rc, ec);
+  LCMG_LAUNCHED();
+}
+
+void launch_dense_setup(const LevelView<double>& L, int B, const double* lam2, double* M, double* W,
+                        double* K, int* info, int max_blocks, cudaStream_t s) {
+  const int64_t nc = L.n;
+  LCMG_CUDA(cudaMemsetAsync(M, 0, sizeof(double) * (size_t)B * nc * nc, s));
+  const int g = grid_for(nc, B, max_blocks);
+  if (L.fine)
+    k_dense_assemble<FineOp<double>><<<g, kBlock, 0, s>>>(L.fine_op(), nc, B, lam2, M);
+  else
+    k_dense_assemble<CoarseOp<double>><<<g, kBlock, 0, s>>>(L.coarse_op(), nc, B, lam2, M);
+  LCMG_LAUNCHED();
+  k_cholesky_inverse<<<B, kBlock, 0, s>>>((int)nc, M, W, K, info);
+  LCMG_LAUNCHED();
+}
+
+void launch_galerkin(const RapIn& in, int nvc, int nhc, double* out, int max_blocks, cudaStream_t s) {
+  const int64_t work = (int64_t)nvc * nhc * kStencil;
+  int64_t g = (work + kBlock - 1) / kBlock;
+  if (g > max_blocks) g = max_blocks;
+  k_galerkin<<<(unsigned)g, kBlock, 0, s>>>(in, nvc, nhc, out);
+  LCMG_LAUNCHED();
+}
+
+template <class T, class TX>
+int launch_update_xr(int64_t n, int B, const ColState& st, const T* p, const T* q, TX* x, T* r,
+                     double* part, int max_blocks, cudaStream_t s) {
+  const int g = grid_for(n, B, max_blocks);
+  k_update_xr<T, TX><<<g, kBlock, 0, s>>>(n, B, st, p, q, x, r, part);
+  LCMG_LAUNCHED();
+  return g;
+}
+
+template <class T>
+void launch_update_p(int64_t n, int B, const ColState& st, const T* z, T* p, int max_blocks,
+                     cudaStream_t s) {
+  const int g = grid_for(n, B, max_blocks);
+  k_update_p<T><<<g, kBlock, 0, s>>>(n, B, st, z, p);
+  LCMG_LAUNCHED();
+}
+
+template <class T>
+void launch_copy_cols(int64_t n, int B, const int* flag, const T* src, T* dst, int max_blocks,
+                      cudaStream_t s) {
+  const int g = grid_for(n, B, max_blocks);
+  k_copy_cols<T><<<g, kBlock, 0, s>>>(n, B, flag, src, dst);
+  LCMG_LAUNCHED();
+}
+
+#define LCMG_INST_T(T)                                                                          \
+  template void launch_dinv<T>(const LevelView<T>&, int, const double*, int, double, T*, int,   \
+                               cudaStream_t);                                                   \
+  template void launch_smooth_zero<T>(const LevelView<T>&, int, const T*, const T*, const T*,   \
+                                      T*, int, int, cudaStream_t);                              \
+  template int launch_smooth<T>(const LevelView<T>&, int, const T*, const T*, const T*,         \
+                                const T*, T*, const int*, double*, int, cudaStream_t);          \
+  template void launch_residual<T>(const LevelView<T>&, int, const T*, const T*, const T*, T*,  \
+                                   int, cudaStream_t);                                          \
+  template void launch_restrict<T>(int, int, int, const T*, T*, int, cudaStream_t);             \
+  template void launch_prolong_add<T>(int, int, int, const T*, T*, int, cudaStream_t);          \
+  template void launch_coarse_solve<T>(int, int, const double*, const T*, T*, cudaStream_t);    \
+  template void launch_update_p<T>(int64_t, int, const ColState&, const T*, T*, int,            \
+                                   cudaStream_t);                                               \
+  template void launch_copy_cols<T>(int64_t, int, const int*, const T*, T*, int, cudaStream_t);
+LCMG_INST_T(float)
+LCMG_INST_T(double)
+#undef LCMG_INST_T
+template int launch_update_xr<double, double>(int64_t, int, const ColState&, const double*,
+                                              const double*, double*, double*, double*, int,
+                                              cudaStream_t);
+template int launch_update_xr<float, float>(int64_t, int, const ColState&, const float*,
+                                            const float*, float*, float*, double*, int,
+                                            cudaStream_t);
+
+}  // namespace lcmg

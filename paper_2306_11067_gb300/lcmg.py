@@ -1,0 +1,356 @@
+"""ctypes binding of liblcmg.so (declared in include/lcmg.h).
+
+Argument marshalling only: every function calls the C entry point of the
+same name; all arithmetic runs in the library's CUDA kernels.  Host arrays
+are numpy arrays; device buffers are torch CUDA tensors (passed by their
+data pointers).  A missing library raises at import of this module's
+``lib()``; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblcmg.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "lcmg.h")
+
+LCMG_OK, LCMG_ERR_INVALID_ARG, LCMG_ERR_NOMEM, LCMG_ERR_CUDA = 0, 1, 2, 3
+LCMG_ERR_NOT_READY, LCMG_ERR_CANCELLED, LCMG_ERR_STATE = 4, 5, 6
+CONVERGED, MAXIT, BREAKDOWN, NONFINITE = 0, 1, 2, 3
+SMOOTH_L1_JACOBI, SMOOTH_JACOBI = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+MODE_BATCHED, MODE_SEQUENTIAL = 0, 1
+
+
+class LcmgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lcmg status {status}: {msg}")
+        self.status = status
+
+
+class lcmg_params(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("coarse_max", C.c_int32), ("nu", C.c_int32),
+                ("smoother", C.c_int32), ("omega", C.c_double), ("q", C.c_double),
+                ("d_min", C.c_double), ("tol", C.c_double), ("maxit", C.c_int32),
+                ("precision", C.c_int32), ("mode", C.c_int32), ("check_every", C.c_int32),
+                ("graphs", C.c_int32)]
+
+
+class lcmg_stats(C.Structure):
+    _fields_ = [("column_iterations", C.c_int64), ("batch_iterations", C.c_int64),
+                ("kernel_launches", C.c_int64), ("iterate_ms", C.c_double)]
+
+
+_lib = None
+_P = C.c_void_p
+_I32 = C.c_int32
+_I64 = C.c_int64
+_D = C.c_double
+_PD = C.POINTER(C.c_double)
+_PI32 = C.POINTER(C.c_int32)
+_PI64 = C.POINTER(C.c_int64)
+
+_SIGS = {
+    "lcmg_default_params": (None, [C.POINTER(lcmg_params)]),
+    "lcmg_last_error": (C.c_char_p, []),
+    "lcmg_version": (C.c_char_p, []),
+    "lcmg_create": (C.c_int, [C.POINTER(_P), C.c_int, _P, C.POINTER(lcmg_params)]),
+    "lcmg_destroy": (C.c_int, [_P]),
+    "lcmg_set_params": (C.c_int, [_P, C.POINTER(lcmg_params)]),
+    "lcmg_set_grid": (C.c_int, [_P, _I32, _I32]),
+    "lcmg_set_forward_csr": (C.c_int, [_P, _I64, _I64, _P, _P, _P, _I32]),
+    "lcmg_set_forward_stencil": (C.c_int, [_P, _I32, _I32, _P]),
+    "lcmg_set_weights": (C.c_int, [_P, _P, _I64]),
+    "lcmg_set_weights_dev": (C.c_int, [_P, _P, _I64]),
+    "lcmg_get_weights": (C.c_int, [_P, _P, _I64]),
+    "lcmg_solve": (C.c_int, [_P, _I32, _P, _I32, _P, _P, _P, _P, _P, _P, _P]),
+    "lcmg_solve_dev": (C.c_int, [_P, _I32, _P, _I32, _P, _P, _P, _P, _P, _P, _P]),
+    "lcmg_lcurve_corner": (C.c_int, [_I32, _P, _P, _PI32]),
+    "lcmg_update_weights": (C.c_int, [_P, _P, _D, _D, _P]),
+    "lcmg_update_weights_dev": (C.c_int, [_P, _P, _D, _D]),
+    "lcmg_cull_lambdas": (C.c_int, [_I32, _I32, _PI32, _PI32]),
+    "lcmg_lcurve_run": (C.c_int, [_P, _I32, _P, _P, _I32, _P, _P, _PI32, _PI64, _PI64]),
+    "lcmg_lcurve_run_dev": (C.c_int, [_P, _I32, _P, _P, _I32, _P, _P, _PI32, _PI64, _PI64]),
+    "lcmg_get_stats": (C.c_int, [_P, C.POINTER(lcmg_stats)]),
+    "lcmg_apply_normal_dev": (C.c_int, [_P, _I32, _P, _P, _P]),
+    "lcmg_apply_vcycle_dev": (C.c_int, [_P, _I32, _P, _P, _P]),
+    "lcmg_get_level": (C.c_int, [_P, _I32, _PI32, _PI32, _P, _P]),
+    "lcmg_num_levels": (C.c_int, [_P, _PI32]),
+    "lcmg_get_diag": (C.c_int, [_P, _P]),
+}
+
+
+def lib() -> C.CDLL:
+    """Load liblcmg.so (fails loudly if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2306_11067_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/lcmg.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(lcmg_\w+)\s*\(", txt, re.M)))
+
+
+def _check(st: int):
+    if st != LCMG_OK:
+        raise LcmgError(st, lib().lcmg_last_error().decode())
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+def lcmg_default_params() -> lcmg_params:
+    p = lcmg_params()
+    lib().lcmg_default_params(C.byref(p))
+    return p
+
+
+def lcmg_version() -> str:
+    return lib().lcmg_version().decode()
+
+
+def lcmg_last_error() -> str:
+    return lib().lcmg_last_error().decode()
+
+
+def lcmg_create(device: int = 0, stream=None, params: lcmg_params | None = None):
+    h = _P()
+    s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().lcmg_create(C.byref(h), device, s, C.byref(params) if params is not None else None))
+    return h
+
+
+def lcmg_destroy(ctx):
+    _check(lib().lcmg_destroy(ctx))
+
+
+def lcmg_set_params(ctx, params: lcmg_params):
+    _check(lib().lcmg_set_params(ctx, C.byref(params)))
+
+
+def lcmg_set_grid(ctx, n_v: int, n_h: int):
+    _check(lib().lcmg_set_grid(ctx, n_v, n_h))
+
+
+def lcmg_set_forward_csr(ctx, m, n, row_ptr, col, val):
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    if val.dtype == np.float32:
+        va, dt = np.ascontiguousarray(val), 0
+    else:
+        va, dt = _f64(val), 1
+    _check(lib().lcmg_set_forward_csr(ctx, m, n, _ptr(rp), _ptr(ci), _ptr(va), dt))
+
+
+def lcmg_set_forward_stencil(ctx, psf):
+    p = _f64(psf)
+    _check(lib().lcmg_set_forward_stencil(ctx, p.shape[0], p.shape[1], _ptr(p)))
+
+
+def lcmg_set_weights(ctx, d):
+    d = _f64(d)
+    _check(lib().lcmg_set_weights(ctx, _ptr(d), d.size))
+
+
+def lcmg_set_weights_dev(ctx, d_dev, n_edges: int):
+    _check(lib().lcmg_set_weights_dev(ctx, _ptr(d_dev), n_edges))
+
+
+def lcmg_get_weights(ctx, n_edges: int):
+    out = np.empty(n_edges)
+    _check(lib().lcmg_get_weights(ctx, _ptr(out), n_edges))
+    return out
+
+
+def lcmg_solve(ctx, lambdas, b, x0=None):
+    """b: (n_rhs, m) or (m,); returns x (n_rhs, n_lambda, n), rho, eta, iters, status."""
+    lam = _f64(lambdas)
+    b2 = _f64(np.atleast_2d(b))
+    nr, nl = b2.shape[0], lam.size
+    n = _solve_n(ctx, x0, b2)
+    x = np.empty((nr, nl, n))
+    rho, eta = np.empty((nr, nl)), np.empty((nr, nl))
+    its, st = np.empty((nr, nl), np.int32), np.empty((nr, nl), np.int32)
+    x0a = None if x0 is None else _f64(x0)
+    _check(lib().lcmg_solve(ctx, nl, _ptr(lam), nr, _ptr(b2), _ptr(x0a), _ptr(x), _ptr(rho),
+                            _ptr(eta), _ptr(its), _ptr(st)))
+    return dict(x=x, rho=rho, eta=eta, iters=its, status=st)
+
+
+_N_CACHE: dict = {}
+
+
+def _solve_n(ctx, x0, b2):
+    key = ctx.value
+    if key in _N_CACHE:
+        return _N_CACHE[key]
+    raise LcmgError(LCMG_ERR_STATE, "grid size unknown to the binding: call lcmg_set_grid through it")
+
+
+def lcmg_solve_dev(ctx, lambdas, b_dev, x_dev, x0_dev=None, rho_dev=None, eta_dev=None,
+                   iters_dev=None, status_dev=None):
+    lam = _f64(lambdas)
+    nr = b_dev.shape[0] if b_dev.dim() == 2 else 1
+    _check(lib().lcmg_solve_dev(ctx, lam.size, _ptr(lam), nr, _ptr(b_dev), _ptr(x0_dev), _ptr(x_dev),
+                                _ptr(rho_dev), _ptr(eta_dev), _ptr(iters_dev), _ptr(status_dev)))
+
+
+def lcmg_lcurve_corner(rho, eta) -> int:
+    r, e = _f64(rho), _f64(eta)
+    idx = C.c_int32()
+    _check(lib().lcmg_lcurve_corner(r.size, _ptr(r), _ptr(e), C.byref(idx)))
+    return idx.value
+
+
+def lcmg_update_weights(ctx, x_star, q, d_min, n_edges: int):
+    xs = _f64(x_star)
+    d = np.empty(n_edges)
+    _check(lib().lcmg_update_weights(ctx, _ptr(xs), q, d_min, _ptr(d)))
+    return d
+
+
+def lcmg_update_weights_dev(ctx, x_star_dev, q, d_min):
+    _check(lib().lcmg_update_weights_dev(ctx, _ptr(x_star_dev), q, d_min))
+
+
+def lcmg_cull_lambdas(m: int, i_prev: int):
+    lo, hi = C.c_int32(), C.c_int32()
+    _check(lib().lcmg_cull_lambdas(m, i_prev, C.byref(lo), C.byref(hi)))
+    return lo.value, hi.value
+
+
+def lcmg_lcurve_run(ctx, lambdas, b, max_outer: int, n: int):
+    lam = _f64(lambdas)
+    bb = _f64(b)
+    x = np.empty(n)
+    hist = np.zeros(max_outer, np.int32)
+    no, ns, nc = C.c_int32(), C.c_int64(), C.c_int64()
+    _check(lib().lcmg_lcurve_run(ctx, lam.size, _ptr(lam), _ptr(bb), max_outer, _ptr(x), _ptr(hist),
+                                 C.byref(no), C.byref(ns), C.byref(nc)))
+    return dict(x=x, history=list(hist[:no.value]), n_solves=ns.value, n_converged=nc.value)
+
+
+def lcmg_lcurve_run_dev(ctx, lambdas, b_dev, max_outer: int, x_out_dev):
+    lam = _f64(lambdas)
+    hist = np.zeros(max_outer, np.int32)
+    no, ns, nc = C.c_int32(), C.c_int64(), C.c_int64()
+    _check(lib().lcmg_lcurve_run_dev(ctx, lam.size, _ptr(lam), _ptr(b_dev), max_outer, _ptr(x_out_dev),
+                                     _ptr(hist), C.byref(no), C.byref(ns), C.byref(nc)))
+    return dict(history=list(hist[:no.value]), n_solves=ns.value, n_converged=nc.value)
+
+
+def lcmg_get_stats(ctx) -> dict:
+    s = lcmg_stats()
+    _check(lib().lcmg_get_stats(ctx, C.byref(s)))
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def lcmg_apply_normal_dev(ctx, lambdas, x_dev, y_dev):
+    lam = _f64(lambdas)
+    _check(lib().lcmg_apply_normal_dev(ctx, lam.size, _ptr(lam), _ptr(x_dev), _ptr(y_dev)))
+
+
+def lcmg_apply_vcycle_dev(ctx, lambdas, r_dev, z_dev):
+    lam = _f64(lambdas)
+    _check(lib().lcmg_apply_vcycle_dev(ctx, lam.size, _ptr(lam), _ptr(r_dev), _ptr(z_dev)))
+
+
+def lcmg_num_levels(ctx) -> int:
+    v = C.c_int32()
+    _check(lib().lcmg_num_levels(ctx, C.byref(v)))
+    return v.value
+
+
+def lcmg_get_level(ctx, k: int):
+    nv, nh = C.c_int32(), C.c_int32()
+    _check(lib().lcmg_get_level(ctx, k, C.byref(nv), C.byref(nh), None, None))
+    n = nv.value * nh.value
+    gl, ga = np.empty((25, n)), np.empty((25, n))
+    if k > 0:
+        _check(lib().lcmg_get_level(ctx, k, None, None, _ptr(gl), _ptr(ga)))
+    return nv.value, nh.value, gl, ga
+
+
+def lcmg_get_diag(ctx, n: int):
+    out = np.empty(n)
+    _check(lib().lcmg_get_diag(ctx, _ptr(out)))
+    return out
+
+
+# ---------------------------------------------------------------------------
+class Solver:
+    """Convenience owner of one context (same calls, bound to it)."""
+
+    def __init__(self, n_v, n_h, device=0, stream=None, **params):
+        p = lcmg_default_params()
+        for k, v in params.items():
+            setattr(p, k, v)
+        self.params = p
+        self.ctx = lcmg_create(device, stream, p)
+        self.n_v, self.n_h = n_v, n_h
+        self.n = n_v * n_h
+        self.n_edges = n_h * (n_v - 1) + (n_h - 1) * n_v
+        lcmg_set_grid(self.ctx, n_v, n_h)
+        _N_CACHE[self.ctx.value] = self.n
+
+    def set_params(self, **params):
+        for k, v in params.items():
+            setattr(self.params, k, v)
+        lcmg_set_params(self.ctx, self.params)
+
+    def set_forward_csr(self, A):
+        lcmg_set_forward_csr(self.ctx, A.m, A.n, A.row_ptr, A.col, A.val)
+
+    def set_forward_stencil(self, psf):
+        lcmg_set_forward_stencil(self.ctx, psf)
+
+    def set_weights(self, d):
+        lcmg_set_weights(self.ctx, d)
+
+    def solve(self, lambdas, b, x0=None):
+        return lcmg_solve(self.ctx, lambdas, b, x0)
+
+    def update_weights(self, x_star, q=2.0, d_min=1e-3):
+        return lcmg_update_weights(self.ctx, x_star, q, d_min, self.n_edges)
+
+    def lcurve_run(self, lambdas, b, max_outer=15):
+        return lcmg_lcurve_run(self.ctx, lambdas, b, max_outer, self.n)
+
+    def stats(self):
+        return lcmg_get_stats(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            _N_CACHE.pop(self.ctx.value, None)
+            lcmg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
