@@ -82,7 +82,7 @@ typedef enum {
 typedef struct {
   int32_t levels;       /* multigrid levels incl. the finest; 0 = coarsen by 2 while
                            both sides are even and one exceeds coarse_max            */
-  int32_t coarse_max;   /* side limit of the coarsest grid for levels = 0 (default 16) */
+  int32_t coarse_max;   /* side limit of the coarsest grid for levels = 0 (default 8)  */
   int32_t nu;           /* pre- = post-smoothing sweeps (default 2; equal counts keep
                            the V-cycle symmetric so CG applies)                      */
   int32_t smoother;     /* lcmg_smoother (default l1-Jacobi)                         */
@@ -96,6 +96,8 @@ typedef struct {
   int32_t check_every;  /* device iterations between host convergence polls (16)     */
   int32_t graphs;       /* 1 = replay each block of check_every iterations as one CUDA
                            graph (default), 0 = launch kernels one by one            */
+  int32_t timing;       /* 1 = time the operator passes with CUDA events (see
+                           lcmg_stats); default 0                                     */
 } lcmg_params;
 
 typedef struct lcmg_ctx lcmg_ctx;
@@ -219,14 +221,23 @@ int lcmg_lcurve_run_dev(lcmg_ctx* ctx, int32_t m_lambda, const double* lambda,
                         int32_t* lambda_idx_history, int32_t* n_outer, int64_t* n_solves,
                         int64_t* n_converged);
 
-/* Statistics of the last solve: total PCG iterations over all systems, the
- * number of batched iterations issued, kernel launches issued, and the
- * milliseconds spent in the device iteration (CUDA events). */
+/* Statistics of the last top-level call (solve or lcurve_run): total PCG
+ * iterations over all systems, batched iterations issued, kernels launched,
+ * and the milliseconds spent in the device iteration (CUDA events).  With
+ * params.timing = 1 the two passes of every operator application
+ * q = K p inside the PCG iteration (A p, then A^T y + lam^2 L^T W L p) are
+ * bracketed by CUDA events on the context's stream: op_ms_a / op_ms_at
+ * are their summed durations, op_launches the number of timed passes and
+ * op_bytes their summed algorithmic (compulsory) DRAM bytes. */
 typedef struct {
   int64_t column_iterations;
   int64_t batch_iterations;
   int64_t kernel_launches;
   double iterate_ms;
+  double op_ms_a;
+  double op_ms_at;
+  int64_t op_launches;
+  int64_t op_bytes;
 } lcmg_stats;
 int lcmg_get_stats(lcmg_ctx* ctx, lcmg_stats* out);
 

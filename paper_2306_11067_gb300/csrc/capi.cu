@@ -60,7 +60,8 @@ struct Level {
   int nv = 0, nh = 0;
   int64_t n = 0;
   DevBuf<double> gl, ga;   // 25 x n (levels >= 1)
-  DevBuf<float> gl32, ga32;
+  DevBuf<double> cf64;     // per-point coefficient rows (smoother layout)
+  DevBuf<float> cf32;
 };
 
 struct LevelWork {
@@ -119,6 +120,12 @@ struct lcmg_ctx {
   int* h_counters = nullptr;  // pinned
   // weight-update scratch
   DevBuf<double> absv, bmax;
+  // events of the operator-pass timing (params.timing)
+  std::vector<cudaEvent_t> tev;
+  int tev_used = 0;
+  // staging for host-pointer calls and the outer loop (grow-only: no
+  // allocation in steady state)
+  DevBuf<double> stage_b, stage_x, stage_x0, run_xres, run_xstar, run_xwin;
   lcmg_stats stats{};
 };
 
@@ -191,10 +198,11 @@ static void build_hierarchy(lcmg_ctx& c) {
       in.g25 = f.gl.p; launch_galerkin(in, g.nv, g.nh, gl, c.maxblk, c.stream);
       in.g25 = f.ga.p; launch_galerkin(in, g.nv, g.nh, ga, c.maxblk, c.stream);
     }
-    const int gg = (int)std::min<int64_t>((kStencil * g.n + kBlock - 1) / kBlock, c.maxblk);
-    k_convert<double, float><<<gg, kBlock, 0, c.stream>>>(kStencil * g.n, gl, g.gl32.need(kStencil * g.n));
+    // smoother copies: per-point rows of both parts (FP64 and FP32)
+    const int gg = (int)std::min<int64_t>((kCoefStride * g.n + kBlock - 1) / kBlock, c.maxblk);
+    k_coef_pack<double><<<gg, kBlock, 0, c.stream>>>(g.n, gl, ga, g.cf64.need(kCoefStride * g.n));
     LCMG_LAUNCHED();
-    k_convert<double, float><<<gg, kBlock, 0, c.stream>>>(kStencil * g.n, ga, g.ga32.need(kStencil * g.n));
+    k_coef_pack<float><<<gg, kBlock, 0, c.stream>>>(g.n, gl, ga, g.cf32.need(kCoefStride * g.n));
     LCMG_LAUNCHED();
   }
   c.hier_ok = true;
@@ -212,7 +220,7 @@ LevelView<double> view<double>(const lcmg_ctx& c, int k) {
   const Level& l = c.lev[k];
   v.nv = l.nv; v.nh = l.nh; v.n = l.n;
   if (k == 0) { v.fine = true; v.ws = c.ws.p; v.we = c.we.p; v.ga = c.diag.p; }
-  else { v.fine = false; v.gl = l.gl.p; v.ga = l.ga.p; }
+  else { v.fine = false; v.cf = l.cf64.p; }
   return v;
 }
 template <>
@@ -221,7 +229,7 @@ LevelView<float> view<float>(const lcmg_ctx& c, int k) {
   const Level& l = c.lev[k];
   v.nv = l.nv; v.nh = l.nh; v.n = l.n;
   if (k == 0) { v.fine = true; v.ws = c.ws32.p; v.we = c.we32.p; v.ga = c.diag32.p; }
-  else { v.fine = false; v.gl = l.gl32.p; v.ga = l.ga32.p; }
+  else { v.fine = false; v.cf = l.cf32.p; }
   return v;
 }
 
@@ -267,6 +275,9 @@ static ColState colstate(lcmg_ctx& c) {
 // Batched solver for one precision T (double: FP64 path; float: mixed)
 // ---------------------------------------------------------------------------
 template <class T>
+static void op_bytes(const lcmg_ctx& c, int B, int64_t* first, int64_t* second);
+
+template <class T>
 struct Batch {
   lcmg_ctx& c;
   int B;
@@ -297,6 +308,37 @@ struct Batch {
 
   // q = K p (T precision) with partials of p.q; returns the partial count
   int apply_K(const T* P, T* Q, double* part);
+
+  // ---- live timing of the operator passes (params.timing) ------------
+  void mark() {
+    if (!c.prm.timing) return;
+    if (c.tev_used >= (int)c.tev.size()) {
+      cudaEvent_t e;
+      LCMG_CUDA(cudaEventCreate(&e));
+      c.tev.push_back(e);
+    }
+    // External: inside a stream capture this becomes an event-record node
+    // of the graph (a plain record would only express a dependency)
+    LCMG_CUDA(cudaEventRecordWithFlags(c.tev[c.tev_used++], s, cudaEventRecordExternal));
+  }
+  // after the stream has been synchronised: add the recorded pass times
+  void collect_timing() {
+    if (!c.prm.timing) return;
+    int64_t b0 = 0, b1 = 0;
+    op_bytes<T>(c, B, &b0, &b1);
+    for (int i = 0; i + 2 < c.tev_used; i += 3) {
+      float a = 0.f, b = 0.f;
+      if (cudaEventElapsedTime(&a, c.tev[i], c.tev[i + 1]) != cudaSuccess ||
+          cudaEventElapsedTime(&b, c.tev[i + 1], c.tev[i + 2]) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      c.stats.op_ms_a += a;
+      c.stats.op_ms_at += b;
+      c.stats.op_launches += 2;
+      c.stats.op_bytes += b0 + b1;
+    }
+  }
   // r64 = c64 - K x64 in FP64 with partials of r64.r64
   int true_residual(double* part);
 
@@ -387,7 +429,7 @@ struct Batch {
     T* R = tp(c.r);
     T* Z = tp(c.z);
     const int nb_pq = apply_K(P, Q, c.part_pq.p);
-    k_scalar_alpha<<<1, kScalarThreads, 0, s>>>(B, nb_pq, c.part_pq.p, st);
+    k_scalar_col_alpha<<<B, kColThreads, 0, s>>>(B, nb_pq, c.part_pq.p, st);
     LCMG_LAUNCHED();
     int nb_rr;
     if (std::is_same<T, double>::value)
@@ -396,7 +438,7 @@ struct Batch {
       nb_rr = launch_update_xr<T, T>(c.n, B, st, P, Q, reinterpret_cast<T*>(c.xlo.p), R, c.part_rr.p, c.maxblk, s);
     const int nb_rz = vcycle(R, Z, c.part_rz.p);
     const double trig = std::is_same<T, float>::value ? 0.01 : 0.0;  // ||r|| fell 10x since the last update
-    k_scalar_beta<<<1, kScalarThreads, 0, s>>>(B, nb_rr, c.part_rr.p, nb_rz, c.part_rz.p, st, c.prm.maxit, trig);
+    k_scalar_col_beta<<<B, kColThreads, 0, s>>>(B, nb_rr, c.part_rr.p, nb_rz, c.part_rz.p, st, c.prm.maxit, trig);
     LCMG_LAUNCHED();
     launch_update_p<T>(c.n, B, st, Z, P, c.maxblk, s);
   }
@@ -475,6 +517,7 @@ struct Batch {
     // one block of `every` iterations, captured once into a CUDA graph
     cudaGraphExec_t exec = nullptr;
     int64_t per_block = 0;  // kernels in one captured block
+    c.tev_used = 0;
     if (c.prm.graphs && active > 0) {
       cudaGraph_t graph = nullptr;
       const int64_t l0 = launch_counter();
@@ -504,10 +547,12 @@ struct Batch {
         LCMG_CUDA(cudaGraphLaunch(exec, s));
         launch_counter() += per_block;
       } else {
+        c.tev_used = 0;
         for (int i = 0; i < every; ++i) iterate_once();
       }
       batch_its += every;
       read_counters();
+      collect_timing();
       active = c.h_counters[0];
       const int pending = c.h_counters[1];
       const int votes = c.h_counters[2];
@@ -540,22 +585,40 @@ const T* Batch<T>::psfT() {
                                         : reinterpret_cast<const T*>(c.psf32.p);
 }
 
+// Algorithmic (compulsory) DRAM bytes of the two operator passes for a
+// batch of B columns in precision T: the operator data once, every input
+// vector read once and every output written once.
+template <class T>
+static void op_bytes(const lcmg_ctx& c, int B, int64_t* first, int64_t* second) {
+  const int64_t sT = sizeof(T), sB = B;
+  if (c.fwd == 1) {
+    const int64_t sV = (std::is_same<T, float>::value || c.vdtype == 0) ? 4 : 8;
+    const int64_t mat = c.nnz * (sV + 4);
+    *first = mat + (c.m + 1) * 8 + c.n * sB * sT + c.m * sB * sT;
+    *second = mat + (c.n + 1) * 8 + c.m * sB * sT + 2 * c.n * sB * sT + 2 * c.n * sT + c.n * sB * sT;
+  } else {
+    *first = 2 * c.n * sB * sT;
+    *second = 3 * c.n * sB * sT + 2 * c.n * sT;
+  }
+}
+
 template <class T>
 int Batch<T>::apply_K(const T* P, T* Q, double* part) {
   T* Y = tp(c.y);
+  mark();
+  int nb;
   if (c.fwd == 1) {
     SpmmArgs a = args(false, B);
     SpmmArgs at = args(true, B);
     if (std::is_same<T, float>::value) {
-      const float* va = c.vdtype == 0 ? c.v32.p : c.v32.p;
-      const float* vt = c.vdtype == 0 ? c.vT32.p : c.vT32.p;
-      launch_spmm<float, float, float, 0>(a, va, reinterpret_cast<const float*>(P), reinterpret_cast<float*>(Y),
+      launch_spmm<float, float, float, 0>(a, c.v32.p, reinterpret_cast<const float*>(P), reinterpret_cast<float*>(Y),
                                           view<float>(c, 0).fine_op(), nullptr, nullptr, nullptr, nullptr,
                                           nullptr, c.maxblk, s);
-      return launch_spmm<float, float, float, 1>(at, vt, reinterpret_cast<const float*>(Y),
-                                                 reinterpret_cast<float*>(Q), view<float>(c, 0).fine_op(),
-                                                 reinterpret_cast<const float*>(P), nullptr, c.lam2.p, nullptr,
-                                                 part, c.maxblk, s);
+      mark();
+      nb = launch_spmm<float, float, float, 1>(at, c.vT32.p, reinterpret_cast<const float*>(Y),
+                                               reinterpret_cast<float*>(Q), view<float>(c, 0).fine_op(),
+                                               reinterpret_cast<const float*>(P), nullptr, c.lam2.p, nullptr,
+                                               part, c.maxblk, s);
     } else {
       const double* Pd = reinterpret_cast<const double*>(P);
       double* Qd = reinterpret_cast<double*>(Q);
@@ -563,23 +626,29 @@ int Batch<T>::apply_K(const T* P, T* Q, double* part) {
       if (c.vdtype == 1) {
         launch_spmm<double, double, double, 0>(a, c.v64.p, Pd, Yd, fop64(), nullptr, nullptr, nullptr, nullptr,
                                                nullptr, c.maxblk, s);
-        return launch_spmm<double, double, double, 1>(at, c.vT64.p, Yd, Qd, fop64(), Pd, nullptr, c.lam2.p,
-                                                      nullptr, part, c.maxblk, s);
-      }
-      launch_spmm<float, double, double, 0>(a, c.v32.p, Pd, Yd, fop64(), nullptr, nullptr, nullptr, nullptr,
-                                            nullptr, c.maxblk, s);
-      return launch_spmm<float, double, double, 1>(at, c.vT32.p, Yd, Qd, fop64(), Pd, nullptr, c.lam2.p,
+        mark();
+        nb = launch_spmm<double, double, double, 1>(at, c.vT64.p, Yd, Qd, fop64(), Pd, nullptr, c.lam2.p,
+                                                    nullptr, part, c.maxblk, s);
+      } else {
+        launch_spmm<float, double, double, 0>(a, c.v32.p, Pd, Yd, fop64(), nullptr, nullptr, nullptr, nullptr,
+                                              nullptr, c.maxblk, s);
+        mark();
+        nb = launch_spmm<float, double, double, 1>(at, c.vT32.p, Yd, Qd, fop64(), Pd, nullptr, c.lam2.p,
                                                    nullptr, part, c.maxblk, s);
+      }
     }
+  } else {
+    // PSF operator
+    nb = grid_for(c.n, B, c.maxblk);
+    PsfArgs pa = psf();
+    k_psf_forward<T, 0><<<nb, kBlock, 0, s>>>(pa, psfT(), B, P, Y, nullptr, 1, 1, nullptr);
+    LCMG_LAUNCHED();
+    mark();
+    k_psf_normal<T, T, 1><<<nb, kBlock, 0, s>>>(pa, psfT(), B, Y, fop(), P, nullptr, c.lam2.p, Q, part);
+    LCMG_LAUNCHED();
   }
-  // PSF operator
-  const int g = grid_for(c.n, B, c.maxblk);
-  PsfArgs pa = psf();
-  k_psf_forward<T, 0><<<g, kBlock, 0, s>>>(pa, psfT(), B, P, Y, nullptr, 1, 1, nullptr);
-  LCMG_LAUNCHED();
-  k_psf_normal<T, T, 1><<<g, kBlock, 0, s>>>(pa, psfT(), B, Y, fop(), P, nullptr, c.lam2.p, Q, part);
-  LCMG_LAUNCHED();
-  return g;
+  mark();
+  return nb;
 }
 
 template <class T>
@@ -780,12 +849,11 @@ static void solve_all(lcmg_ctx& c, int nl, const double* lam, int nrhs, const do
 static void upload_b(lcmg_ctx& c, int nrhs, const double* b, bool dev) {
   // b planar [nrhs][m] -> interleaved [m][nrhs]
   double* bi = c.bvec.need((size_t)c.m * nrhs);
-  DevBuf<double> tmp;
   const double* src = b;
   if (!dev) {
-    tmp.need((size_t)c.m * nrhs);
-    LCMG_CUDA(cudaMemcpyAsync(tmp.p, b, sizeof(double) * c.m * nrhs, cudaMemcpyHostToDevice, c.stream));
-    src = tmp.p;
+    double* tmp = c.stage_b.need((size_t)c.m * nrhs);
+    LCMG_CUDA(cudaMemcpyAsync(tmp, b, sizeof(double) * c.m * nrhs, cudaMemcpyHostToDevice, c.stream));
+    src = tmp;
   }
   k_planar_to_inter<<<grid_for(c.m, nrhs, c.maxblk), kBlock, 0, c.stream>>>(c.m, nrhs, src, bi);
   LCMG_LAUNCHED();
@@ -848,7 +916,9 @@ static void lcurve_run_impl(lcmg_ctx& c, int m, const double* lam, int max_outer
   check_lambdas(m, lam);
   if (max_outer < 1) throw ArgError("max_outer must be >= 1");
   const int64_t n = c.n;
-  DevBuf<double> xres, xstar, xwin;
+  DevBuf<double>& xres = c.run_xres;
+  DevBuf<double>& xstar = c.run_xstar;
+  DevBuf<double>& xwin = c.run_xwin;
   xres.need((size_t)m * n);
   xstar.need(n);
   LCMG_CUDA(cudaMemsetAsync(xstar.p, 0, sizeof(double) * n, c.stream));
@@ -947,7 +1017,7 @@ void lcmg_default_params(lcmg_params* p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));
   p->levels = 0;
-  p->coarse_max = 16;
+  p->coarse_max = 8;
   p->nu = 2;
   p->smoother = LCMG_SMOOTH_L1_JACOBI;
   p->omega = 2.0 / 3.0;
@@ -959,6 +1029,7 @@ void lcmg_default_params(lcmg_params* p) {
   p->mode = LCMG_MODE_BATCHED;
   p->check_every = 16;
   p->graphs = 1;
+  p->timing = 0;
 }
 
 const char* lcmg_last_error(void) { return lcmg::g_err.c_str(); }
@@ -998,6 +1069,7 @@ int lcmg_destroy(lcmg_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+  for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   API_END
@@ -1181,7 +1253,7 @@ int lcmg_solve_dev(lcmg_ctx* ctx, int32_t n_lambda, const double* lambda, int32_
   std::vector<double> rho(total), eta(total);
   std::vector<int> its(total), st(total);
   const double* x0 = x0_dev;
-  lcmg::DevBuf<double> x0copy;
+  lcmg::DevBuf<double>& x0copy = ctx->stage_x0;
   if (x0_dev && x0_dev == x_dev) {  // in-place warm start
     x0copy.need((size_t)total * ctx->n);
     LCMG_CUDA(cudaMemcpyAsync(x0copy.p, x0_dev, sizeof(double) * total * ctx->n, cudaMemcpyDeviceToDevice,
@@ -1213,7 +1285,8 @@ int lcmg_solve(lcmg_ctx* ctx, int32_t n_lambda, const double* lambda, int32_t n_
   if (n_rhs < 1 || !b || !x) throw lcmg::ArgError("bad right-hand sides or output");
   const int total = n_lambda * n_rhs;
   lcmg::upload_b(*ctx, n_rhs, b, false);
-  lcmg::DevBuf<double> xd, x0d;
+  lcmg::DevBuf<double>& xd = ctx->stage_x;
+  lcmg::DevBuf<double>& x0d = ctx->stage_x0;
   xd.need((size_t)total * ctx->n);
   if (x0) {
     x0d.need((size_t)total * ctx->n);
@@ -1258,7 +1331,7 @@ int lcmg_update_weights(lcmg_ctx* ctx, const double* x_star, double q, double d_
   NEED_CTX();
   if (ctx->nv == 0 || !x_star) throw lcmg::ArgError("grid not set or null x");
   LCMG_CUDA(cudaSetDevice(ctx->device));
-  lcmg::DevBuf<double> xs;
+  lcmg::DevBuf<double>& xs = ctx->stage_x;
   xs.need(ctx->n);
   LCMG_CUDA(cudaMemcpy(xs.p, x_star, sizeof(double) * ctx->n, cudaMemcpyHostToDevice));
   lcmg::update_weights_dev(*ctx, xs.p, q, d_min);
@@ -1297,7 +1370,8 @@ int lcmg_lcurve_run(lcmg_ctx* ctx, int32_t m_lambda, const double* lambda, const
   LCMG_CUDA(cudaSetDevice(ctx->device));
   if (!b || !x_out || !lambda_idx_history || !n_outer) throw lcmg::ArgError("null argument");
   lcmg::require_ready(*ctx);
-  lcmg::DevBuf<double> bd, xd;
+  lcmg::DevBuf<double>& bd = ctx->stage_b;
+  lcmg::DevBuf<double>& xd = ctx->stage_x;
   bd.need(ctx->m);
   xd.need(ctx->n);
   LCMG_CUDA(cudaMemcpy(bd.p, b, sizeof(double) * ctx->m, cudaMemcpyHostToDevice));

@@ -79,18 +79,65 @@ struct FineOp {
   }
 };
 
-// Coarse level: 25 coefficient arrays per part, coefficient of neighbour
-// (i+di, j+dj) of point p at gl[((di+2) + 5 (dj+2)) * n + p].
+// Coarse level: per point a row of kCoefStride values, the 25 coefficients
+// of lam^2-part G_L at [0, 25) and of G_A at [32, 57); the coefficient of
+// neighbour (i+di, j+dj) has offset o = (di+2) + 5 (dj+2).  Coefficients of
+// neighbours outside the grid are zero.
+constexpr int kCoefStride = 64;
+
+template <class T>
+struct CoefVec;
+template <>
+struct CoefVec<float> {
+  using V = float4;
+  static constexpr int W = 4;
+};
+template <>
+struct CoefVec<double> {
+  using V = double2;
+  static constexpr int W = 2;
+};
+
+template <class T>
+__device__ __forceinline__ void vstore(T* dst, const typename CoefVec<T>::V& v);
+template <>
+__device__ __forceinline__ void vstore<float>(float* d, const float4& v) { d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w; }
+template <>
+__device__ __forceinline__ void vstore<double>(double* d, const double2& v) { d[0] = v.x; d[1] = v.y; }
+
 template <class T>
 struct CoarseOp {
   int nv, nh;
   int64_t n;
-  const T* __restrict__ gl;
-  const T* __restrict__ ga;
+  const T* __restrict__ cf;  // [n][kCoefStride]
+
+  // k[o] = lam2 G_L[o] + G_A[o] for point p (vector loads)
+  __device__ __forceinline__ void coefs(int64_t p, T lam2, T (&k)[28]) const {
+    using VT = typename CoefVec<T>::V;
+    constexpr int W = CoefVec<T>::W;
+    const VT* row = reinterpret_cast<const VT*>(cf + p * kCoefStride);
+    T gl[28], ga[28];
+#pragma unroll
+    for (int q = 0; q < 28 / W; ++q) {
+      vstore<T>(gl + q * W, row[q]);
+      vstore<T>(ga + q * W, row[32 / W + q]);
+    }
+#pragma unroll
+    for (int o = 0; o < 28; ++o) k[o] = lam2 * gl[o] + ga[o];
+  }
 
   template <class F>
   __device__ __forceinline__ T apply(int64_t p, int i, int j, T lam2, F v) const {
+    T k[28];
+    coefs(p, lam2, k);
     T acc = 0;
+    if (i >= 2 && i + 2 < nv && j >= 2 && j + 2 < nh) {
+#pragma unroll
+      for (int dj = -2; dj <= 2; ++dj)
+#pragma unroll
+        for (int di = -2; di <= 2; ++di) acc += k[(di + 2) + 5 * (dj + 2)] * v(p + di + (int64_t)dj * nv);
+      return acc;
+    }
 #pragma unroll
     for (int dj = -2; dj <= 2; ++dj) {
       const int jj = j + dj;
@@ -99,23 +146,24 @@ struct CoarseOp {
       for (int di = -2; di <= 2; ++di) {
         const int ii = i + di;
         if (ii < 0 || ii >= nv) continue;
-        const int o = (di + 2) + 5 * (dj + 2);
-        const T k = lam2 * gl[o * n + p] + ga[o * n + p];
-        acc += k * v((int64_t)ii + (int64_t)jj * nv);
+        acc += k[(di + 2) + 5 * (dj + 2)] * v((int64_t)ii + (int64_t)jj * nv);
       }
     }
     return acc;
   }
   __device__ __forceinline__ double l1(int64_t p, int i, int j, double lam2) const {
+    const T* row = cf + p * kCoefStride;
     double s = 0;
-    for (int o = 0; o < kStencil; ++o) s += fabs(lam2 * (double)gl[o * n + p] + (double)ga[o * n + p]);
+    for (int o = 0; o < kStencil; ++o) s += fabs(lam2 * (double)row[o] + (double)row[32 + o]);
     return s;
   }
   __device__ __forceinline__ double center(int64_t p, int, int, double lam2) const {
-    return lam2 * (double)gl[12 * n + p] + (double)ga[12 * n + p];
+    const T* row = cf + p * kCoefStride;
+    return lam2 * (double)row[12] + (double)row[32 + 12];
   }
   template <class F>
   __device__ __forceinline__ void row(int64_t p, int i, int j, double lam2, F emit) const {
+    const T* rw = cf + p * kCoefStride;
     for (int dj = -2; dj <= 2; ++dj) {
       const int jj = j + dj;
       if (jj < 0 || jj >= nh) continue;
@@ -123,11 +171,27 @@ struct CoarseOp {
         const int ii = i + di;
         if (ii < 0 || ii >= nv) continue;
         const int o = (di + 2) + 5 * (dj + 2);
-        emit((int64_t)ii + (int64_t)jj * nv, lam2 * (double)gl[o * n + p] + (double)ga[o * n + p]);
+        emit((int64_t)ii + (int64_t)jj * nv, lam2 * (double)rw[o] + (double)rw[32 + o]);
       }
     }
   }
 };
+
+// SoA (25 x n per part, from the Galerkin products) -> AoS rows of the
+// smoother; entries 25..31 and 57..63 are zero.
+template <class T>
+__global__ void k_coef_pack(int64_t n, const double* __restrict__ gl, const double* __restrict__ ga,
+                            T* __restrict__ cf) {
+  for (int64_t t = (int64_t)blockIdx.x * kBlock + threadIdx.x; t < n * kCoefStride;
+       t += (int64_t)gridDim.x * kBlock) {
+    const int64_t p = t / kCoefStride;
+    const int o = (int)(t - p * kCoefStride);
+    double v = 0.0;
+    if (o < kStencil) v = gl[(int64_t)o * n + p];
+    else if (o >= 32 && o < 32 + kStencil) v = ga[(int64_t)(o - 32) * n + p];
+    cf[t] = (T)v;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // CSR SpMM over B interleaved columns.  One warp per row; the 32 lanes are
@@ -171,18 +235,35 @@ __global__ void __launch_bounds__(kBlock)
 #pragma unroll
   for (int t = 0; t < CPG; ++t) dacc[t] = 0.0;
 
+  constexpr int U = 4;  // nnz per lane in flight
   for (int64_t r = warp; r < a.rows; r += nwarps) {
     const int64_t k0 = a.rp[r], k1 = a.rp[r + 1];
     T acc[CPG];
 #pragma unroll
     for (int t = 0; t < CPG; ++t) acc[t] = 0;
-    for (int64_t k = k0 + s; k < k1; k += S) {
-      const int64_t c = a.ci[k];
-      const T v = (T)va[k];
-      const T* xr = X + c * a.B + cbase;
+    for (int64_t kb = k0 + s; kb < k1; kb += S * U) {
+      // the matrix is streamed once per apply: load it evict-first so the
+      // gathered vectors stay in L2; all loads of the step are independent
+      int cu[U];
+      T vu[U];
 #pragma unroll
-      for (int t = 0; t < CPG; ++t)
-        if (cbase + t < cend) acc[t] += v * xr[t];
+      for (int u = 0; u < U; ++u) {
+        const int64_t k = kb + (int64_t)u * S;
+        const bool ok = k < k1;
+        cu[u] = ok ? __ldcs(a.ci + k) : 0;
+        vu[u] = ok ? (T)__ldcs(va + k) : (T)0;
+      }
+      T xv[U][CPG];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const T* xr = X + (int64_t)cu[u] * a.B + cbase;
+#pragma unroll
+        for (int t = 0; t < CPG; ++t) xv[u][t] = (cbase + t < cend) ? xr[t] : (T)0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int t = 0; t < CPG; ++t) acc[t] += vu[u] * xv[u][t];
     }
 #pragma unroll
     for (int off = G; off < 32; off <<= 1)
@@ -628,6 +709,92 @@ __device__ __forceinline__ double sum_parts(const double* part, int nblk, int B,
   double s = 0.0;
   for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * B + col];
   return s;
+}
+
+// One block of kColThreads threads per column sums that column's partials
+// (fixed thread stride and tree: deterministic) so the FP64 additions are
+// spread over B multiprocessors.
+constexpr int kColThreads = 128;
+
+__device__ __forceinline__ double block_sum_parts(const double* part, int nblk, int B, int col) {
+  __shared__ double sm[kColThreads / 32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += kColThreads) s += part[(int64_t)b * B + col];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < kColThreads / 32; ++w) t += sm[w];
+  return t;
+}
+
+// alpha = rz / p^T q ; grid = B blocks.  Also clears the counters that
+// k_scalar_col_beta accumulates.
+static __global__ void __launch_bounds__(kColThreads)
+    k_scalar_col_alpha(int B, int nblk, const double* __restrict__ pq_part, ColState st) {
+  const int col = blockIdx.x;
+  if (col == 0 && threadIdx.x < 3) st.counters[threadIdx.x] = 0;
+  if (!st.active[col]) {
+    if (threadIdx.x == 0) st.alpha[col] = 0.0;
+    return;
+  }
+  const double pq = block_sum_parts(pq_part, nblk, B, col);
+  if (threadIdx.x != 0) return;
+  st.iters[col] += 1;
+  if (!isfinite(pq)) {
+    st.status[col] = ST_NONFINITE;
+    st.active[col] = 0;
+    st.alpha[col] = 0.0;
+  } else if (!(pq > 0.0)) {
+    st.status[col] = ST_BREAKDOWN;
+    st.active[col] = 0;
+    st.alpha[col] = 0.0;
+  } else {
+    st.alpha[col] = st.rz[col] / pq;
+  }
+}
+
+// rr, recursive convergence and beta for one column per block; counters
+// (cleared by k_scalar_col_alpha) accumulate with integer atomics.
+static __global__ void __launch_bounds__(kColThreads)
+    k_scalar_col_beta(int B, int nblk_rr, const double* __restrict__ rr_part, int nblk_rz,
+                      const double* __restrict__ rz_part, ColState st, int maxit, double rel_trigger) {
+  const int col = blockIdx.x;
+  if (st.active[col]) {
+    const double rr = block_sum_parts(rr_part, nblk_rr, B, col);
+    const double rzn = block_sum_parts(rz_part, nblk_rz, B, col);
+    if (threadIdx.x == 0) {
+      st.rr[col] = rr;
+      if (!isfinite(rr) || !isfinite(rzn)) {
+        st.status[col] = ST_NONFINITE;
+        st.active[col] = 0;
+        st.beta[col] = 0.0;
+      } else if (rr <= st.tol2cc[col]) {
+        st.pending[col] = 1;
+        st.active[col] = 0;
+        st.beta[col] = 0.0;
+      } else if (st.iters[col] >= maxit) {
+        st.status[col] = ST_MAXIT;
+        st.active[col] = 0;
+        st.beta[col] = 0.0;
+      } else if (!(rzn > 0.0)) {
+        st.status[col] = ST_BREAKDOWN;
+        st.active[col] = 0;
+        st.beta[col] = 0.0;
+      } else {
+        st.beta[col] = rzn / st.rz[col];
+        st.rz[col] = rzn;
+        if (rel_trigger > 0.0 && rr < rel_trigger * st.rmax[col]) atomicAdd(&st.counters[2], 1);
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (st.active[col]) atomicAdd(&st.counters[0], 1);
+    if (st.pending[col]) atomicAdd(&st.counters[1], 1);
+  }
 }
 
 // alpha = rz / p^T q

@@ -13,10 +13,10 @@ struct LevelView {
   bool fine = true;
   const T* ws = nullptr;  // fine level: squared edge weights
   const T* we = nullptr;
-  const T* ga = nullptr;  // fine: diag(A^T A); coarse: 25 x n A-part
-  const T* gl = nullptr;  // coarse: 25 x n L-part
+  const T* ga = nullptr;  // fine: diag(A^T A)
+  const T* cf = nullptr;  // coarse: per-point coefficient rows
   FineOp<T> fine_op() const { return FineOp<T>{nv, nh, ws, we, ga}; }
-  CoarseOp<T> coarse_op() const { return CoarseOp<T>{nv, nh, n, gl, ga}; }
+  CoarseOp<T> coarse_op() const { return CoarseOp<T>{nv, nh, n, cf}; }
 };
 
 // Y = A X / Q = A^T Y + lam2 L^T W L P (+dot) / rho partials / true residual.
