@@ -264,6 +264,40 @@ int lcmg_num_levels(lcmg_ctx* ctx, int32_t* levels);
 /* diag(A^T A) (n doubles, host). */
 int lcmg_get_diag(lcmg_ctx* ctx, double* diag_out);
 
+/* Allocation-free application of q_j = (A^T A + lambda_j^2 L^T D^2 L) p_j.
+ * The paper has no counterpart: this exists for callers that cannot
+ * allocate device memory where they need the operator (code under an
+ * external memory manager that owns every device byte, a real-time loop
+ * that cannot pay an allocation's synchronisation, a thread that must not
+ * enter the allocator).  Unlike lcmg_apply_normal_dev it needs no context
+ * and calls no cudaMalloc/cudaFree: every input and output is a
+ * caller-owned device pointer on `device`, and the intermediate A p lives
+ * in a fixed array of 2^19 doubles (4 MiB) in the library's device image,
+ * held by every GPU that loads the library until the process exits.
+ *   device, stream   CUDA device of all pointers; stream (cudaStream_t) the
+ *                    two kernels are launched on; the call does not
+ *                    synchronise.  The caller's current device is restored.
+ *   n_v, n_h, m      image grid and the number of rows of A
+ *   row_ptr[m+1], col[nnz], val[nnz]          A as CSR (int64, int32, values)
+ *   row_ptr_t[n+1], col_t[nnz], val_t[nnz]    A^T as CSR (n = n_v n_h)
+ *   val_dtype        0 = FP32 values, 1 = FP64 values (both matrices)
+ *   d[n_edges]       edge weights D, ordered as in lcmg_set_weights
+ *   n_cols           columns, 1..64, with n_cols * m <= 2^19
+ *   lambda[n_cols]   host array
+ *   p, q             [n_cols][n] device arrays (each column contiguous)
+ * Arithmetic is FP64.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, once per device, with that device
+ * current); make that first call before any stream capture.  Every call
+ * shares the one array and overwrites what it reads, so calls whose kernels
+ * overlap on the GPU (other streams, other threads) race: order them.
+ * Errors: INVALID_ARG (sizes, null pointers, n_cols * m above the limit),
+ * CUDA. */
+int lcmg_apply_normal_noalloc(int device, void* stream, int32_t n_v, int32_t n_h, int64_t m,
+                              const int64_t* row_ptr, const int32_t* col, const void* val,
+                              const int64_t* row_ptr_t, const int32_t* col_t, const void* val_t,
+                              int32_t val_dtype, const double* d, int32_t n_cols,
+                              const double* lambda, const double* p, double* q);
+
 #ifdef __cplusplus
 }
 #endif

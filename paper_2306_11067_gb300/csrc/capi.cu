@@ -132,6 +132,8 @@ struct lcmg_ctx {
 namespace lcmg {
 
 static void set_err(const std::string& s) { g_err = s; }
+// for entry points defined in other translation units
+void set_error_message(const std::string& s) { g_err = s; }
 
 static void check_params(const lcmg_params& p) {
   if (p.levels < 0 || p.coarse_max < 1 || p.nu < 1 || p.nu > 16) throw ArgError("invalid levels/coarse_max/nu");

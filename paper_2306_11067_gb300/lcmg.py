@@ -83,6 +83,8 @@ _SIGS = {
     "lcmg_get_level": (C.c_int, [_P, _I32, _PI32, _PI32, _P, _P]),
     "lcmg_num_levels": (C.c_int, [_P, _PI32]),
     "lcmg_get_diag": (C.c_int, [_P, _P]),
+    "lcmg_apply_normal_noalloc": (C.c_int, [C.c_int, _P, _I32, _I32, _I64, _P, _P, _P, _P, _P, _P, _I32, _P,
+                                            _I32, _P, _P, _P]),
 }
 
 
@@ -295,6 +297,19 @@ def lcmg_get_level(ctx, k: int):
     if k > 0:
         _check(lib().lcmg_get_level(ctx, k, None, None, _ptr(gl), _ptr(ga)))
     return nv.value, nh.value, gl, ga
+
+
+def lcmg_apply_normal_noalloc(device, stream, n_v, n_h, m, row_ptr, col, val, row_ptr_t, col_t, val_t,
+                              d, lambdas, p, q):
+    """Allocation-free q = (A^T A + lambda^2 L^T D^2 L) p; every array is a
+    torch CUDA tensor on `device` except ``lambdas`` (host).  For callers
+    that cannot allocate device memory at the point of use."""
+    lam = _f64(lambdas)
+    dt = 0 if str(val.dtype).endswith("float32") else 1
+    s = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().lcmg_apply_normal_noalloc(device, s, n_v, n_h, m, _ptr(row_ptr), _ptr(col), _ptr(val),
+                                           _ptr(row_ptr_t), _ptr(col_t), _ptr(val_t), dt, _ptr(d), lam.size,
+                                           _ptr(lam), _ptr(p), _ptr(q)))
 
 
 def lcmg_get_diag(ctx, n: int):
