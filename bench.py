@@ -260,6 +260,7 @@ def main():
     op_ms_at = sum(s["op_ms_at"] for _, s in results)
     op_launches = sum(s["op_launches"] for _, s in results)
     op_bytes = sum(s["op_bytes"] for _, s in results)
+    batch_its = sum(s["batch_iterations"] for _, s in results)
     history = results[-1][0]["history"]
 
     # whole-job aggregate over ranks
@@ -311,7 +312,10 @@ def main():
         "avg_pass_us": (op_ms * 1e3 / op_launches) if op_launches else None,
         "avg_us_A": (op_ms_a * 2e3 / op_launches) if op_launches else None,
         "avg_us_At": (op_ms_at * 2e3 / op_launches) if op_launches else None,
-        "share_of_device_time": (op_ms / dev_ms) if dev_ms > 0 else None,
+        # the passes are timed on a sample of the iterations: scale the mean
+        # per-iteration time by every iteration of the timed steps
+        "share_of_device_time": ((op_ms * 2 / op_launches) * batch_its / dev_ms)
+        if (dev_ms > 0 and op_launches) else None,
     }
 
     # ---------------- CPU oracle baseline (rank 0, N = 1 only) ------------

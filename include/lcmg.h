@@ -98,6 +98,29 @@ typedef struct {
                            graph (default), 0 = launch kernels one by one            */
   int32_t timing;       /* 1 = time the operator passes with CUDA events (see
                            lcmg_stats); default 0                                     */
+  int32_t fused;        /* 1 = run everything of a PCG iteration between the two
+                           operator passes (alpha, x/r update, the whole V-cycle,
+                           beta, p update) as one kernel on one thread-block
+                           cluster when the GPU supports it; 2 = the same with
+                           L2-only loads of data written within the kernel;
+                           0 = one kernel per step (default)                        */
+  int32_t tail_points;  /* levels whose points x columns are at most this run their
+                           whole V-cycle part (down to the coarsest solve and back)
+                           in one CTA; 0 = off (default; on GB300 the one-CTA form
+                           is slower than one multi-block kernel per step)          */
+  int32_t pdl;          /* 1 = launch the kernels of the PCG iteration with
+                           programmatic dependent launch, so each kernel is
+                           scheduled while its predecessor drains; 0 = plain
+                           stream order (default: no gain measured on GB300)        */
+  int32_t fold;         /* 1 = compute alpha and beta in the last block of the
+                           kernels that produce their dot products; 0 = separate
+                           one-block scalar kernels (default: the fold lengthens
+                           the A^T pass by more than the kernel it saves)       */
+  int32_t staged;       /* 1 = stream the CSR matrix of A and A^T through shared
+                           memory with bulk asynchronous copies (cp.async.bulk,
+                           mbarrier ring of 3 stages) so the HBM stream does not
+                           wait on the vector gathers; 0 = direct warp-per-row
+                           loads (default)                                       */
 } lcmg_params;
 
 typedef struct lcmg_ctx lcmg_ctx;
@@ -238,6 +261,7 @@ typedef struct {
   double op_ms_at;
   int64_t op_launches;
   int64_t op_bytes;
+  int32_t fused_ctas;   /* CTAs of the cluster running the fused iteration, 0 if unused */
 } lcmg_stats;
 int lcmg_get_stats(lcmg_ctx* ctx, lcmg_stats* out);
 

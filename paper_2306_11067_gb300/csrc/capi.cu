@@ -16,6 +16,10 @@
 #include <vector>
 
 #include "launch.h"
+#include "spmm_staged.cuh"
+#include "mega.cuh"
+#include "tail.cuh"
+#include "tail_launch.h"
 #include "lcmg.h"
 
 namespace lcmg {
@@ -92,6 +96,11 @@ struct lcmg_ctx {
   DevBuf<int32_t> ci, ciT;
   DevBuf<float> v32, vT32;
   DevBuf<double> v64, vT64;
+  // row chunks of A and A^T for the shared-memory-staged SpMM
+  DevBuf<int32_t> ck_row, ckT_row;
+  DevBuf<int64_t> ck_nz, ckT_nz;
+  int64_t nck = 0, nckT = 0;
+  DevBuf<int> spmm_err;  // set by a staged SpMM whose stage wait gave up
   int rv = 0, rh = 0;
   DevBuf<double> psf64;
   DevBuf<float> psf32;
@@ -112,10 +121,11 @@ struct lcmg_ctx {
   DevBuf<double> lam2;
   DevBuf<char> lam2T;
   DevBuf<double> kinv, Mw, Ww;
-  DevBuf<double> part_pq, part_rr, part_rz, part_x;
+  DevBuf<double> part_pq, part_rr, part_rz, part_x, mega_part;
   DevBuf<double> s_rz, s_alpha, s_beta, s_rr, s_rmax, s_tol2cc, s_cc, s_rrtrue, s_out;
   DevBuf<int> s_active, s_iters, s_status, s_pending, s_counters, s_info, s_flag;
   DevBuf<double*> colptr;
+  DevBuf<int> tickets;  // last-block tickets of the folded scalar updates (kept at zero)
   DevBuf<int> colmap;
   int* h_counters = nullptr;  // pinned
   // weight-update scratch
@@ -132,6 +142,56 @@ struct lcmg_ctx {
 namespace lcmg {
 
 static void set_err(const std::string& s) { g_err = s; }
+
+// SpMM arguments for A (trans false) or A^T over ld interleaved columns
+static SpmmArgs csr_args(const lcmg_ctx& c, bool trans, int ld) {
+  SpmmArgs a{};
+  a.rows = trans ? c.n : c.m;
+  a.rp = trans ? c.rpT.p : c.rp.p;
+  a.ci = trans ? c.ciT.p : c.ci.p;
+  a.B = ld; a.c0 = 0; a.nb = ld; a.nl = 1; a.nrhs = 1;
+  if (c.prm.staged) {
+    a.ck_row = trans ? c.ckT_row.p : c.ck_row.p;
+    a.ck_nz = trans ? c.ckT_nz.p : c.ck_nz.p;
+    a.nck = trans ? c.nckT : c.nck;
+    a.err = c.spmm_err.p;
+  }
+  return a;
+}
+
+// Raise if a staged SpMM reported a stage wait that gave up (and clear it).
+static void check_spmm_err(lcmg_ctx& c) {
+  if (!c.prm.staged || c.fwd != 1) return;
+  int e = 0;
+  LCMG_CUDA(cudaMemcpyAsync(&e, c.spmm_err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  LCMG_CUDA(cudaStreamSynchronize(c.stream));
+  if (e != 0) {
+    LCMG_CUDA(cudaMemsetAsync(c.spmm_err.p, 0, sizeof(int), c.stream));
+    throw CudaError("staged SpMM: a shared-memory stage was not filled within its wait limit");
+  }
+}
+
+// Chunks of consecutive rows with at most kChunkNnz nonzeros and at most
+// kChunkRows rows; a row with more than kChunkNnz nonzeros is its own chunk.
+static int64_t build_chunks(const int64_t* rp, int64_t rows, DevBuf<int32_t>& d_row, DevBuf<int64_t>& d_nz) {
+  std::vector<int32_t> row;
+  std::vector<int64_t> nz;
+  int64_t r = 0;
+  while (r < rows) {
+    row.push_back((int32_t)r);
+    nz.push_back(rp[r]);
+    int64_t e = r + 1;
+    if (rp[r + 1] - rp[r] <= kChunkNnz)
+      while (e < rows && e - r < kChunkRows && rp[e + 1] - rp[r] <= kChunkNnz) ++e;
+    r = e;
+  }
+  row.push_back((int32_t)rows);
+  nz.push_back(rp[rows]);
+  const int64_t nck = (int64_t)row.size() - 1;
+  LCMG_CUDA(cudaMemcpy(d_row.need(row.size()), row.data(), sizeof(int32_t) * row.size(), cudaMemcpyHostToDevice));
+  LCMG_CUDA(cudaMemcpy(d_nz.need(nz.size()), nz.data(), sizeof(int64_t) * nz.size(), cudaMemcpyHostToDevice));
+  return nck;
+}
 // for entry points defined in other translation units
 void set_error_message(const std::string& s) { g_err = s; }
 
@@ -144,6 +204,11 @@ static void check_params(const lcmg_params& p) {
   if (p.precision != LCMG_PREC_FP64 && p.precision != LCMG_PREC_MIXED) throw ArgError("invalid precision");
   if (p.mode != LCMG_MODE_BATCHED && p.mode != LCMG_MODE_SEQUENTIAL) throw ArgError("invalid mode");
   if (p.check_every < 1) throw ArgError("check_every must be >= 1");
+  if (p.fused < 0 || p.fused > 2) throw ArgError("fused must be 0, 1 or 2");
+  if (p.tail_points < 0) throw ArgError("tail_points must be >= 0");
+  if (p.pdl != 0 && p.pdl != 1) throw ArgError("pdl must be 0 or 1");
+  if (p.fold != 0 && p.fold != 1) throw ArgError("fold must be 0 or 1");
+  if (p.staged != 0 && p.staged != 1) throw ArgError("staged must be 0 or 1");
 }
 
 static int sum_blocks(int nb) { return std::max(1, std::min(nb, kMaxBlocks)); }
@@ -162,11 +227,11 @@ static int level_count(const lcmg_ctx& c) {
 
 static void refresh_fine(lcmg_ctx& c) {
   const int g = (int)std::min<int64_t>((c.n + kBlock - 1) / kBlock, c.maxblk);
-  k_edge_to_pixel<<<g, kBlock, 0, c.stream>>>(c.nv, c.nh, c.d.p, c.ws.need(c.n), c.we.need(c.n));
+  klaunch(k_edge_to_pixel, dim3(g), dim3(kBlock), 0, c.stream, c.nv, c.nh, c.d.p, c.ws.need(c.n), c.we.need(c.n));
   LCMG_LAUNCHED();
-  k_convert<double, float><<<g, kBlock, 0, c.stream>>>(c.n, c.ws.p, c.ws32.need(c.n));
+  klaunch(k_convert<double, float>, dim3(g), dim3(kBlock), 0, c.stream, c.n, c.ws.p, c.ws32.need(c.n));
   LCMG_LAUNCHED();
-  k_convert<double, float><<<g, kBlock, 0, c.stream>>>(c.n, c.we.p, c.we32.need(c.n));
+  klaunch(k_convert<double, float>, dim3(g), dim3(kBlock), 0, c.stream, c.n, c.we.p, c.we32.need(c.n));
   LCMG_LAUNCHED();
   c.hier_ok = false;
 }
@@ -202,9 +267,9 @@ static void build_hierarchy(lcmg_ctx& c) {
     }
     // smoother copies: per-point rows of both parts (FP64 and FP32)
     const int gg = (int)std::min<int64_t>((kCoefStride * g.n + kBlock - 1) / kBlock, c.maxblk);
-    k_coef_pack<double><<<gg, kBlock, 0, c.stream>>>(g.n, gl, ga, g.cf64.need(kCoefStride * g.n));
+    klaunch(k_coef_pack<double>, dim3(gg), dim3(kBlock), 0, c.stream, g.n, gl, ga, g.cf64.need(kCoefStride * g.n));
     LCMG_LAUNCHED();
-    k_coef_pack<float><<<gg, kBlock, 0, c.stream>>>(g.n, gl, ga, g.cf32.need(kCoefStride * g.n));
+    klaunch(k_coef_pack<float>, dim3(gg), dim3(kBlock), 0, c.stream, g.n, gl, ga, g.cf32.need(kCoefStride * g.n));
     LCMG_LAUNCHED();
   }
   c.hier_ok = true;
@@ -257,10 +322,15 @@ static void ensure_work(lcmg_ctx& c, int B) {
   c.lam2.need(B); c.lam2T.need(B * tb);
   const size_t pb = (size_t)kMaxBlocks * B;
   c.part_pq.need(pb); c.part_rr.need(pb); c.part_rz.need(pb); c.part_x.need(pb);
+  c.mega_part.need((size_t)kMegaMaxCtas * 2 * kMaxB);
   for (auto* b : {&c.s_rz, &c.s_alpha, &c.s_beta, &c.s_rr, &c.s_rmax, &c.s_tol2cc, &c.s_cc, &c.s_rrtrue, &c.s_out})
     b->need(B);
   for (auto* b : {&c.s_active, &c.s_iters, &c.s_status, &c.s_pending, &c.s_info, &c.s_flag}) b->need(B);
   c.s_counters.need(4);
+  if (!c.tickets.p) {
+    c.tickets.need(4);
+    LCMG_CUDA(cudaMemset(c.tickets.p, 0, 4 * sizeof(int)));
+  }
   if (!c.h_counters) LCMG_CUDA(cudaMallocHost(&c.h_counters, 4 * sizeof(int)));
   c.Bcap = std::max(c.Bcap, B);
 }
@@ -293,14 +363,7 @@ struct Batch {
   FineOp<T> fop() { return view<T>(c, 0).fine_op(); }
   FineOp<double> fop64() { return view<double>(c, 0).fine_op(); }
 
-  SpmmArgs args(bool trans, int ld) {
-    SpmmArgs a{};
-    a.rows = trans ? c.n : c.m;
-    a.rp = trans ? c.rpT.p : c.rp.p;
-    a.ci = trans ? c.ciT.p : c.ci.p;
-    a.B = ld; a.c0 = 0; a.nb = ld; a.nl = 1; a.nrhs = 1;
-    return a;
-  }
+  SpmmArgs args(bool trans, int ld) { return csr_args(c, trans, ld); }
   PsfArgs psf() {
     PsfArgs a{};
     a.nv = c.nv; a.nh = c.nh; a.rv = c.rv; a.rh = c.rh; a.psf = c.psf64.p;
@@ -309,11 +372,15 @@ struct Batch {
   const T* psfT();
 
   // q = K p (T precision) with partials of p.q; returns the partial count
-  int apply_K(const T* P, T* Q, double* part);
+  int apply_K(const T* P, T* Q, double* part, const ScalarFold* fold = nullptr, bool* folded = nullptr);
 
   // ---- live timing of the operator passes (params.timing) ------------
+  // Only the first iteration of each block of check_every iterations is
+  // bracketed by events (a sample: the event-record nodes themselves cost
+  // time inside the graph).
+  bool timing_now = false;
   void mark() {
-    if (!c.prm.timing) return;
+    if (!c.prm.timing || !timing_now) return;
     if (c.tev_used >= (int)c.tev.size()) {
       cudaEvent_t e;
       LCMG_CUDA(cudaEventCreate(&e));
@@ -345,8 +412,12 @@ struct Batch {
   int true_residual(double* part);
 
   // ---- V-cycle (Algorithm 1, gamma = 1, zero initial guess) ----------
-  void sweeps(int k, int m, const T* rhs, T* z, T* t, double* part, int* nb_out) {
-    // m Jacobi sweeps z <- z + D^{-1}(rhs - K z), ending in z
+  // m Jacobi sweeps z <- z + D^{-1}(rhs - K z), ending in z; with part the
+  // r.z partials of the result, and with fold (even m only) the beta update
+  // in the last sweep's last block (*folded reports whether it happened)
+  void sweeps(int k, int m, const T* rhs, T* z, T* t, double* part, int* nb_out,
+              const ScalarFold* fold = nullptr, bool* folded = nullptr) {
+    if (folded) *folded = false;
     if (m <= 0) return;
     LevelView<T> L = view<T>(c, k);
     const T* dinv = tp(c.lw[k].dinv);
@@ -354,8 +425,10 @@ struct Batch {
     T* b = t;
     for (int i = 0; i < m; ++i) {
       const bool last = (i == m - 1);
-      int nb = launch_smooth<T>(L, B, lam2T(), dinv, rhs, a, b, nullptr, (last && (m % 2 == 0)) ? part : nullptr,
-                                c.maxblk, s);
+      const bool with_dot = last && (m % 2 == 0);
+      int nb = launch_smooth<T>(L, B, lam2T(), dinv, rhs, a, b, nullptr, with_dot ? part : nullptr,
+                                c.maxblk, s, (with_dot && part) ? fold : nullptr);
+      if (with_dot && part && fold && folded) *folded = true;
       if (last && (m % 2 == 0) && nb_out) *nb_out = nb;
       std::swap(a, b);
     }
@@ -363,20 +436,29 @@ struct Batch {
       launch_copy_cols<T>(L.n, B, nullptr, t, z, c.maxblk, s);
       if (part) {
         const int g = grid_for(L.n, B, c.maxblk);
-        k_col_dot<T><<<g, kBlock, 0, s>>>(L.n, B, rhs, z, part);
+        klaunch(k_col_dot<T>, dim3(g), dim3(kBlock), 0, s, L.n, B, rhs, z, part);
         LCMG_LAUNCHED();
         if (nb_out) *nb_out = g;
       }
     }
   }
 
-  int vcycle(const T* r0, T* z0, double* part) {
+  // first level (>= 1) whose points x columns fit the one-CTA tail, else nlev
+  int tail_level() const {
+    if (c.prm.tail_points <= 0 || nlev < 2) return nlev;
+    for (int k = 1; k < nlev; ++k)
+      if (c.lev[k].n * B <= c.prm.tail_points && nlev - k <= kTailMaxLevels) return k;
+    return nlev;
+  }
+
+  int vcycle(const T* r0, T* z0, double* part, const ScalarFold* fold = nullptr, bool* folded = nullptr) {
+    if (folded) *folded = false;
     const int nu = c.prm.nu;
     int nb = 0;
     if (nlev == 1) {
       launch_coarse_solve<T>((int)c.lev[0].n, B, c.kinv.p, r0, z0, s);
       const int g = grid_for(c.n, B, c.maxblk);
-      k_col_dot<T><<<g, kBlock, 0, s>>>(c.n, B, r0, z0, part);
+      klaunch(k_col_dot<T>, dim3(g), dim3(kBlock), 0, s, c.n, B, r0, z0, part);
       LCMG_LAUNCHED();
       return g;
     }
@@ -384,7 +466,10 @@ struct Batch {
     std::vector<T*> zz(nlev);
     rhs[0] = r0; zz[0] = z0;
     for (int k = 1; k < nlev; ++k) { rhs[k] = tp(c.lw[k].rhs); zz[k] = tp(c.lw[k].z); }
-    for (int k = 0; k + 1 < nlev; ++k) {
+    // levels k0 .. nlev-1 run in one CTA when they are small enough
+    const int k0 = tail_level();
+    const int kstop = (k0 < nlev) ? k0 : nlev - 1;
+    for (int k = 0; k < kstop; ++k) {
       LevelView<T> L = view<T>(c, k);
       const T* dinv = tp(c.lw[k].dinv);
       launch_smooth_zero<T>(L, B, lam2T(), dinv, rhs[k], zz[k], nu >= 2 ? 1 : 0, c.maxblk, s);
@@ -392,10 +477,34 @@ struct Batch {
       launch_residual<T>(L, B, lam2T(), rhs[k], zz[k], tp(c.lw[k].res), c.maxblk, s);
       launch_restrict<T>(c.lev[k + 1].nv, c.lev[k + 1].nh, B, tp(c.lw[k].res), tp(c.lw[k + 1].rhs), c.maxblk, s);
     }
-    launch_coarse_solve<T>((int)c.lev[nlev - 1].n, B, c.kinv.p, rhs[nlev - 1], zz[nlev - 1], s);
-    for (int k = nlev - 2; k >= 0; --k) {
+    if (k0 < nlev) {
+      TailArgs<T> ta{};
+      ta.B = B;
+      ta.nl = nlev - k0;
+      ta.nu = nu;
+      ta.nc = (int)c.lev[nlev - 1].n;
+      ta.kinv = c.kinv.p;
+      ta.lam2T = lam2T();
+      for (int k = k0; k < nlev; ++k) {
+        TailLevel<T>& t = ta.lev[k - k0];
+        t.nv = c.lev[k].nv;
+        t.nh = c.lev[k].nh;
+        t.n = c.lev[k].n;
+        t.cf = view<T>(c, k).cf;
+        t.dinv = tp(c.lw[k].dinv);
+        t.rhs = tp(c.lw[k].rhs);
+        t.z = tp(c.lw[k].z);
+        t.t = tp(c.lw[k].t);
+        t.res = tp(c.lw[k].res);
+      }
+      launch_vcycle_tail<T>(ta, s);
+    } else {
+      launch_coarse_solve<T>((int)c.lev[nlev - 1].n, B, c.kinv.p, rhs[nlev - 1], zz[nlev - 1], s);
+    }
+    for (int k = kstop - 1; k >= 0; --k) {
       launch_prolong_add<T>(c.lev[k + 1].nv, c.lev[k + 1].nh, B, zz[k + 1], zz[k], c.maxblk, s);
-      sweeps(k, nu, rhs[k], zz[k], tp(c.lw[k].t), k == 0 ? part : nullptr, k == 0 ? &nb : nullptr);
+      sweeps(k, nu, rhs[k], zz[k], tp(c.lw[k].t), k == 0 ? part : nullptr, k == 0 ? &nb : nullptr,
+             k == 0 ? fold : nullptr, k == 0 ? folded : nullptr);
     }
     return nb;
   }
@@ -423,25 +532,94 @@ struct Batch {
     LCMG_CUDA(cudaStreamSynchronize(s));
   }
 
+  // the one-cluster iteration kernel is used when enabled and supported
+  bool use_fused() const {
+    return c.prm.fused && nlev <= kMegaMaxLevels && mega_cluster_ctas<T>() > 0 &&
+           (int64_t)c.lev[nlev - 1].n <= 4096;
+  }
+
+  MegaArgs<T> mega_args(int nb_pq) {
+    MegaArgs<T> a{};
+    a.B = B;
+    a.nlev = nlev;
+    a.nu = c.prm.nu;
+    a.nc = (int)c.lev[nlev - 1].n;
+    for (int k = 0; k < nlev; ++k) {
+      LevelView<T> v = view<T>(c, k);
+      MegaLevel<T>& m = a.lev[k];
+      m.nv = v.nv;
+      m.nh = v.nh;
+      m.n = v.n;
+      m.fine = k == 0;
+      m.ws = v.ws;
+      m.we = v.we;
+      m.ga = v.ga;
+      m.cf = v.cf;
+      m.dinv = tp(c.lw[k].dinv);
+      m.rhs = k == 0 ? tp(c.r) : tp(c.lw[k].rhs);
+      m.z = k == 0 ? tp(c.z) : tp(c.lw[k].z);
+      m.t = tp(c.lw[k].t);
+      m.res = tp(c.lw[k].res);
+    }
+    a.kinv = c.kinv.p;
+    a.x = std::is_same<T, double>::value ? reinterpret_cast<T*>(c.x64.p) : reinterpret_cast<T*>(c.xlo.p);
+    a.p = tp(c.p);
+    a.q = tp(c.q);
+    a.lam2T = lam2T();
+    a.st = colstate(c);
+    a.pq_part = c.part_pq.p;
+    a.nblk_pq = nb_pq;
+    a.cta_part = c.mega_part.p;
+    a.maxit = c.prm.maxit;
+    a.rel_trigger = std::is_same<T, float>::value ? 0.01 : 0.0;
+    return a;
+  }
+
   // one PCG iteration for all active columns
-  void iterate_once() {
+  void iterate_once(bool time_it = false) {
+    timing_now = time_it;
     ColState st = colstate(c);
     T* P = tp(c.p);
     T* Q = tp(c.q);
     T* R = tp(c.r);
     T* Z = tp(c.z);
-    const int nb_pq = apply_K(P, Q, c.part_pq.p);
-    k_scalar_col_alpha<<<B, kColThreads, 0, s>>>(B, nb_pq, c.part_pq.p, st);
-    LCMG_LAUNCHED();
+    const double trig = std::is_same<T, float>::value ? 0.01 : 0.0;  // ||r|| fell 10x since the last update
+    if (use_fused()) {
+      const int nb_pq = apply_K(P, Q, c.part_pq.p);
+      launch_pcg_mega<T>(mega_args(nb_pq), mega_cluster_ctas<T>(), c.prm.fused == 2, s);
+      c.stats.fused_ctas = mega_cluster_ctas<T>();
+      return;
+    }
+    // alpha in the last block of the A^T pass when the operator allows it
+    ScalarFold fa{};
+    fa.st = st;
+    fa.ticket = c.tickets.p;
+    bool alpha_folded = false;
+    const int nb_pq = apply_K(P, Q, c.part_pq.p, c.prm.fold ? &fa : nullptr, &alpha_folded);
+    if (!alpha_folded) {
+      klaunch(k_scalar_col_alpha, dim3(B), dim3(kColThreads), 0, s, B, nb_pq, c.part_pq.p, st);
+      LCMG_LAUNCHED();
+    }
     int nb_rr;
     if (std::is_same<T, double>::value)
       nb_rr = launch_update_xr<T, T>(c.n, B, st, P, Q, reinterpret_cast<T*>(c.x64.p), R, c.part_rr.p, c.maxblk, s);
     else
       nb_rr = launch_update_xr<T, T>(c.n, B, st, P, Q, reinterpret_cast<T*>(c.xlo.p), R, c.part_rr.p, c.maxblk, s);
-    const int nb_rz = vcycle(R, Z, c.part_rz.p);
-    const double trig = std::is_same<T, float>::value ? 0.01 : 0.0;  // ||r|| fell 10x since the last update
-    k_scalar_col_beta<<<B, kColThreads, 0, s>>>(B, nb_rr, c.part_rr.p, nb_rz, c.part_rz.p, st, c.prm.maxit, trig);
-    LCMG_LAUNCHED();
+    // beta in the last block of the final level-0 sweep when possible
+    ScalarFold fb{};
+    fb.st = st;
+    fb.ticket = c.tickets.p + 1;
+    fb.rr_part = c.part_rr.p;
+    fb.nblk_rr = nb_rr;
+    fb.maxit = c.prm.maxit;
+    fb.rel_trigger = trig;
+    bool beta_folded = false;
+    const int nb_rz = vcycle(R, Z, c.part_rz.p, c.prm.fold ? &fb : nullptr, &beta_folded);
+    if (!beta_folded) {
+      klaunch(k_scalar_col_beta, dim3(B), dim3(kColThreads), 0, s, B, nb_rr, c.part_rr.p, nb_rz, c.part_rz.p, st,
+              c.prm.maxit, trig);
+      LCMG_LAUNCHED();
+    }
     launch_update_p<T>(c.n, B, st, Z, P, c.maxblk, s);
   }
 
@@ -451,21 +629,21 @@ struct Batch {
     ColState st = colstate(c);
     if (!std::is_same<T, double>::value) {
       const int g = (int)std::min<int64_t>(((int64_t)c.n * B + kBlock - 1) / kBlock, c.maxblk);
-      k_flush_x<<<g, kBlock, 0, s>>>((int64_t)c.n * B, c.xlo.p, c.x64.p);
+      klaunch(k_flush_x, dim3(g), dim3(kBlock), 0, s, (int64_t)c.n * B, c.xlo.p, c.x64.p);
       LCMG_LAUNCHED();
     }
     const int nb = true_residual(c.part_x.p);
-    k_sum_parts<<<1, kScalarThreads, 0, s>>>(B, nb, c.part_x.p, c.s_rrtrue.p);
+    klaunch(k_sum_parts, dim3(1), dim3(kScalarThreads), 0, s, B, nb, c.part_x.p, c.s_rrtrue.p);
     LCMG_LAUNCHED();
-    k_true_check<<<1, kBlock, 0, s>>>(B, c.s_rrtrue.p, st, replace_active ? 1 : 0, c.s_flag.p);
+    klaunch(k_true_check, dim3(1), dim3(kBlock), 0, s, B, c.s_rrtrue.p, st, replace_active ? 1 : 0, c.s_flag.p);
     LCMG_LAUNCHED();
     const int g = grid_for(c.n, B, c.maxblk);
-    k_take_residual<T><<<g, kBlock, 0, s>>>(c.n, B, c.s_flag.p, c.r64.p, tp(c.r));
+    klaunch(k_take_residual<T>, dim3(g), dim3(kBlock), 0, s, c.n, B, c.s_flag.p, c.r64.p, tp(c.r));
     LCMG_LAUNCHED();
     read_counters();
     if (c.h_counters[3] > 0) {  // restarted columns: z = B r, p = z, rz = r.z
       const int nbz = vcycle(tp(c.r), tp(c.z), c.part_rz.p);
-      k_restart_finish<T><<<g, kBlock, 0, s>>>(c.n, B, nbz, c.part_rz.p, c.s_flag.p, st, tp(c.z), tp(c.p));
+      klaunch(k_restart_finish<T>, dim3(g), dim3(kBlock), 0, s, c.n, B, nbz, c.part_rz.p, c.s_flag.p, st, tp(c.z), tp(c.p));
       LCMG_LAUNCHED();
     }
   }
@@ -473,34 +651,40 @@ struct Batch {
   // Run PCG on the batch whose x64 (initial guesses) and c64 (right-hand
   // sides A^T b) are set.  Returns the number of batch iterations.
   int64_t run(const std::vector<double>& lam) {
+    // programmatic dependent launch for the kernels of this run
+    struct PdlScope {
+      bool prev;
+      explicit PdlScope(bool on) : prev(pdl_flag()) { pdl_flag() = on; }
+      ~PdlScope() { pdl_flag() = prev; }
+    } pdl_scope(c.prm.pdl == 1);
     setup(lam);
     ColState st = colstate(c);
     // ||c||^2 and the true initial residual
     const int g = grid_for(c.n, B, c.maxblk);
-    k_col_dot<double><<<g, kBlock, 0, s>>>(c.n, B, c.c64.p, c.c64.p, c.part_x.p);
+    klaunch(k_col_dot<double>, dim3(g), dim3(kBlock), 0, s, c.n, B, c.c64.p, c.c64.p, c.part_x.p);
     LCMG_LAUNCHED();
-    k_sum_parts<<<1, kScalarThreads, 0, s>>>(B, g, c.part_x.p, c.s_cc.p);
+    klaunch(k_sum_parts, dim3(1), dim3(kScalarThreads), 0, s, B, g, c.part_x.p, c.s_cc.p);
     LCMG_LAUNCHED();
-    k_zero_cols<<<g, kBlock, 0, s>>>(c.n, B, c.s_cc.p, c.x64.p);
+    klaunch(k_zero_cols, dim3(g), dim3(kBlock), 0, s, c.n, B, c.s_cc.p, c.x64.p);
     LCMG_LAUNCHED();
     const int nb = true_residual(c.part_x.p);
-    k_sum_parts<<<1, kScalarThreads, 0, s>>>(B, nb, c.part_x.p, c.s_rrtrue.p);
+    klaunch(k_sum_parts, dim3(1), dim3(kScalarThreads), 0, s, B, nb, c.part_x.p, c.s_rrtrue.p);
     LCMG_LAUNCHED();
-    k_init_state<<<1, kBlock, 0, s>>>(B, c.prm.tol, c.s_cc.p, c.s_rrtrue.p, st);
+    klaunch(k_init_state, dim3(1), dim3(kBlock), 0, s, B, c.prm.tol, c.s_cc.p, c.s_rrtrue.p, st);
     LCMG_LAUNCHED();
     // r = (T) r64 for every column
     LCMG_CUDA(cudaMemsetAsync(c.s_flag.p, 0, sizeof(int) * B, s));
     {
       std::vector<int> ones(B, 1);
       LCMG_CUDA(cudaMemcpyAsync(c.s_flag.p, ones.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
-      k_take_residual<T><<<g, kBlock, 0, s>>>(c.n, B, c.s_flag.p, c.r64.p, tp(c.r));
+      klaunch(k_take_residual<T>, dim3(g), dim3(kBlock), 0, s, c.n, B, c.s_flag.p, c.r64.p, tp(c.r));
       LCMG_LAUNCHED();
       LCMG_CUDA(cudaStreamSynchronize(s));
     }
     if (!std::is_same<T, double>::value) LCMG_CUDA(cudaMemsetAsync(c.xlo.p, 0, sizeof(float) * c.n * B, s));
     // z = B r ; p = z ; rz = r.z   (for every column; frozen ones are unaffected)
     const int nbz = vcycle(tp(c.r), tp(c.z), c.part_rz.p);
-    k_sum_parts<<<1, kScalarThreads, 0, s>>>(B, nbz, c.part_rz.p, c.s_rz.p);
+    klaunch(k_sum_parts, dim3(1), dim3(kScalarThreads), 0, s, B, nbz, c.part_rz.p, c.s_rz.p);
     LCMG_LAUNCHED();
     launch_copy_cols<T>(c.n, B, nullptr, tp(c.z), tp(c.p), c.maxblk, s);
     int64_t batch_its = 0;
@@ -525,7 +709,7 @@ struct Batch {
       const int64_t l0 = launch_counter();
       LCMG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
       try {
-        for (int i = 0; i < every; ++i) iterate_once();
+        for (int i = 0; i < every; ++i) iterate_once(i == 0);
       } catch (...) {
         cudaStreamEndCapture(s, &graph);
         if (graph) cudaGraphDestroy(graph);
@@ -550,7 +734,7 @@ struct Batch {
         launch_counter() += per_block;
       } else {
         c.tev_used = 0;
-        for (int i = 0; i < every; ++i) iterate_once();
+        for (int i = 0; i < every; ++i) iterate_once(i == 0);
       }
       batch_its += every;
       read_counters();
@@ -566,7 +750,7 @@ struct Batch {
     }
     if (!std::is_same<T, double>::value) {
       const int gg = (int)std::min<int64_t>(((int64_t)c.n * B + kBlock - 1) / kBlock, c.maxblk);
-      k_flush_x<<<gg, kBlock, 0, s>>>((int64_t)c.n * B, c.xlo.p, c.x64.p);
+      klaunch(k_flush_x, dim3(gg), dim3(kBlock), 0, s, (int64_t)c.n * B, c.xlo.p, c.x64.p);
       LCMG_LAUNCHED();
     }
     LCMG_CUDA(cudaEventRecord(e1, s));
@@ -605,7 +789,8 @@ static void op_bytes(const lcmg_ctx& c, int B, int64_t* first, int64_t* second) 
 }
 
 template <class T>
-int Batch<T>::apply_K(const T* P, T* Q, double* part) {
+int Batch<T>::apply_K(const T* P, T* Q, double* part, const ScalarFold* fold, bool* folded) {
+  if (folded) *folded = false;
   T* Y = tp(c.y);
   mark();
   int nb;
@@ -620,7 +805,7 @@ int Batch<T>::apply_K(const T* P, T* Q, double* part) {
       nb = launch_spmm<float, float, float, 1>(at, c.vT32.p, reinterpret_cast<const float*>(Y),
                                                reinterpret_cast<float*>(Q), view<float>(c, 0).fine_op(),
                                                reinterpret_cast<const float*>(P), nullptr, c.lam2.p, nullptr,
-                                               part, c.maxblk, s);
+                                               part, c.maxblk, s, fold);
     } else {
       const double* Pd = reinterpret_cast<const double*>(P);
       double* Qd = reinterpret_cast<double*>(Q);
@@ -630,23 +815,24 @@ int Batch<T>::apply_K(const T* P, T* Q, double* part) {
                                                nullptr, c.maxblk, s);
         mark();
         nb = launch_spmm<double, double, double, 1>(at, c.vT64.p, Yd, Qd, fop64(), Pd, nullptr, c.lam2.p,
-                                                    nullptr, part, c.maxblk, s);
+                                                    nullptr, part, c.maxblk, s, fold);
       } else {
         launch_spmm<float, double, double, 0>(a, c.v32.p, Pd, Yd, fop64(), nullptr, nullptr, nullptr, nullptr,
                                               nullptr, c.maxblk, s);
         mark();
         nb = launch_spmm<float, double, double, 1>(at, c.vT32.p, Yd, Qd, fop64(), Pd, nullptr, c.lam2.p,
-                                                   nullptr, part, c.maxblk, s);
+                                                   nullptr, part, c.maxblk, s, fold);
       }
     }
+    if (folded) *folded = fold != nullptr;
   } else {
     // PSF operator
     nb = grid_for(c.n, B, c.maxblk);
     PsfArgs pa = psf();
-    k_psf_forward<T, 0><<<nb, kBlock, 0, s>>>(pa, psfT(), B, P, Y, nullptr, 1, 1, nullptr);
+    klaunch(k_psf_forward<T, 0>, dim3(nb), dim3(kBlock), 0, s, pa, psfT(), B, P, Y, nullptr, 1, 1, nullptr);
     LCMG_LAUNCHED();
     mark();
-    k_psf_normal<T, T, 1><<<nb, kBlock, 0, s>>>(pa, psfT(), B, Y, fop(), P, nullptr, c.lam2.p, Q, part);
+    klaunch(k_psf_normal<T, T, 1>, dim3(nb), dim3(kBlock), 0, s, pa, psfT(), B, Y, fop(), P, nullptr, c.lam2.p, Q, part);
     LCMG_LAUNCHED();
   }
   mark();
@@ -672,9 +858,9 @@ int Batch<T>::true_residual(double* part) {
   }
   const int g = grid_for(c.n, B, c.maxblk);
   PsfArgs pa = psf();
-  k_psf_forward<double, 0><<<g, kBlock, 0, s>>>(pa, c.psf64.p, B, c.x64.p, Y, nullptr, 1, 1, nullptr);
+  klaunch(k_psf_forward<double, 0>, dim3(g), dim3(kBlock), 0, s, pa, c.psf64.p, B, c.x64.p, Y, nullptr, 1, 1, nullptr);
   LCMG_LAUNCHED();
-  k_psf_normal<double, double, 3><<<g, kBlock, 0, s>>>(pa, c.psf64.p, B, Y, fop64(), c.x64.p, c.c64.p, c.lam2.p,
+  klaunch(k_psf_normal<double, double, 3>, dim3(g), dim3(kBlock), 0, s, pa, c.psf64.p, B, Y, fop64(), c.x64.p, c.c64.p, c.lam2.p,
                                                        c.r64.p, part);
   LCMG_LAUNCHED();
   return g;
@@ -687,8 +873,7 @@ int Batch<T>::true_residual(double* part) {
 static void compute_rhs(lcmg_ctx& c, int nrhs) {
   double* cv = c.cvec.need((size_t)c.n * nrhs);
   if (c.fwd == 1) {
-    SpmmArgs a{};
-    a.rows = c.n; a.rp = c.rpT.p; a.ci = c.ciT.p; a.B = nrhs; a.c0 = 0; a.nb = nrhs; a.nl = 1; a.nrhs = 1;
+    SpmmArgs a = csr_args(c, true, nrhs);
     FineOp<double> f = view<double>(c, 0).fine_op();
     if (c.vdtype == 1)
       launch_spmm<double, double, double, 0>(a, c.vT64.p, c.bvec.p, cv, f, nullptr, nullptr, nullptr, nullptr,
@@ -699,7 +884,7 @@ static void compute_rhs(lcmg_ctx& c, int nrhs) {
   } else {
     PsfArgs pa{};
     pa.nv = c.nv; pa.nh = c.nh; pa.rv = c.rv; pa.rh = c.rh; pa.psf = c.psf64.p;
-    k_psf_rhs<<<grid_for(c.n, nrhs, c.maxblk), kBlock, 0, c.stream>>>(pa, nrhs, c.bvec.p, cv);
+    klaunch(k_psf_rhs, dim3(grid_for(c.n, nrhs, c.maxblk)), dim3(kBlock), 0, c.stream, pa, nrhs, c.bvec.p, cv);
     LCMG_LAUNCHED();
   }
 }
@@ -731,9 +916,9 @@ static void solve_columns(lcmg_ctx& c, const std::vector<ColSpec>& cols, int nrh
   LCMG_CUDA(cudaMemcpyAsync(dptr, hptr.data(), sizeof(double*) * 2 * B, cudaMemcpyHostToDevice, s));
   LCMG_CUDA(cudaMemcpyAsync(dmap, hmap.data(), sizeof(int) * B, cudaMemcpyHostToDevice, s));
   const int gn = grid_for(c.n, B, c.maxblk);
-  k_gather_cols<<<gn, kBlock, 0, s>>>(c.n, B, dptr, c.x64.p);
+  klaunch(k_gather_cols, dim3(gn), dim3(kBlock), 0, s, c.n, B, dptr, c.x64.p);
   LCMG_LAUNCHED();
-  k_gather_map<<<gn, kBlock, 0, s>>>(c.n, B, nrhs, dmap, c.cvec.p, c.c64.p);
+  klaunch(k_gather_map, dim3(gn), dim3(kBlock), 0, s, c.n, B, nrhs, dmap, c.cvec.p, c.c64.p);
   LCMG_LAUNCHED();
   LCMG_CUDA(cudaStreamSynchronize(s));  // host tables must outlive the copies
   std::vector<double> lam(B);
@@ -746,16 +931,16 @@ static void solve_columns(lcmg_ctx& c, const std::vector<ColSpec>& cols, int nrh
     b.run(lam);
   }
   // outputs: x (the pointer table is unchanged since the gather)
-  k_scatter_cols<<<gn, kBlock, 0, s>>>(c.n, B, c.x64.p, c.colptr.p + B);
+  klaunch(k_scatter_cols, dim3(gn), dim3(kBlock), 0, s, c.n, B, c.x64.p, c.colptr.p + B);
   LCMG_LAUNCHED();
   // rho = ||A x - b|| per column: b of each column's right-hand side
   double* bcol = c.y64.p;  // [m][B]
-  k_gather_map<<<grid_for(c.m, B, c.maxblk), kBlock, 0, s>>>(c.m, B, nrhs, dmap, c.bvec.p, bcol);
+  klaunch(k_gather_map, dim3(grid_for(c.m, B, c.maxblk)), dim3(kBlock), 0, s, c.m, B, nrhs, dmap, c.bvec.p, bcol);
   LCMG_LAUNCHED();
   int nb;
   if (c.fwd == 1) {
-    SpmmArgs a{};
-    a.rows = c.m; a.rp = c.rp.p; a.ci = c.ci.p; a.B = B; a.c0 = 0; a.nb = B; a.nl = 1; a.nrhs = B;
+    SpmmArgs a = csr_args(c, false, B);
+    a.nrhs = B;
     FineOp<double> f = view<double>(c, 0).fine_op();
     if (c.vdtype == 1)
       nb = launch_spmm<double, double, double, 2>(a, c.v64.p, c.x64.p, (double*)nullptr, f, nullptr, nullptr,
@@ -767,23 +952,24 @@ static void solve_columns(lcmg_ctx& c, const std::vector<ColSpec>& cols, int nrh
     PsfArgs pa{};
     pa.nv = c.nv; pa.nh = c.nh; pa.rv = c.rv; pa.rh = c.rh; pa.psf = c.psf64.p;
     nb = grid_for(c.n, B, c.maxblk);
-    k_psf_forward<double, 2><<<nb, kBlock, 0, s>>>(pa, c.psf64.p, B, c.x64.p, nullptr, bcol, 1, B, c.part_x.p);
+    klaunch(k_psf_forward<double, 2>, dim3(nb), dim3(kBlock), 0, s, pa, c.psf64.p, B, c.x64.p, nullptr, bcol, 1, B, c.part_x.p);
     LCMG_LAUNCHED();
   }
-  k_sum_parts<<<1, kScalarThreads, 0, s>>>(B, nb, c.part_x.p, c.s_out.p);
+  klaunch(k_sum_parts, dim3(1), dim3(kScalarThreads), 0, s, B, nb, c.part_x.p, c.s_out.p);
   LCMG_LAUNCHED();
   std::vector<double> hr(B), he(B);
   LCMG_CUDA(cudaMemcpyAsync(hr.data(), c.s_out.p, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
   const int g = grid_for(c.n, B, c.maxblk);
-  k_seminorm<<<g, kBlock, 0, s>>>(c.nv, c.nh, B, c.ws.p, c.we.p, c.x64.p, c.part_x.p);
+  klaunch(k_seminorm, dim3(g), dim3(kBlock), 0, s, c.nv, c.nh, B, c.ws.p, c.we.p, c.x64.p, c.part_x.p);
   LCMG_LAUNCHED();
-  k_sum_parts<<<1, kScalarThreads, 0, s>>>(B, g, c.part_x.p, c.s_out.p);
+  klaunch(k_sum_parts, dim3(1), dim3(kScalarThreads), 0, s, B, g, c.part_x.p, c.s_out.p);
   LCMG_LAUNCHED();
   LCMG_CUDA(cudaMemcpyAsync(he.data(), c.s_out.p, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
   std::vector<int> hi(B), hs(B);
   LCMG_CUDA(cudaMemcpyAsync(hi.data(), c.s_iters.p, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
   LCMG_CUDA(cudaMemcpyAsync(hs.data(), c.s_status.p, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
   LCMG_CUDA(cudaStreamSynchronize(s));
+  check_spmm_err(c);
   for (int j = 0; j < B; ++j) {
     if (rho) rho[j] = std::sqrt(hr[j]);
     if (eta) eta[j] = std::sqrt(he[j]);
@@ -857,7 +1043,7 @@ static void upload_b(lcmg_ctx& c, int nrhs, const double* b, bool dev) {
     LCMG_CUDA(cudaMemcpyAsync(tmp, b, sizeof(double) * c.m * nrhs, cudaMemcpyHostToDevice, c.stream));
     src = tmp;
   }
-  k_planar_to_inter<<<grid_for(c.m, nrhs, c.maxblk), kBlock, 0, c.stream>>>(c.m, nrhs, src, bi);
+  klaunch(k_planar_to_inter, dim3(grid_for(c.m, nrhs, c.maxblk)), dim3(kBlock), 0, c.stream, c.m, nrhs, src, bi);
   LCMG_LAUNCHED();
   compute_rhs(c, nrhs);
   LCMG_CUDA(cudaStreamSynchronize(c.stream));
@@ -898,9 +1084,9 @@ static void update_weights_dev(lcmg_ctx& c, const double* xs, double q, double d
   const int g = (int)std::min<int64_t>((c.ne + kBlock - 1) / kBlock, c.maxblk);
   double* absv = c.absv.need(c.ne);
   double* bmax = c.bmax.need(g);
-  k_weighted_grad<<<g, kBlock, 0, c.stream>>>(c.nv, c.nh, c.d.p, xs, absv, bmax);
+  klaunch(k_weighted_grad, dim3(g), dim3(kBlock), 0, c.stream, c.nv, c.nh, c.d.p, xs, absv, bmax);
   LCMG_LAUNCHED();
-  k_weight_apply<<<g, kBlock, 0, c.stream>>>(c.ne, g, bmax, absv, q, dmin, c.d.p);
+  klaunch(k_weight_apply, dim3(g), dim3(kBlock), 0, c.stream, c.ne, g, bmax, absv, q, dmin, c.d.p);
   LCMG_LAUNCHED();
   refresh_fine(c);
 }
@@ -1032,6 +1218,11 @@ void lcmg_default_params(lcmg_params* p) {
   p->check_every = 16;
   p->graphs = 1;
   p->timing = 0;
+  p->fused = 0;
+  p->tail_points = 0;
+  p->pdl = 0;
+  p->fold = 0;
+  p->staged = 0;
 }
 
 const char* lcmg_last_error(void) { return lcmg::g_err.c_str(); }
@@ -1061,6 +1252,10 @@ int lcmg_create(lcmg_ctx** out, int device, void* stream, const lcmg_params* p) 
   LCMG_CUDA(cudaGetDeviceProperties(&prop, device));
   c->sms = prop.multiProcessorCount;
   c->maxblk = std::min(lcmg::kMaxBlocks, c->sms * 8);
+  LCMG_CUDA(cudaMemset(c->spmm_err.need(1), 0, sizeof(int)));
+  // opt the staged SpMM kernels into their shared memory here, outside any
+  // stream capture
+  lcmg::prepare_spmm_staged();
   *out = c;
   API_END
 }
@@ -1141,29 +1336,41 @@ int lcmg_set_forward_csr(lcmg_ctx* ctx, int64_t m, int64_t n, const int64_t* row
   ctx->nnz = nnz;
   ctx->vdtype = val_dtype;
   cudaStream_t s = ctx->stream;
-  LCMG_CUDA(cudaMemcpy(ctx->rp.need(m + 1), row_ptr, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice));
-  LCMG_CUDA(cudaMemcpy(ctx->ci.need(nnz), col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
-  LCMG_CUDA(cudaMemcpy(ctx->rpT.need(n + 1), rpT.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
-  LCMG_CUDA(cudaMemcpy(ctx->ciT.need(nnz), ciT.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
+  // row pointers padded: a staged copy of rp may read one entry past rp[m]
+  LCMG_CUDA(cudaMemcpy(ctx->rp.need(m + 1 + lcmg::kCsrPad), row_ptr, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice));
+  LCMG_CUDA(cudaMemcpy(ctx->ci.need(nnz + lcmg::kCsrPad), col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
+  LCMG_CUDA(cudaMemcpy(ctx->rpT.need(n + 1 + lcmg::kCsrPad), rpT.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
+  LCMG_CUDA(cudaMemcpy(ctx->ciT.need(nnz + lcmg::kCsrPad), ciT.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
   std::vector<float> tmpf(nnz);
   if (val_dtype == 0) {
-    LCMG_CUDA(cudaMemcpy(ctx->v32.need(nnz), vf, sizeof(float) * nnz, cudaMemcpyHostToDevice));
+    LCMG_CUDA(cudaMemcpy(ctx->v32.need(nnz + lcmg::kCsrPad), vf, sizeof(float) * nnz, cudaMemcpyHostToDevice));
   } else {
-    LCMG_CUDA(cudaMemcpy(ctx->v64.need(nnz), vd, sizeof(double) * nnz, cudaMemcpyHostToDevice));
-    LCMG_CUDA(cudaMemcpy(ctx->vT64.need(nnz), vT.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
+    LCMG_CUDA(cudaMemcpy(ctx->v64.need(nnz + lcmg::kCsrPad), vd, sizeof(double) * nnz, cudaMemcpyHostToDevice));
+    LCMG_CUDA(cudaMemcpy(ctx->vT64.need(nnz + lcmg::kCsrPad), vT.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
     for (int64_t k = 0; k < nnz; ++k) tmpf[k] = (float)vd[k];
-    LCMG_CUDA(cudaMemcpy(ctx->v32.need(nnz), tmpf.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice));
+    LCMG_CUDA(cudaMemcpy(ctx->v32.need(nnz + lcmg::kCsrPad), tmpf.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice));
   }
   for (int64_t k = 0; k < nnz; ++k) tmpf[k] = (float)vT[k];
-  LCMG_CUDA(cudaMemcpy(ctx->vT32.need(nnz), tmpf.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice));
+  LCMG_CUDA(cudaMemcpy(ctx->vT32.need(nnz + lcmg::kCsrPad), tmpf.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice));
+  // zero padding after the last nonzero (read by the 16-byte vector loads)
+  LCMG_CUDA(cudaMemset(ctx->ci.p + nnz, 0, sizeof(int32_t) * lcmg::kCsrPad));
+  LCMG_CUDA(cudaMemset(ctx->ciT.p + nnz, 0, sizeof(int32_t) * lcmg::kCsrPad));
+  LCMG_CUDA(cudaMemset(ctx->v32.p + nnz, 0, sizeof(float) * lcmg::kCsrPad));
+  LCMG_CUDA(cudaMemset(ctx->vT32.p + nnz, 0, sizeof(float) * lcmg::kCsrPad));
+  if (val_dtype == 1) {
+    LCMG_CUDA(cudaMemset(ctx->v64.p + nnz, 0, sizeof(double) * lcmg::kCsrPad));
+    LCMG_CUDA(cudaMemset(ctx->vT64.p + nnz, 0, sizeof(double) * lcmg::kCsrPad));
+  }
+  ctx->nck = lcmg::build_chunks(row_ptr, m, ctx->ck_row, ctx->ck_nz);
+  ctx->nckT = lcmg::build_chunks(rpT.data(), n, ctx->ckT_row, ctx->ckT_nz);
   // diag(A^T A): sums of squares along the rows of A^T
   const int g = (int)std::min<int64_t>((n * 32 + lcmg::kBlock - 1) / lcmg::kBlock, ctx->maxblk);
   if (val_dtype == 1)
-    lcmg::k_diag_ata<double><<<g, lcmg::kBlock, 0, s>>>(n, ctx->rpT.p, ctx->vT64.p, ctx->diag.need(n));
+    klaunch(lcmg::k_diag_ata<double>, dim3(g), dim3(lcmg::kBlock), 0, s, n, ctx->rpT.p, ctx->vT64.p, ctx->diag.need(n));
   else
-    lcmg::k_diag_ata<float><<<g, lcmg::kBlock, 0, s>>>(n, ctx->rpT.p, ctx->vT32.p, ctx->diag.need(n));
+    klaunch(lcmg::k_diag_ata<float>, dim3(g), dim3(lcmg::kBlock), 0, s, n, ctx->rpT.p, ctx->vT32.p, ctx->diag.need(n));
   LCMG_LAUNCHED();
-  lcmg::k_convert<double, float><<<g, lcmg::kBlock, 0, s>>>(n, ctx->diag.p, ctx->diag32.need(n));
+  klaunch(lcmg::k_convert<double, float>, dim3(g), dim3(lcmg::kBlock), 0, s, n, ctx->diag.p, ctx->diag32.need(n));
   LCMG_LAUNCHED();
   LCMG_CUDA(cudaStreamSynchronize(s));
   ctx->fwd = 1;
@@ -1189,9 +1396,9 @@ int lcmg_set_forward_stencil(lcmg_ctx* ctx, int32_t kh, int32_t kw, const double
   lcmg::PsfArgs pa{};
   pa.nv = ctx->nv; pa.nh = ctx->nh; pa.rv = ctx->rv; pa.rh = ctx->rh; pa.psf = ctx->psf64.p;
   const int g = (int)std::min<int64_t>((ctx->n + lcmg::kBlock - 1) / lcmg::kBlock, ctx->maxblk);
-  lcmg::k_psf_diag<<<g, lcmg::kBlock, 0, ctx->stream>>>(pa, ctx->diag.need(ctx->n));
+  klaunch(lcmg::k_psf_diag, dim3(g), dim3(lcmg::kBlock), 0, ctx->stream, pa, ctx->diag.need(ctx->n));
   LCMG_LAUNCHED();
-  lcmg::k_convert<double, float><<<g, lcmg::kBlock, 0, ctx->stream>>>(ctx->n, ctx->diag.p, ctx->diag32.need(ctx->n));
+  klaunch(lcmg::k_convert<double, float>, dim3(g), dim3(lcmg::kBlock), 0, ctx->stream, ctx->n, ctx->diag.p, ctx->diag32.need(ctx->n));
   LCMG_LAUNCHED();
   LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->fwd = 2;
@@ -1409,17 +1616,18 @@ int lcmg_apply_normal_dev(lcmg_ctx* ctx, int32_t n_cols, const double* lambda, c
   for (int j = 0; j < B; ++j) l2[j] = lambda[j] * lambda[j];
   LCMG_CUDA(cudaMemcpy(ctx->lam2.p, l2.data(), sizeof(double) * B, cudaMemcpyHostToDevice));
   const int g = lcmg::grid_for(ctx->n, B, ctx->maxblk);
-  lcmg::k_planar_to_inter<<<g, lcmg::kBlock, 0, ctx->stream>>>(ctx->n, B, x_dev, ctx->x64.p);
+  klaunch(lcmg::k_planar_to_inter, dim3(g), dim3(lcmg::kBlock), 0, ctx->stream, ctx->n, B, x_dev, ctx->x64.p);
   LCMG_LAUNCHED();
   LCMG_CUDA(cudaMemsetAsync(ctx->c64.p, 0, sizeof(double) * ctx->n * B, ctx->stream));
   lcmg::Batch<double> b(*ctx, B);
   b.true_residual(ctx->part_x.p);  // r64 = 0 - K x
   const int ge = (int)std::min<int64_t>(((int64_t)ctx->n * B + lcmg::kBlock - 1) / lcmg::kBlock, ctx->maxblk);
-  lcmg::k_negate<<<ge, lcmg::kBlock, 0, ctx->stream>>>((int64_t)ctx->n * B, ctx->r64.p);
+  klaunch(lcmg::k_negate, dim3(ge), dim3(lcmg::kBlock), 0, ctx->stream, (int64_t)ctx->n * B, ctx->r64.p);
   LCMG_LAUNCHED();
-  lcmg::k_inter_to_planar<<<g, lcmg::kBlock, 0, ctx->stream>>>(ctx->n, B, ctx->r64.p, y_dev);
+  klaunch(lcmg::k_inter_to_planar, dim3(g), dim3(lcmg::kBlock), 0, ctx->stream, ctx->n, B, ctx->r64.p, y_dev);
   LCMG_LAUNCHED();
   LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
+  lcmg::check_spmm_err(*ctx);
   API_END
 }
 
@@ -1437,24 +1645,24 @@ int lcmg_apply_vcycle_dev(lcmg_ctx* ctx, int32_t n_cols, const double* lambda, c
   if (ctx->prm.precision == LCMG_PREC_FP64) {
     lcmg::Batch<double> b(*ctx, B);
     b.setup(lam);
-    lcmg::k_planar_to_inter<<<g, lcmg::kBlock, 0, ctx->stream>>>(ctx->n, B, r_dev, reinterpret_cast<double*>(ctx->r.p));
+    klaunch(lcmg::k_planar_to_inter, dim3(g), dim3(lcmg::kBlock), 0, ctx->stream, ctx->n, B, r_dev, reinterpret_cast<double*>(ctx->r.p));
     LCMG_LAUNCHED();
     b.vcycle(reinterpret_cast<double*>(ctx->r.p), reinterpret_cast<double*>(ctx->z.p), ctx->part_x.p);
-    lcmg::k_inter_to_planar<<<g, lcmg::kBlock, 0, ctx->stream>>>(ctx->n, B, reinterpret_cast<double*>(ctx->z.p), z_dev);
+    klaunch(lcmg::k_inter_to_planar, dim3(g), dim3(lcmg::kBlock), 0, ctx->stream, ctx->n, B, reinterpret_cast<double*>(ctx->z.p), z_dev);
     LCMG_LAUNCHED();
   } else {
     lcmg::Batch<float> b(*ctx, B);
     b.setup(lam);
-    lcmg::k_planar_to_inter<<<g, lcmg::kBlock, 0, ctx->stream>>>(ctx->n, B, r_dev, ctx->r64.p);
+    klaunch(lcmg::k_planar_to_inter, dim3(g), dim3(lcmg::kBlock), 0, ctx->stream, ctx->n, B, r_dev, ctx->r64.p);
     LCMG_LAUNCHED();
-    lcmg::k_convert<double, float><<<g, lcmg::kBlock, 0, ctx->stream>>>((int64_t)ctx->n * B, ctx->r64.p,
+    klaunch(lcmg::k_convert<double, float>, dim3(g), dim3(lcmg::kBlock), 0, ctx->stream, (int64_t)ctx->n * B, ctx->r64.p,
                                                                          reinterpret_cast<float*>(ctx->r.p));
     LCMG_LAUNCHED();
     b.vcycle(reinterpret_cast<float*>(ctx->r.p), reinterpret_cast<float*>(ctx->z.p), ctx->part_x.p);
-    lcmg::k_convert<float, double><<<g, lcmg::kBlock, 0, ctx->stream>>>((int64_t)ctx->n * B,
+    klaunch(lcmg::k_convert<float, double>, dim3(g), dim3(lcmg::kBlock), 0, ctx->stream, (int64_t)ctx->n * B,
                                                                          reinterpret_cast<float*>(ctx->z.p), ctx->r64.p);
     LCMG_LAUNCHED();
-    lcmg::k_inter_to_planar<<<g, lcmg::kBlock, 0, ctx->stream>>>(ctx->n, B, ctx->r64.p, z_dev);
+    klaunch(lcmg::k_inter_to_planar, dim3(g), dim3(lcmg::kBlock), 0, ctx->stream, ctx->n, B, ctx->r64.p, z_dev);
     LCMG_LAUNCHED();
   }
   LCMG_CUDA(cudaStreamSynchronize(ctx->stream));

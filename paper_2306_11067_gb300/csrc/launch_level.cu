@@ -9,9 +9,9 @@ void launch_dinv(const LevelView<T>& L, int B, const double* lam2, int smoother,
                  T* dinv, int max_blocks, cudaStream_t s) {
   const int g = grid_for(L.n, B, max_blocks);
   if (L.fine)
-    k_dinv<FineOp<T>, T><<<g, kBlock, 0, s>>>(L.fine_op(), L.n, B, lam2, smoother, omega, dinv);
+    klaunch(k_dinv<FineOp<T>, T>, dim3(g), dim3(kBlock), 0, s, L.fine_op(), L.n, B, lam2, smoother, omega, dinv);
   else
-    k_dinv<CoarseOp<T>, T><<<g, kBlock, 0, s>>>(L.coarse_op(), L.n, B, lam2, smoother, omega, dinv);
+    klaunch(k_dinv<CoarseOp<T>, T>, dim3(g), dim3(kBlock), 0, s, L.coarse_op(), L.n, B, lam2, smoother, omega, dinv);
   LCMG_LAUNCHED();
 }
 
@@ -20,21 +20,22 @@ void launch_smooth_zero(const LevelView<T>& L, int B, const T* lam2, const T* di
                         T* z, int two, int max_blocks, cudaStream_t s) {
   const int g = grid_for(L.n, B, max_blocks);
   if (L.fine)
-    k_smooth_zero<FineOp<T>, T><<<g, kBlock, 0, s>>>(L.fine_op(), L.n, B, lam2, dinv, r, z, two);
+    klaunch(k_smooth_zero<FineOp<T>, T>, dim3(g), dim3(kBlock), 0, s, L.fine_op(), L.n, B, lam2, dinv, r, z, two);
   else
-    k_smooth_zero<CoarseOp<T>, T><<<g, kBlock, 0, s>>>(L.coarse_op(), L.n, B, lam2, dinv, r, z, two);
+    klaunch(k_smooth_zero<CoarseOp<T>, T>, dim3(g), dim3(kBlock), 0, s, L.coarse_op(), L.n, B, lam2, dinv, r, z, two);
   LCMG_LAUNCHED();
 }
 
 template <class T>
 int launch_smooth(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const T* r,
                   const T* zin, T* zout, const int* active, double* part, int max_blocks,
-                  cudaStream_t s) {
+                  cudaStream_t s, const ScalarFold* fold) {
+  const ScalarFold f = fold ? *fold : ScalarFold{};
   const int g = grid_for(L.n, B, max_blocks);
   if (L.fine)
-    k_smooth<FineOp<T>, T><<<g, kBlock, 0, s>>>(L.fine_op(), L.n, B, lam2, dinv, r, zin, zout, active, part);
+    klaunch(k_smooth<FineOp<T>, T>, dim3(g), dim3(kBlock), 0, s, L.fine_op(), L.n, B, lam2, dinv, r, zin, zout, active, part, f);
   else
-    k_smooth<CoarseOp<T>, T><<<g, kBlock, 0, s>>>(L.coarse_op(), L.n, B, lam2, dinv, r, zin, zout, active, part);
+    klaunch(k_smooth<CoarseOp<T>, T>, dim3(g), dim3(kBlock), 0, s, L.coarse_op(), L.n, B, lam2, dinv, r, zin, zout, active, part, f);
   LCMG_LAUNCHED();
   return g;
 }
@@ -44,23 +45,23 @@ void launch_residual(const LevelView<T>& L, int B, const T* lam2, const T* r, co
                      int max_blocks, cudaStream_t s) {
   const int g = grid_for(L.n, B, max_blocks);
   if (L.fine)
-    k_residual<FineOp<T>, T><<<g, kBlock, 0, s>>>(L.fine_op(), L.n, B, lam2, r, z, res);
+    klaunch(k_residual<FineOp<T>, T>, dim3(g), dim3(kBlock), 0, s, L.fine_op(), L.n, B, lam2, r, z, res);
   else
-    k_residual<CoarseOp<T>, T><<<g, kBlock, 0, s>>>(L.coarse_op(), L.n, B, lam2, r, z, res);
+    klaunch(k_residual<CoarseOp<T>, T>, dim3(g), dim3(kBlock), 0, s, L.coarse_op(), L.n, B, lam2, r, z, res);
   LCMG_LAUNCHED();
 }
 
 template <class T>
 void launch_restrict(int nvc, int nhc, int B, const T* rf, T* rc, int max_blocks, cudaStream_t s) {
   const int g = grid_for((int64_t)nvc * nhc, B, max_blocks);
-  k_restrict<T><<<g, kBlock, 0, s>>>(nvc, nhc, B, rf, rc);
+  klaunch(k_restrict<T>, dim3(g), dim3(kBlock), 0, s, nvc, nhc, B, rf, rc);
   LCMG_LAUNCHED();
 }
 
 template <class T>
 void launch_prolong_add(int nvc, int nhc, int B, const T* ec, T* zf, int max_blocks, cudaStream_t s) {
   const int g = grid_for((int64_t)4 * nvc * nhc, B, max_blocks);
-  k_prolong_add<T><<<g, kBlock, 0, s>>>(nvc, nhc, B, ec, zf);
+  klaunch(k_prolong_add<T>, dim3(g), dim3(kBlock), 0, s, nvc, nhc, B, ec, zf);
   LCMG_LAUNCHED();
 }
 
@@ -68,7 +69,7 @@ template <class T>
 void launch_coarse_solve(int nc, int B, const double* kinv, const T* rc, T* ec, cudaStream_t s) {
   const size_t smem = sizeof(double) * (size_t)nc;
   dim3 grid((unsigned)((nc + kBlock / 32 - 1) / (kBlock / 32)), (unsigned)B);
-  k_coarse_solve<T><<<grid, kBlock, smem, s>>>(nc, B, kinv, rc, ec);
+  klaunch(k_coarse_solve<T>, dim3(grid), dim3(kBlock), smem, s, nc, B, kinv, rc, ec);
   LCMG_LAUNCHED();
 }
 
@@ -78,11 +79,11 @@ void launch_dense_setup(const LevelView<double>& L, int B, const double* lam2, d
   LCMG_CUDA(cudaMemsetAsync(M, 0, sizeof(double) * (size_t)B * nc * nc, s));
   const int g = grid_for(nc, B, max_blocks);
   if (L.fine)
-    k_dense_assemble<FineOp<double>><<<g, kBlock, 0, s>>>(L.fine_op(), nc, B, lam2, M);
+    klaunch(k_dense_assemble<FineOp<double>>, dim3(g), dim3(kBlock), 0, s, L.fine_op(), nc, B, lam2, M);
   else
-    k_dense_assemble<CoarseOp<double>><<<g, kBlock, 0, s>>>(L.coarse_op(), nc, B, lam2, M);
+    klaunch(k_dense_assemble<CoarseOp<double>>, dim3(g), dim3(kBlock), 0, s, L.coarse_op(), nc, B, lam2, M);
   LCMG_LAUNCHED();
-  k_cholesky_inverse<<<B, kBlock, 0, s>>>((int)nc, M, W, K, info);
+  klaunch(k_cholesky_inverse, dim3(B), dim3(kBlock), 0, s, (int)nc, M, W, K, info);
   LCMG_LAUNCHED();
 }
 
@@ -90,7 +91,7 @@ void launch_galerkin(const RapIn& in, int nvc, int nhc, double* out, int max_blo
   const int64_t work = (int64_t)nvc * nhc * kStencil;
   int64_t g = (work + kBlock - 1) / kBlock;
   if (g > max_blocks) g = max_blocks;
-  k_galerkin<<<(unsigned)g, kBlock, 0, s>>>(in, nvc, nhc, out);
+  klaunch(k_galerkin, dim3((unsigned)g), dim3(kBlock), 0, s, in, nvc, nhc, out);
   LCMG_LAUNCHED();
 }
 
@@ -98,7 +99,7 @@ template <class T, class TX>
 int launch_update_xr(int64_t n, int B, const ColState& st, const T* p, const T* q, TX* x, T* r,
                      double* part, int max_blocks, cudaStream_t s) {
   const int g = grid_for(n, B, max_blocks);
-  k_update_xr<T, TX><<<g, kBlock, 0, s>>>(n, B, st, p, q, x, r, part);
+  klaunch(k_update_xr<T, TX>, dim3(g), dim3(kBlock), 0, s, n, B, st, p, q, x, r, part);
   LCMG_LAUNCHED();
   return g;
 }
@@ -107,7 +108,7 @@ template <class T>
 void launch_update_p(int64_t n, int B, const ColState& st, const T* z, T* p, int max_blocks,
                      cudaStream_t s) {
   const int g = grid_for(n, B, max_blocks);
-  k_update_p<T><<<g, kBlock, 0, s>>>(n, B, st, z, p);
+  klaunch(k_update_p<T>, dim3(g), dim3(kBlock), 0, s, n, B, st, z, p);
   LCMG_LAUNCHED();
 }
 
@@ -115,7 +116,7 @@ template <class T>
 void launch_copy_cols(int64_t n, int B, const int* flag, const T* src, T* dst, int max_blocks,
                       cudaStream_t s) {
   const int g = grid_for(n, B, max_blocks);
-  k_copy_cols<T><<<g, kBlock, 0, s>>>(n, B, flag, src, dst);
+  klaunch(k_copy_cols<T>, dim3(g), dim3(kBlock), 0, s, n, B, flag, src, dst);
   LCMG_LAUNCHED();
 }
 
@@ -125,7 +126,8 @@ void launch_copy_cols(int64_t n, int B, const int* flag, const T* src, T* dst, i
   template void launch_smooth_zero<T>(const LevelView<T>&, int, const T*, const T*, const T*,   \
                                       T*, int, int, cudaStream_t);                              \
   template int launch_smooth<T>(const LevelView<T>&, int, const T*, const T*, const T*,         \
-                                const T*, T*, const int*, double*, int, cudaStream_t);          \
+                                const T*, T*, const int*, double*, int, cudaStream_t,           \
+                                const ScalarFold*);                                             \
   template void launch_residual<T>(const LevelView<T>&, int, const T*, const T*, const T*, T*,  \
                                    int, cudaStream_t);                                          \
   template void launch_restrict<T>(int, int, int, const T*, T*, int, cudaStream_t);             \

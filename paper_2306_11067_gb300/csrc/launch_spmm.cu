@@ -1,56 +1,112 @@
 // CSR SpMM launchers: pick the lane split (G column groups x 32/G nnz
 // groups, CPG columns per lane) from the batch width.
+#include <mutex>
+#include <type_traits>
+
 #include "launch.h"
+#include "spmm_staged.cuh"
 
 namespace lcmg {
+
+// Blocks of the staged kernel resident per SM, with its dynamic shared
+// memory opted in (once per device and instantiation).
+template <class V, class T, class TO, int G, int CPG, int MODE>
+static int staged_blocks_per_sm() {
+  static std::mutex mu;
+  static int per_dev[64] = {0};
+  int dev = 0;
+  LCMG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw ArgError("device ordinal out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (per_dev[dev] == 0) {
+    auto k = k_spmm_staged<V, T, TO, G, CPG, MODE>;
+    LCMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, StageGeo<V>::total));
+    int nb = 0;
+    LCMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, StageGeo<V>::total));
+    if (nb < 1) throw CudaError("staged SpMM kernel does not fit on an SM");
+    int sms = 0;
+    LCMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    per_dev[dev] = nb * sms;
+  }
+  return per_dev[dev];
+}
 
 template <class V, class T, class TO, int G, int CPG, int MODE>
 static int run(const SpmmArgs& a0, const V* va, const T* X, TO* Y, const FineOp<T>& fop,
                const T* P, const T* C, const double* lam2, const double* bvec, double* part,
-               int max_blocks, cudaStream_t s) {
+               int max_blocks, cudaStream_t s, const ScalarFold* fold) {
   SpmmArgs a = a0;
   const int width = G * CPG;
+  if (a.ck_row != nullptr) {
+    // persistent: every resident block walks chunks blockIdx.x + i * gridDim.x
+    int64_t blocks = staged_blocks_per_sm<V, T, TO, G, CPG, MODE>();
+    if (blocks > max_blocks) blocks = max_blocks;
+    if (blocks > a.nck) blocks = a.nck;
+    if (blocks < 1) blocks = 1;
+    dim3 grid((unsigned)blocks, (unsigned)((a.nb + width - 1) / width));
+    klaunch(k_spmm_staged<V, T, TO, G, CPG, MODE>, grid, dim3(kBlock), (size_t)StageGeo<V>::total, s, a, va, X,
+            Y, fop, P, C, lam2, bvec, part, fold ? *fold : ScalarFold{});
+    LCMG_LAUNCHED();
+    return (int)blocks;
+  }
   int64_t blocks = (a.rows + (kBlock / 32) - 1) / (kBlock / 32);
   if (blocks > max_blocks) blocks = max_blocks;
   if (blocks < 1) blocks = 1;
   dim3 grid((unsigned)blocks, (unsigned)((a.nb + width - 1) / width));
-  k_spmm<V, T, TO, G, CPG, MODE><<<grid, kBlock, 0, s>>>(a, va, X, Y, fop, P, C, lam2, bvec, part);
+  klaunch(k_spmm<V, T, TO, G, CPG, MODE>, dim3(grid), dim3(kBlock), 0, s, a, va, X, Y, fop, P, C, lam2, bvec, part,
+          fold ? *fold : ScalarFold{});
   LCMG_LAUNCHED();
   return (int)blocks;
+}
+
+// Lane split (G column groups, CPG columns per lane) for a batch of nb
+// columns: f(integral_constant<G>, integral_constant<CPG>).
+template <int MODE, class F>
+static int dispatch_split(int nb, F&& f) {
+  using std::integral_constant;
+  if (MODE == 0 || MODE == 1) {
+    if (nb == 1) return f(integral_constant<int, 1>{}, integral_constant<int, 1>{});
+    if (nb == 2) return f(integral_constant<int, 2>{}, integral_constant<int, 1>{});
+    if (nb <= 4) return f(integral_constant<int, 4>{}, integral_constant<int, 1>{});
+    if (nb <= 8) return f(integral_constant<int, 4>{}, integral_constant<int, 2>{});
+    if (nb <= 12) return f(integral_constant<int, 4>{}, integral_constant<int, 3>{});
+    if (nb <= 16) return f(integral_constant<int, 4>{}, integral_constant<int, 4>{});
+    if (nb <= 20) return f(integral_constant<int, 4>{}, integral_constant<int, 5>{});
+    if (nb <= 24) return f(integral_constant<int, 4>{}, integral_constant<int, 6>{});
+    if (nb <= 32) return f(integral_constant<int, 4>{}, integral_constant<int, 8>{});
+    return f(integral_constant<int, 8>{}, integral_constant<int, 8>{});
+  }
+  if (nb == 1) return f(integral_constant<int, 1>{}, integral_constant<int, 1>{});
+  if (nb <= 8) return f(integral_constant<int, 4>{}, integral_constant<int, 2>{});
+  if (nb <= 32) return f(integral_constant<int, 4>{}, integral_constant<int, 8>{});
+  return f(integral_constant<int, 8>{}, integral_constant<int, 8>{});
 }
 
 template <class V, class T, class TO, int MODE>
 int launch_spmm(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop,
                 const T* P, const T* C, const double* lam2, const double* bvec, double* part,
-                int max_blocks, cudaStream_t s) {
-#define LCMG_RUN(G, CPG) \
-  return run<V, T, TO, G, CPG, MODE>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s)
-  const int nb = a.nb;
-  if (MODE == 0 || MODE == 1) {
-    if (nb == 1) LCMG_RUN(1, 1);
-    if (nb == 2) LCMG_RUN(2, 1);
-    if (nb <= 4) LCMG_RUN(4, 1);
-    if (nb <= 8) LCMG_RUN(4, 2);
-    if (nb <= 12) LCMG_RUN(4, 3);
-    if (nb <= 16) LCMG_RUN(4, 4);
-    if (nb <= 20) LCMG_RUN(4, 5);
-    if (nb <= 24) LCMG_RUN(4, 6);
-    if (nb <= 32) LCMG_RUN(4, 8);
-    LCMG_RUN(8, 8);
-  } else {
-    if (nb == 1) LCMG_RUN(1, 1);
-    if (nb <= 8) LCMG_RUN(4, 2);
-    if (nb <= 32) LCMG_RUN(4, 8);
-    LCMG_RUN(8, 8);
-  }
-#undef LCMG_RUN
+                int max_blocks, cudaStream_t s, const ScalarFold* fold) {
+  return dispatch_split<MODE>(a.nb, [&](auto g, auto cpg) {
+    return run<V, T, TO, decltype(g)::value, decltype(cpg)::value, MODE>(a, va, X, Y, fop, P, C, lam2, bvec,
+                                                                         part, max_blocks, s, fold);
+  });
+}
+
+// Opt every staged instantiation of (V, T, TO, MODE) into its dynamic
+// shared memory on the current device.
+template <class V, class T, class TO, int MODE>
+static void prepare_staged() {
+  for (int nb : {1, 2, 4, 8, 12, 16, 20, 24, 32, 64})
+    dispatch_split<MODE>(nb, [&](auto g, auto cpg) {
+      return staged_blocks_per_sm<V, T, TO, decltype(g)::value, decltype(cpg)::value, MODE>();
+    });
 }
 
 #define LCMG_INST(V, T, TO, MODE)                                                             \
   template int launch_spmm<V, T, TO, MODE>(const SpmmArgs&, const V*, const T*, TO*,          \
                                            const FineOp<T>&, const T*, const T*,              \
                                            const double*, const double*, double*, int,        \
-                                           cudaStream_t);
+                                           cudaStream_t, const ScalarFold*);
 // FP32 path
 LCMG_INST(float, float, float, 0)
 LCMG_INST(float, float, float, 1)
@@ -64,5 +120,18 @@ LCMG_INST(double, double, double, 1)
 LCMG_INST(double, double, double, 2)
 LCMG_INST(double, double, double, 3)
 #undef LCMG_INST
+
+void prepare_spmm_staged() {
+  prepare_staged<float, float, float, 0>();
+  prepare_staged<float, float, float, 1>();
+  prepare_staged<float, double, double, 0>();
+  prepare_staged<float, double, double, 1>();
+  prepare_staged<float, double, double, 2>();
+  prepare_staged<float, double, double, 3>();
+  prepare_staged<double, double, double, 0>();
+  prepare_staged<double, double, double, 1>();
+  prepare_staged<double, double, double, 2>();
+  prepare_staged<double, double, double, 3>();
+}
 
 }  // namespace lcmg
