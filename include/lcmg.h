@@ -121,6 +121,10 @@ typedef struct {
                            mbarrier ring of 3 stages) so the HBM stream does not
                            wait on the vector gathers; 0 = direct warp-per-row
                            loads (default)                                       */
+  int32_t vfuse;        /* 1 = run each V-cycle level (nu = 1 or 2) as two kernels on
+                           8 x 8 coarse-point tiles held in shared memory: pre-
+                           smoothing + residual + restriction, then prolongation +
+                           post-smoothing; 0 = one kernel per step (default)     */
 } lcmg_params;
 
 typedef struct lcmg_ctx lcmg_ctx;

@@ -17,6 +17,7 @@
 
 #include "launch.h"
 #include "spmm_staged.cuh"
+#include "vfused.cuh"
 #include "mega.cuh"
 #include "tail.cuh"
 #include "tail_launch.h"
@@ -209,6 +210,7 @@ static void check_params(const lcmg_params& p) {
   if (p.pdl != 0 && p.pdl != 1) throw ArgError("pdl must be 0 or 1");
   if (p.fold != 0 && p.fold != 1) throw ArgError("fold must be 0 or 1");
   if (p.staged != 0 && p.staged != 1) throw ArgError("staged must be 0 or 1");
+  if (p.vfuse != 0 && p.vfuse != 1) throw ArgError("vfuse must be 0 or 1");
 }
 
 static int sum_blocks(int nb) { return std::max(1, std::min(nb, kMaxBlocks)); }
@@ -466,6 +468,21 @@ struct Batch {
     std::vector<T*> zz(nlev);
     rhs[0] = r0; zz[0] = z0;
     for (int k = 1; k < nlev; ++k) { rhs[k] = tp(c.lw[k].rhs); zz[k] = tp(c.lw[k].z); }
+    // (the finest level's tiles hold the r.z partials: at most kMaxBlocks)
+    const int64_t tiles0 = (int64_t)((c.lev[0].nv / 2 + kVTile - 1) / kVTile) * ((c.lev[0].nh / 2 + kVTile - 1) / kVTile);
+    if (c.prm.vfuse && (nu == 1 || nu == 2) && c.prm.tail_points <= 0 && tiles0 <= kMaxBlocks) {
+      // two kernels per level: pre-smoothed z of level k goes to t[k]
+      for (int k = 0; k + 1 < nlev; ++k)
+        launch_vdown<T>(view<T>(c, k), B, lam2T(), tp(c.lw[k].dinv), rhs[k], tp(c.lw[k].t), tp(c.lw[k + 1].rhs),
+                        nu, s);
+      launch_coarse_solve<T>((int)c.lev[nlev - 1].n, B, c.kinv.p, rhs[nlev - 1], zz[nlev - 1], s);
+      for (int k = nlev - 2; k >= 0; --k) {
+        const int g = launch_vup<T>(view<T>(c, k), B, lam2T(), tp(c.lw[k].dinv), rhs[k], zz[k + 1],
+                                    tp(c.lw[k].t), zz[k], k == 0 ? part : nullptr, nu, s);
+        if (k == 0) nb = g;
+      }
+      return nb;
+    }
     // levels k0 .. nlev-1 run in one CTA when they are small enough
     const int k0 = tail_level();
     const int kstop = (k0 < nlev) ? k0 : nlev - 1;
@@ -1223,6 +1240,7 @@ void lcmg_default_params(lcmg_params* p) {
   p->pdl = 0;
   p->fold = 0;
   p->staged = 0;
+  p->vfuse = 0;
 }
 
 const char* lcmg_last_error(void) { return lcmg::g_err.c_str(); }

@@ -53,6 +53,19 @@ struct FineOp {
   __device__ __forceinline__ T apply(int64_t p, int i, int j, T lam2, F v) const {
     return lam2 * lap(p, i, j, v) + ga[p] * v(p);
   }
+  // the same with the value accessor v(di, dj) of the neighbour at offset
+  // (di, dj) (shared-memory tiles)
+  static constexpr int kRadius = 1;
+  template <class F>
+  __device__ __forceinline__ T apply_off(int64_t p, int i, int j, T lam2, F v) const {
+    const T zp = v(0, 0);
+    T acc = 0;
+    if (i + 1 < nv) acc += ws[p] * (zp - v(1, 0));
+    if (i > 0) acc += ws[p - 1] * (zp - v(-1, 0));
+    if (j + 1 < nh) acc += we[p] * (zp - v(0, 1));
+    if (j > 0) acc += we[p - nv] * (zp - v(0, -1));
+    return lam2 * acc + ga[p] * zp;
+  }
   __device__ __forceinline__ double diagL(int64_t p, int i, int j) const {
     double s = 0;
     if (i + 1 < nv) s += (double)ws[p];
@@ -147,6 +160,32 @@ struct CoarseOp {
         const int ii = i + di;
         if (ii < 0 || ii >= nv) continue;
         acc += k[(di + 2) + 5 * (dj + 2)] * v((int64_t)ii + (int64_t)jj * nv);
+      }
+    }
+    return acc;
+  }
+  static constexpr int kRadius = 2;
+  template <class F>
+  __device__ __forceinline__ T apply_off(int64_t p, int i, int j, T lam2, F v) const {
+    T k[28];
+    coefs(p, lam2, k);
+    T acc = 0;
+    if (i >= 2 && i + 2 < nv && j >= 2 && j + 2 < nh) {
+#pragma unroll
+      for (int dj = -2; dj <= 2; ++dj)
+#pragma unroll
+        for (int di = -2; di <= 2; ++di) acc += k[(di + 2) + 5 * (dj + 2)] * v(di, dj);
+      return acc;
+    }
+#pragma unroll
+    for (int dj = -2; dj <= 2; ++dj) {
+      const int jj = j + dj;
+      if (jj < 0 || jj >= nh) continue;
+#pragma unroll
+      for (int di = -2; di <= 2; ++di) {
+        const int ii = i + di;
+        if (ii < 0 || ii >= nv) continue;
+        acc += k[(di + 2) + 5 * (dj + 2)] * v(di, dj);
       }
     }
     return acc;

@@ -46,6 +46,16 @@ void launch_residual(const LevelView<T>& L, int B, const T* lam2, const T* r, co
                      int max_blocks, cudaStream_t s);
 template <class T>
 void launch_restrict(int nvc, int nhc, int B, const T* rf, T* rc, int max_blocks, cudaStream_t s);
+// Level k of the V-cycle in two kernels (nu = 1 or 2 sweeps): down = pre-
+// smoothing from zero, residual and restriction (z -> zpre, R res -> rc);
+// up = zpre + P ec followed by nu sweeps (-> zout; r.z partials into part
+// when part is set).  Both return their block count (tiles).
+template <class T>
+int launch_vdown(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const T* r, T* zpre, T* rc,
+                 int nu, cudaStream_t s);
+template <class T>
+int launch_vup(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const T* r, const T* ec,
+               const T* zpre, T* zout, double* part, int nu, cudaStream_t s);
 template <class T>
 void launch_prolong_add(int nvc, int nhc, int B, const T* ec, T* zf, int max_blocks, cudaStream_t s);
 template <class T>

@@ -1,6 +1,7 @@
 // Launchers of the V-cycle level kernels, the coarsest-level dense setup,
 // the Galerkin products and the PCG vector updates.
 #include "launch.h"
+#include "vfused.cuh"
 
 namespace lcmg {
 
@@ -49,6 +50,38 @@ void launch_residual(const LevelView<T>& L, int B, const T* lam2, const T* r, co
   else
     klaunch(k_residual<CoarseOp<T>, T>, dim3(g), dim3(kBlock), 0, s, L.coarse_op(), L.n, B, lam2, r, z, res);
   LCMG_LAUNCHED();
+}
+
+template <class T>
+int launch_vdown(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const T* r, T* zpre, T* rc,
+                 int nu, cudaStream_t s) {
+  const int ntx = (L.nv / 2 + kVTile - 1) / kVTile, nty = (L.nh / 2 + kVTile - 1) / kVTile;
+  const dim3 grid((unsigned)(ntx * nty), (unsigned)B);
+  if (L.fine) {
+    if (nu == 1) klaunch(k_vdown<FineOp<T>, T, 1>, grid, dim3(kBlock), 0, s, L.fine_op(), B, lam2, dinv, r, zpre, rc, ntx);
+    else klaunch(k_vdown<FineOp<T>, T, 2>, grid, dim3(kBlock), 0, s, L.fine_op(), B, lam2, dinv, r, zpre, rc, ntx);
+  } else {
+    if (nu == 1) klaunch(k_vdown<CoarseOp<T>, T, 1>, grid, dim3(kBlock), 0, s, L.coarse_op(), B, lam2, dinv, r, zpre, rc, ntx);
+    else klaunch(k_vdown<CoarseOp<T>, T, 2>, grid, dim3(kBlock), 0, s, L.coarse_op(), B, lam2, dinv, r, zpre, rc, ntx);
+  }
+  LCMG_LAUNCHED();
+  return ntx * nty;
+}
+
+template <class T>
+int launch_vup(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const T* r, const T* ec,
+               const T* zpre, T* zout, double* part, int nu, cudaStream_t s) {
+  const int ntx = (L.nv / 2 + kVTile - 1) / kVTile, nty = (L.nh / 2 + kVTile - 1) / kVTile;
+  const dim3 grid((unsigned)(ntx * nty), (unsigned)B);
+  if (L.fine) {
+    if (nu == 1) klaunch(k_vup<FineOp<T>, T, 1>, grid, dim3(kBlock), 0, s, L.fine_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
+    else klaunch(k_vup<FineOp<T>, T, 2>, grid, dim3(kBlock), 0, s, L.fine_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
+  } else {
+    if (nu == 1) klaunch(k_vup<CoarseOp<T>, T, 1>, grid, dim3(kBlock), 0, s, L.coarse_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
+    else klaunch(k_vup<CoarseOp<T>, T, 2>, grid, dim3(kBlock), 0, s, L.coarse_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
+  }
+  LCMG_LAUNCHED();
+  return ntx * nty;
 }
 
 template <class T>
@@ -131,6 +164,10 @@ void launch_copy_cols(int64_t n, int B, const int* flag, const T* src, T* dst, i
   template void launch_residual<T>(const LevelView<T>&, int, const T*, const T*, const T*, T*,  \
                                    int, cudaStream_t);                                          \
   template void launch_restrict<T>(int, int, int, const T*, T*, int, cudaStream_t);             \
+  template int launch_vdown<T>(const LevelView<T>&, int, const T*, const T*, const T*, T*, T*,    \
+                               int, cudaStream_t);                                                \
+  template int launch_vup<T>(const LevelView<T>&, int, const T*, const T*, const T*, const T*,    \
+                             const T*, T*, double*, int, cudaStream_t);                           \
   template void launch_prolong_add<T>(int, int, int, const T*, T*, int, cudaStream_t);          \
   template void launch_coarse_solve<T>(int, int, const double*, const T*, T*, cudaStream_t);    \
   template void launch_update_p<T>(int64_t, int, const ColState&, const T*, T*, int,            \

@@ -22,7 +22,7 @@ static int staged_blocks_per_sm() {
     auto k = k_spmm_staged<V, T, TO, G, CPG, MODE>;
     LCMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, StageGeo<V>::total));
     int nb = 0;
-    LCMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kBlock, StageGeo<V>::total));
+    LCMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kStagedThreads, StageGeo<V>::total));
     if (nb < 1) throw CudaError("staged SpMM kernel does not fit on an SM");
     int sms = 0;
     LCMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -44,7 +44,7 @@ static int run(const SpmmArgs& a0, const V* va, const T* X, TO* Y, const FineOp<
     if (blocks > a.nck) blocks = a.nck;
     if (blocks < 1) blocks = 1;
     dim3 grid((unsigned)blocks, (unsigned)((a.nb + width - 1) / width));
-    klaunch(k_spmm_staged<V, T, TO, G, CPG, MODE>, grid, dim3(kBlock), (size_t)StageGeo<V>::total, s, a, va, X,
+    klaunch(k_spmm_staged<V, T, TO, G, CPG, MODE>, grid, dim3(kStagedThreads), (size_t)StageGeo<V>::total, s, a, va, X,
             Y, fop, P, C, lam2, bvec, part, fold ? *fold : ScalarFold{});
     LCMG_LAUNCHED();
     return (int)blocks;

@@ -40,7 +40,8 @@ class lcmg_params(C.Structure):
                 ("graphs", C.c_int32), ("timing", C.c_int32), ("fused", C.c_int32),
                 ("tail_points", C.c_int32), ("pdl", C.c_int32),
                 ("fold", C.c_int32),
-                ("staged", C.c_int32)]
+                ("staged", C.c_int32),
+                ("vfuse", C.c_int32)]
 
 
 class lcmg_stats(C.Structure):
