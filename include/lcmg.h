@@ -121,10 +121,14 @@ typedef struct {
                            mbarrier ring of 3 stages) so the HBM stream does not
                            wait on the vector gathers; 0 = direct warp-per-row
                            loads (default)                                       */
-  int32_t vfuse;        /* 1 = run each V-cycle level (nu = 1 or 2) as two kernels on
+  int32_t vfuse;        /* run each V-cycle level (nu = 1 or 2) as two kernels on
                            8 x 8 coarse-point tiles held in shared memory: pre-
                            smoothing + residual + restriction, then prolongation +
-                           post-smoothing; 0 = one kernel per step (default)     */
+                           post-smoothing.  1 = for batches of at most 4 columns
+                           (default), 2 = always, 0 = one kernel per step        */
+  int32_t spmm_rows;    /* rows of A / A^T a block of the direct SpMM takes as one
+                           contiguous range (>= 8; 8 = default): longer ranges
+                           let neighbouring rows reuse gathered entries in L1   */
 } lcmg_params;
 
 typedef struct lcmg_ctx lcmg_ctx;

@@ -74,6 +74,9 @@ struct LevelWork {
 };
 
 constexpr int kMaxBlocks = 2048;
+// widest batch for which params.vfuse = 1 picks the two-kernels-per-level
+// V-cycle (its blocks read one column each: wider batches read strided)
+constexpr int kVfuseAutoB = 4;
 
 }  // namespace lcmg
 
@@ -151,6 +154,7 @@ static SpmmArgs csr_args(const lcmg_ctx& c, bool trans, int ld) {
   a.rp = trans ? c.rpT.p : c.rp.p;
   a.ci = trans ? c.ciT.p : c.ci.p;
   a.B = ld; a.c0 = 0; a.nb = ld; a.nl = 1; a.nrhs = 1;
+  a.rpb = c.prm.spmm_rows;
   if (c.prm.staged) {
     a.ck_row = trans ? c.ckT_row.p : c.ck_row.p;
     a.ck_nz = trans ? c.ckT_nz.p : c.ck_nz.p;
@@ -210,7 +214,8 @@ static void check_params(const lcmg_params& p) {
   if (p.pdl != 0 && p.pdl != 1) throw ArgError("pdl must be 0 or 1");
   if (p.fold != 0 && p.fold != 1) throw ArgError("fold must be 0 or 1");
   if (p.staged != 0 && p.staged != 1) throw ArgError("staged must be 0 or 1");
-  if (p.vfuse != 0 && p.vfuse != 1) throw ArgError("vfuse must be 0 or 1");
+  if (p.vfuse < 0 || p.vfuse > 2) throw ArgError("vfuse must be 0, 1 or 2");
+  if (p.spmm_rows < 0) throw ArgError("spmm_rows must be >= 0");
 }
 
 static int sum_blocks(int nb) { return std::max(1, std::min(nb, kMaxBlocks)); }
@@ -470,7 +475,8 @@ struct Batch {
     for (int k = 1; k < nlev; ++k) { rhs[k] = tp(c.lw[k].rhs); zz[k] = tp(c.lw[k].z); }
     // (the finest level's tiles hold the r.z partials: at most kMaxBlocks)
     const int64_t tiles0 = (int64_t)((c.lev[0].nv / 2 + kVTile - 1) / kVTile) * ((c.lev[0].nh / 2 + kVTile - 1) / kVTile);
-    if (c.prm.vfuse && (nu == 1 || nu == 2) && c.prm.tail_points <= 0 && tiles0 <= kMaxBlocks) {
+    const bool vf = c.prm.vfuse == 2 || (c.prm.vfuse == 1 && B <= kVfuseAutoB);
+    if (vf && (nu == 1 || nu == 2) && c.prm.tail_points <= 0 && tiles0 <= kMaxBlocks) {
       // two kernels per level: pre-smoothed z of level k goes to t[k]
       for (int k = 0; k + 1 < nlev; ++k)
         launch_vdown<T>(view<T>(c, k), B, lam2T(), tp(c.lw[k].dinv), rhs[k], tp(c.lw[k].t), tp(c.lw[k + 1].rhs),
@@ -1240,7 +1246,8 @@ void lcmg_default_params(lcmg_params* p) {
   p->pdl = 0;
   p->fold = 0;
   p->staged = 0;
-  p->vfuse = 0;
+  p->vfuse = 1;
+  p->spmm_rows = 8;
 }
 
 const char* lcmg_last_error(void) { return lcmg::g_err.c_str(); }

@@ -152,7 +152,7 @@ def test_vcycle_parity(smoother, n_v, n_h, levels, tail_points):
     """tail_points 0: one kernel per level step; 4096: the small levels in one
     CTA; 100000: every coarse level in one CTA."""
     A = pg.blur_csr(n_v, n_h, pg.gaussian_psf(2, 1.0))
-    s = Solver(n_v, n_h, levels=levels, smoother=smoother, tail_points=tail_points)
+    s = Solver(n_v, n_h, levels=levels, smoother=smoother, tail_points=tail_points, vfuse=0)
     s.set_forward_csr(A)
     d = pg.random_weights(ops.n_edges(n_v, n_h), 9)
     s.set_weights(d)

@@ -1,4 +1,4 @@
-"""The two-kernels-per-level V-cycle (params.vfuse = 1) against the oracle.
+"""The two-kernels-per-level V-cycle (params.vfuse = 2: always) against the oracle.
 
 Each level runs as a down kernel (pre-smoothing from zero, residual,
 restriction) and an up kernel (prolongation, post-smoothing) over 8 x 8
@@ -31,7 +31,7 @@ def _rel(a, b):
 @pytest.mark.parametrize("precision", [L.PREC_FP64, L.PREC_MIXED])
 def test_vfused_vcycle_matches_oracle(smoother, n_v, n_h, levels, nu, precision):
     A = pg.blur_csr(n_v, n_h, pg.gaussian_psf(2, 1.0))
-    s = Solver(n_v, n_h, levels=levels, smoother=smoother, nu=nu, vfuse=1, precision=precision)
+    s = Solver(n_v, n_h, levels=levels, smoother=smoother, nu=nu, vfuse=2, precision=precision)
     s.set_forward_csr(A)
     d = pg.random_weights(ops.n_edges(n_v, n_h), 9)
     s.set_weights(d)
@@ -62,7 +62,7 @@ def test_vfused_matches_per_step_kernels():
     lams = np.array([0.01, 1.0])
     R = pg.rng(8).standard_normal((2, n * n))
     out = []
-    for vf in (0, 1):
+    for vf in (0, 2):
         s = Solver(n, n, vfuse=vf)
         s.set_forward_csr(Acsr)
         s.set_weights(d)
@@ -85,7 +85,7 @@ def test_vfused_ct_solve_matches_oracle(precision, bound, nlam):
     P = pg.make_problem("ct256", size=N)
     d = pg.random_weights(ops.n_edges(N, N), 5, d_min=0.05)
     lams = np.geomspace(0.02, 5.0, nlam) if nlam > 1 else np.array([0.2])
-    s = Solver(N, N, levels=4, vfuse=1, staged=1, precision=precision, tol=1e-12, maxit=20000)
+    s = Solver(N, N, levels=4, vfuse=2, staged=1, precision=precision, tol=1e-12, maxit=20000)
     s.set_forward_csr(P.A)
     s.set_weights(d)
     out = s.solve(lams, P.b[:, 0])
