@@ -126,9 +126,6 @@ typedef struct {
                            smoothing + residual + restriction, then prolongation +
                            post-smoothing.  1 = for batches of at most 4 columns
                            (default), 2 = always, 0 = one kernel per step        */
-  int32_t spmm_rows;    /* rows of A / A^T a block of the direct SpMM takes as one
-                           contiguous range (>= 8; 8 = default): longer ranges
-                           let neighbouring rows reuse gathered entries in L1   */
 } lcmg_params;
 
 typedef struct lcmg_ctx lcmg_ctx;

@@ -154,7 +154,6 @@ static SpmmArgs csr_args(const lcmg_ctx& c, bool trans, int ld) {
   a.rp = trans ? c.rpT.p : c.rp.p;
   a.ci = trans ? c.ciT.p : c.ci.p;
   a.B = ld; a.c0 = 0; a.nb = ld; a.nl = 1; a.nrhs = 1;
-  a.rpb = c.prm.spmm_rows;
   if (c.prm.staged) {
     a.ck_row = trans ? c.ckT_row.p : c.ck_row.p;
     a.ck_nz = trans ? c.ckT_nz.p : c.ck_nz.p;
@@ -215,7 +214,6 @@ static void check_params(const lcmg_params& p) {
   if (p.fold != 0 && p.fold != 1) throw ArgError("fold must be 0 or 1");
   if (p.staged != 0 && p.staged != 1) throw ArgError("staged must be 0 or 1");
   if (p.vfuse < 0 || p.vfuse > 2) throw ArgError("vfuse must be 0, 1 or 2");
-  if (p.spmm_rows < 0) throw ArgError("spmm_rows must be >= 0");
 }
 
 static int sum_blocks(int nb) { return std::max(1, std::min(nb, kMaxBlocks)); }
@@ -1247,7 +1245,6 @@ void lcmg_default_params(lcmg_params* p) {
   p->fold = 0;
   p->staged = 0;
   p->vfuse = 1;
-  p->spmm_rows = 8;
 }
 
 const char* lcmg_last_error(void) { return lcmg::g_err.c_str(); }

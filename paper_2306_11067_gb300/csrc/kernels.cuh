@@ -395,11 +395,6 @@ struct SpmmArgs {
   const int64_t* ck_nz;   // nck + 1 first nonzeros (rp[ck_row[c]])
   int64_t nck;
   int* err;               // set to 1 when a staging wait gives up
-  // direct kernel: a block walks ranges of rpb consecutive rows (ranges
-  // blockIdx.x, blockIdx.x + gridDim.x, ...), its warps taking the rows of
-  // a range in turn, so neighbouring rows reuse the vector entries they
-  // gather from L1; values below 8 mean 8 (one row per warp and range)
-  int rpb;
 };
 
 template <class V, class T, class TO, int G, int CPG, int MODE>
@@ -413,6 +408,8 @@ __global__ void __launch_bounds__(kBlock)
   __shared__ double sdot[kBlock / 32][G * CPG];
   const int lane = threadIdx.x & 31, warp_in_block = threadIdx.x >> 5;
   const int g = lane % G, s = lane / G;
+  const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kBlock) >> 5;
   const int cfirst = a.c0 + blockIdx.y * (G * CPG);
   const int cend = min(a.c0 + a.nb, cfirst + G * CPG);
   const int cbase = cfirst + g * CPG;
@@ -421,71 +418,66 @@ __global__ void __launch_bounds__(kBlock)
   for (int t = 0; t < CPG; ++t) dacc[t] = 0.0;
 
   constexpr int U = 4;  // nonzeros per lane in flight
-  const int64_t R = a.rpb > kBlock / 32 ? a.rpb : kBlock / 32;
-  const int64_t nrange = (a.rows + R - 1) / R;
-  for (int64_t rg = blockIdx.x; rg < nrange; rg += gridDim.x) {
-    const int64_t rend = min(a.rows, (rg + 1) * R);
-    for (int64_t r = rg * R + warp_in_block; r < rend; r += kBlock / 32) {
-      const int64_t k0 = a.rp[r], k1 = a.rp[r + 1];
-      T acc[CPG];
+  for (int64_t r = warp; r < a.rows; r += nwarps) {
+    const int64_t k0 = a.rp[r], k1 = a.rp[r + 1];
+    T acc[CPG];
 #pragma unroll
-      for (int t = 0; t < CPG; ++t) acc[t] = 0;
-      for (int64_t kb = k0 + s; kb < k1; kb += S * U) {
-        // the matrix is streamed once per apply: load it evict-first so the
-        // gathered vectors stay in L2; all loads of the step are independent
-        int cu[U];
-        T vu[U];
+    for (int t = 0; t < CPG; ++t) acc[t] = 0;
+    for (int64_t kb = k0 + s; kb < k1; kb += S * U) {
+      // the matrix is streamed once per apply: load it evict-first so the
+      // gathered vectors stay in L2; all loads of the step are independent
+      int cu[U];
+      T vu[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int64_t k = kb + (int64_t)u * S;
-          const bool ok = k < k1;
-          cu[u] = ok ? __ldcs(a.ci + k) : 0;
-          vu[u] = ok ? (T)__ldcs(va + k) : (T)0;
-        }
-        T xv[U][CPG];
+      for (int u = 0; u < U; ++u) {
+        const int64_t k = kb + (int64_t)u * S;
+        const bool ok = k < k1;
+        cu[u] = ok ? __ldcs(a.ci + k) : 0;
+        vu[u] = ok ? (T)__ldcs(va + k) : (T)0;
+      }
+      T xv[U][CPG];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const T* xr = X + (int64_t)cu[u] * a.B + cbase;
+      for (int u = 0; u < U; ++u) {
+        const T* xr = X + (int64_t)cu[u] * a.B + cbase;
 #pragma unroll
-          for (int t = 0; t < CPG; ++t) xv[u][t] = (cbase + t < cend) ? xr[t] : (T)0;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-          for (int t = 0; t < CPG; ++t) acc[t] += vu[u] * xv[u][t];
+        for (int t = 0; t < CPG; ++t) xv[u][t] = (cbase + t < cend) ? xr[t] : (T)0;
       }
 #pragma unroll
-      for (int off = G; off < 32; off <<= 1)
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int t = 0; t < CPG; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], off);
-      if (s == 0) {
-        int i = 0, j = 0;
-        if (MODE == 1 || MODE == 3) {
-          j = (int)(r / fop.nv);
-          i = (int)(r - (int64_t)j * fop.nv);
-        }
+        for (int t = 0; t < CPG; ++t) acc[t] += vu[u] * xv[u][t];
+    }
 #pragma unroll
-        for (int t = 0; t < CPG; ++t) {
-          const int col = cbase + t;
-          if (col >= cend) continue;
-          if (MODE == 0) {
-            Y[r * a.B + col] = (TO)acc[t];
-          } else if (MODE == 1 || MODE == 3) {
-            auto pv = [&](int64_t q) { return P[q * a.B + col]; };
-            const T lap = fop.lap(r, i, j, pv);
-            const T qv = acc[t] + (T)lam2[col] * lap;
-            if (MODE == 1) {
-              Y[r * a.B + col] = (TO)qv;
-              dacc[t] += to_d(P[r * a.B + col]) * to_d(qv);
-            } else {
-              const T rv = C[r * a.B + col] - qv;
-              Y[r * a.B + col] = (TO)rv;
-              dacc[t] += to_d(rv) * to_d(rv);
-            }
-          } else {  // MODE 2
-            const double e = to_d(acc[t]) - bvec[r * a.nrhs + col / a.nl];
-            dacc[t] += e * e;
+    for (int off = G; off < 32; off <<= 1)
+#pragma unroll
+      for (int t = 0; t < CPG; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], off);
+    if (s == 0) {
+      int i = 0, j = 0;
+      if (MODE == 1 || MODE == 3) {
+        j = (int)(r / fop.nv);
+        i = (int)(r - (int64_t)j * fop.nv);
+      }
+#pragma unroll
+      for (int t = 0; t < CPG; ++t) {
+        const int col = cbase + t;
+        if (col >= cend) continue;
+        if (MODE == 0) {
+          Y[r * a.B + col] = (TO)acc[t];
+        } else if (MODE == 1 || MODE == 3) {
+          auto pv = [&](int64_t q) { return P[q * a.B + col]; };
+          const T lap = fop.lap(r, i, j, pv);
+          const T qv = acc[t] + (T)lam2[col] * lap;
+          if (MODE == 1) {
+            Y[r * a.B + col] = (TO)qv;
+            dacc[t] += to_d(P[r * a.B + col]) * to_d(qv);
+          } else {
+            const T rv = C[r * a.B + col] - qv;
+            Y[r * a.B + col] = (TO)rv;
+            dacc[t] += to_d(rv) * to_d(rv);
           }
+        } else {  // MODE 2
+          const double e = to_d(acc[t]) - bvec[r * a.nrhs + col / a.nl];
+          dacc[t] += e * e;
         }
       }
     }

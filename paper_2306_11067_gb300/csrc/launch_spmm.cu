@@ -49,8 +49,7 @@ static int run(const SpmmArgs& a0, const V* va, const T* X, TO* Y, const FineOp<
     LCMG_LAUNCHED();
     return (int)blocks;
   }
-  const int64_t R = a.rpb > kBlock / 32 ? a.rpb : kBlock / 32;
-  int64_t blocks = (a.rows + R - 1) / R;
+  int64_t blocks = (a.rows + (kBlock / 32) - 1) / (kBlock / 32);
   if (blocks > max_blocks) blocks = max_blocks;
   if (blocks < 1) blocks = 1;
   dim3 grid((unsigned)blocks, (unsigned)((a.nb + width - 1) / width));

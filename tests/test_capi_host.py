@@ -30,7 +30,7 @@ def test_default_params():
     assert (p.nu, p.coarse_max, p.maxit, p.check_every, p.graphs) == (2, 8, 10000, 16, 1)
     assert (p.tol, p.q, p.d_min) == (1e-6, 2.0, 1e-3)
     # execution-path options: the measured-fastest combination on GB300
-    assert (p.fused, p.tail_points, p.pdl, p.fold, p.staged, p.vfuse, p.spmm_rows) == (0, 0, 0, 0, 0, 1, 8)
+    assert (p.fused, p.tail_points, p.pdl, p.fold, p.staged, p.vfuse) == (0, 0, 0, 0, 0, 1)
     assert L.lcmg_version().startswith("lcmg")
 
 
