@@ -502,6 +502,115 @@ __global__ void __launch_bounds__(kBlock)
   }
 }
 
+// ---------------------------------------------------------------------------
+// One column (a batch of B = 1, the paper's warm-start chain).  A row is
+// handled by LPR lanes, so a warp works on 32 / LPR rows at once; each lane
+// keeps U nonzeros in flight, and the row pointers of the warp's next rows
+// are loaded before the current rows' gathers (PF).  Same modes as k_spmm.
+// Measured on GB300 (256^2 CT, 15M nonzeros): y = A p is fastest with 32
+// lanes per row and U = 4; the transposed pass, whose epilogue (L^T W L p
+// and p.q) runs on one lane per row, with 8 lanes per row and U = 8.
+// ---------------------------------------------------------------------------
+template <class V, class T, class TO, int MODE, int U, int LPR, bool PF>
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? (LPR == 32 ? 8 : 4) : (LPR == 32 ? 5 : 3))
+    k_spmv1(SpmmArgs a, const V* __restrict__ va, const T* __restrict__ X, TO* __restrict__ Y,
+            FineOp<T> fop, const T* __restrict__ P, const T* __restrict__ C,
+            const double* __restrict__ lam2, const double* __restrict__ bvec,
+            double* __restrict__ part, ScalarFold fold) {
+  pdl_entry();
+  constexpr int RPW = 32 / LPR;  // rows per warp step
+  __shared__ double sdot[kBlock / 32];
+  const int lane = threadIdx.x & 31;
+  const int sl = lane % LPR, hw = lane / LPR;
+  const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kBlock) >> 5;
+  const int64_t ld = a.B;
+  const int col = a.c0;
+  const T l2 = (MODE == 1 || MODE == 3) ? (T)lam2[col] : (T)0;
+  double dacc = 0.0;
+  int64_t wr = warp;
+  int64_t r = wr * RPW + hw;
+  int64_t k0 = 0, k1 = 0;
+  if (r < a.rows) {
+    k0 = a.rp[r];
+    k1 = a.rp[r + 1];
+  }
+  // every lane of a warp runs the same number of steps (the shuffles below
+  // take the whole warp); lanes past the last row compute nothing
+  while (wr * RPW < a.rows) {
+    const int64_t wrn = wr + nwarps;
+    const int64_t rn = wrn * RPW + hw;
+    int64_t k0n = 0, k1n = 0;
+    if (PF && rn < a.rows) {
+      k0n = a.rp[rn];
+      k1n = a.rp[rn + 1];
+    }
+    T acc = 0;
+    for (int64_t kb = k0 + sl; kb < k1; kb += LPR * U) {
+      // the matrix is streamed once per apply: evict-first loads
+      int cu[U];
+      T vu[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t k = kb + (int64_t)u * LPR;
+        const bool ok = k < k1;
+        cu[u] = ok ? __ldcs(a.ci + k) : 0;
+        vu[u] = ok ? (T)__ldcs(va + k) : (T)0;
+      }
+      T xv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) xv[u] = X[(int64_t)cu[u] * ld + col];
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc += vu[u] * xv[u];
+    }
+#pragma unroll
+    for (int off = LPR / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (sl == 0 && r < a.rows) {
+      if (MODE == 0) {
+        Y[r * ld + col] = (TO)acc;
+      } else if (MODE == 1 || MODE == 3) {
+        const int j = (int)(r / fop.nv), i = (int)(r - (int64_t)j * fop.nv);
+        auto pv = [&](int64_t q) { return P[q * ld + col]; };
+        const T qv = acc + l2 * fop.lap(r, i, j, pv);
+        if (MODE == 1) {
+          Y[r * ld + col] = (TO)qv;
+          dacc += to_d(P[r * ld + col]) * to_d(qv);
+        } else {
+          const T rv = C[r * ld + col] - qv;
+          Y[r * ld + col] = (TO)rv;
+          dacc += to_d(rv) * to_d(rv);
+        }
+      } else {  // MODE 2
+        const double e = to_d(acc) - bvec[r * a.nrhs + col / a.nl];
+        dacc += e * e;
+      }
+    }
+    wr = wrn;
+    r = rn;
+    if (PF) {
+      k0 = k0n;
+      k1 = k1n;
+    } else if (r < a.rows) {
+      k0 = a.rp[r];
+      k1 = a.rp[r + 1];
+    }
+  }
+  if (MODE != 0) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, off);
+    if (lane == 0) sdot[threadIdx.x >> 5] = dacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < kBlock / 32; ++w) sum += sdot[w];
+      part[(int64_t)blockIdx.x * ld + col] = sum;
+    }
+    if (MODE == 1 && fold.ticket != nullptr) {
+      if (last_block(fold.ticket)) fold_alpha(fold.st, a.B, part, (int)gridDim.x);
+    }
+  }
+}
+
 constexpr int kCsrPad = 4;  // padding elements after the last nonzero of a CSR array
 
 // ---------------------------------------------------------------------------

@@ -1,7 +1,9 @@
 // CSR SpMM launchers: pick the lane split (G column groups x 32/G nnz
 // groups, CPG columns per lane) from the batch width.
+#include <map>
 #include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "launch.h"
 #include "spmm_staged.cuh"
@@ -31,6 +33,47 @@ static int staged_blocks_per_sm() {
   return per_dev[dev];
 }
 
+// Blocks of a kernel that are resident at once on the current device (the
+// grid of one full wave): a grid-stride kernel launched with more blocks
+// than this runs a second, partial wave.
+template <class K>
+static int resident_grid(K kern, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  int dev = 0;
+  LCMG_CUDA(cudaGetDevice(&dev));
+  const auto key = std::make_pair(reinterpret_cast<const void*>(kern), dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int nb = 0, sms = 0;
+  LCMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem));
+  LCMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (nb < 1) nb = 1;
+  cache[key] = nb * sms;
+  return nb * sms;
+}
+
+// One column: k_spmv1 with the per-pass configuration measured fastest.
+template <class V, class T, class TO, int MODE>
+static int run1(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop, const T* P,
+                const T* C, const double* lam2, const double* bvec, double* part, int max_blocks,
+                cudaStream_t s, const ScalarFold* fold) {
+  constexpr bool kT = (MODE == 1 || MODE == 3);  // transposed pass with the fine-level epilogue
+  constexpr int U = kT ? 8 : 4;
+  constexpr int LPR = kT ? 8 : 32;
+  auto k = k_spmv1<V, T, TO, MODE, U, LPR, true>;
+  int64_t blocks = resident_grid(k, kBlock, 0);
+  const int64_t need = (a.rows * LPR + kBlock - 1) / kBlock;
+  if (blocks > need) blocks = need;
+  if (blocks > max_blocks) blocks = max_blocks;
+  if (blocks < 1) blocks = 1;
+  klaunch(k, dim3((unsigned)blocks), dim3(kBlock), 0, s, a, va, X, Y, fop, P, C, lam2, bvec, part,
+          fold ? *fold : ScalarFold{});
+  LCMG_LAUNCHED();
+  return (int)blocks;
+}
+
 template <class V, class T, class TO, int G, int CPG, int MODE>
 static int run(const SpmmArgs& a0, const V* va, const T* X, TO* Y, const FineOp<T>& fop,
                const T* P, const T* C, const double* lam2, const double* bvec, double* part,
@@ -49,12 +92,15 @@ static int run(const SpmmArgs& a0, const V* va, const T* X, TO* Y, const FineOp<
     LCMG_LAUNCHED();
     return (int)blocks;
   }
+  if (G == 1 && CPG == 1) return run1<V, T, TO, MODE>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
+  auto k = k_spmm<V, T, TO, G, CPG, MODE>;
   int64_t blocks = (a.rows + (kBlock / 32) - 1) / (kBlock / 32);
+  const int64_t wave = resident_grid(k, kBlock, 0);
+  if (blocks > wave) blocks = wave;
   if (blocks > max_blocks) blocks = max_blocks;
   if (blocks < 1) blocks = 1;
   dim3 grid((unsigned)blocks, (unsigned)((a.nb + width - 1) / width));
-  klaunch(k_spmm<V, T, TO, G, CPG, MODE>, dim3(grid), dim3(kBlock), 0, s, a, va, X, Y, fop, P, C, lam2, bvec, part,
-          fold ? *fold : ScalarFold{});
+  klaunch(k, dim3(grid), dim3(kBlock), 0, s, a, va, X, Y, fop, P, C, lam2, bvec, part, fold ? *fold : ScalarFold{});
   LCMG_LAUNCHED();
   return (int)blocks;
 }
