@@ -126,6 +126,11 @@ typedef struct {
                            smoothing + residual + restriction, then prolongation +
                            post-smoothing.  1 = for batches of at most 4 columns
                            (default), 2 = always, 0 = one kernel per step        */
+  int32_t keep_direction; /* a column whose recursive residual met tol but whose
+                           FP64 true residual did not: 1 = replace the residual
+                           and continue from the current search direction
+                           (residual replacement); 0 = restart with p = z
+                           (default)                                            */
 } lcmg_params;
 
 typedef struct lcmg_ctx lcmg_ctx;

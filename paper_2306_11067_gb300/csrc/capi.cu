@@ -214,6 +214,7 @@ static void check_params(const lcmg_params& p) {
   if (p.fold != 0 && p.fold != 1) throw ArgError("fold must be 0 or 1");
   if (p.staged != 0 && p.staged != 1) throw ArgError("staged must be 0 or 1");
   if (p.vfuse < 0 || p.vfuse > 2) throw ArgError("vfuse must be 0, 1 or 2");
+  if (p.keep_direction != 0 && p.keep_direction != 1) throw ArgError("keep_direction must be 0 or 1");
 }
 
 static int sum_blocks(int nb) { return std::max(1, std::min(nb, kMaxBlocks)); }
@@ -345,6 +346,8 @@ static ColState colstate(lcmg_ctx& c) {
   s.rz = c.s_rz.p; s.alpha = c.s_alpha.p; s.beta = c.s_beta.p; s.rr = c.s_rr.p; s.rmax = c.s_rmax.p;
   s.tol2cc = c.s_tol2cc.p; s.active = c.s_active.p; s.iters = c.s_iters.p; s.status = c.s_status.p;
   s.pending = c.s_pending.p; s.counters = c.s_counters.p;
+  // the one-cluster iteration kernel restarts failed columns itself
+  s.keep = (c.prm.keep_direction && !c.prm.fused) ? 1 : 0;
   return s;
 }
 
@@ -1245,6 +1248,7 @@ void lcmg_default_params(lcmg_params* p) {
   p->fold = 0;
   p->staged = 0;
   p->vfuse = 1;
+  p->keep_direction = 0;
 }
 
 const char* lcmg_last_error(void) { return lcmg::g_err.c_str(); }

@@ -253,7 +253,25 @@ struct ColState {
   int* status;
   int* pending;    // recursive residual reached tol: true residual needed
   int* counters;   // [0] active columns, [1] pending columns, [2] reliable-update votes
+  int keep;        // 1: a column whose true residual fails the check continues
+                   // from its current search direction (residual replacement);
+                   // 0: it restarts with p = z
 };
+
+// The recursive residual of column col reached tol: the column waits for
+// its true-residual check.  With st.keep its beta and rz advance as in a
+// regular step (k_update_p then forms p = z + beta p for it), so that a
+// failed check continues CG from that direction with the residual replaced.
+__device__ __forceinline__ void mark_pending(const ColState& st, int col, double rzn) {
+  st.pending[col] = 1;
+  st.active[col] = 0;
+  if (st.keep && rzn > 0.0) {
+    st.beta[col] = rzn / st.rz[col];
+    st.rz[col] = rzn;
+  } else {
+    st.beta[col] = 0.0;
+  }
+}
 
 // The scalar update folded into the producing kernel's last block.
 struct ScalarFold {
@@ -338,9 +356,7 @@ __device__ __forceinline__ void fold_beta(const ScalarFold& f, int B, const doub
       st.active[col] = 0;
       st.beta[col] = 0.0;
     } else if (rr <= st.tol2cc[col]) {
-      st.pending[col] = 1;
-      st.active[col] = 0;
-      st.beta[col] = 0.0;
+      mark_pending(st, col, rzn);
     } else if (st.iters[col] >= f.maxit) {
       st.status[col] = ST_MAXIT;
       st.active[col] = 0;
@@ -970,7 +986,7 @@ __global__ void __launch_bounds__(kBlock)
     k_update_p(int64_t n, int B, ColState st, const T* __restrict__ z, T* __restrict__ p) {
   pdl_entry();
   const ColMap cm(B);
-  if (!cm.ok || !st.active[cm.col]) return;
+  if (!cm.ok || !(st.active[cm.col] || (st.keep && st.pending[cm.col]))) return;
   const int col = cm.col;
   const T be = (T)st.beta[col];
   for (int64_t i = cm.first(); i < n; i += cm.stride()) {
@@ -1075,9 +1091,7 @@ static __global__ void __launch_bounds__(kColThreads)
         st.active[col] = 0;
         st.beta[col] = 0.0;
       } else if (rr <= st.tol2cc[col]) {
-        st.pending[col] = 1;
-        st.active[col] = 0;
-        st.beta[col] = 0.0;
+        mark_pending(st, col, rzn);
       } else if (st.iters[col] >= maxit) {
         st.status[col] = ST_MAXIT;
         st.active[col] = 0;
@@ -1147,9 +1161,7 @@ static __global__ void __launch_bounds__(kScalarThreads)
       st.active[col] = 0;
       st.beta[col] = 0.0;
     } else if (rr <= st.tol2cc[col]) {
-      st.pending[col] = 1;
-      st.active[col] = 0;
-      st.beta[col] = 0.0;
+      mark_pending(st, col, rzn);
     } else if (st.iters[col] >= maxit) {
       st.status[col] = ST_MAXIT;
       st.active[col] = 0;
@@ -1452,7 +1464,7 @@ static __global__ void k_true_check(int B, const double* __restrict__ rr_true, C
         st.active[col] = 1;
         st.rmax[col] = rr;
         st.rr[col] = rr;
-        f = 1;
+        f = st.keep ? 2 : 1;  // 2: replace the residual only; 1: also restart
       }
     } else if (st.active[col] && replace_active) {
       st.rmax[col] = rr;

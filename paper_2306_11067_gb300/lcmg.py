@@ -41,7 +41,8 @@ class lcmg_params(C.Structure):
                 ("tail_points", C.c_int32), ("pdl", C.c_int32),
                 ("fold", C.c_int32),
                 ("staged", C.c_int32),
-                ("vfuse", C.c_int32)]
+                ("vfuse", C.c_int32),
+                ("keep_direction", C.c_int32)]
 
 
 class lcmg_stats(C.Structure):
