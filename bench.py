@@ -39,7 +39,7 @@ WORKLOAD_DESC = ("ct256: 256x256 parallel-beam CT, 180 angles x 363 bins exact r
                  "largest-lambda-first warm-start chain), rel-res 1e-6, 6-level V(2,2) l1-Jacobi")
 METRIC = "lambda-solves/s at rel-res 1e-6"
 KERNEL_SRC = os.path.join(ROOT, "paper_2306_11067_gb300", "csrc", "kernels.cuh")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_spmm_ct256_traffic.txt")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_spmv1_ct256_traffic.txt")
 
 
 def parse():
@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--oracle-sample", type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="profiler workload: one lambda of the workload, this many PCG iterations, no JSON line")
     return ap.parse_args()
 
 
@@ -178,6 +180,21 @@ def recorded_traffic():
         return None
 
 
+def profile_workload(args):
+    """A short run for profiler captures: the workload's operator and
+    hierarchy, one lambda (the middle of the grid) solved from zero for
+    args.profile_iters PCG iterations (mixed precision, one column)."""
+    import problemgen as pg
+    from paper_2306_11067_gb300 import lcmg as L
+    P = pg.make_problem(WORKLOAD)
+    s = L.Solver(P.n_v, P.n_h, precision=L.PREC_MIXED, mode=L.MODE_SEQUENTIAL, tol=1e-30,
+                 maxit=args.profile_iters)
+    s.set_forward_csr(P.A)
+    lam = P.lambdas[len(P.lambdas) // 2: len(P.lambdas) // 2 + 1]
+    s.solve(lam, P.b[:, 0])
+    s.close()
+
+
 # ---------------------------------------------------------------------------
 def main():
     args = parse()
@@ -190,6 +207,8 @@ def main():
 
     if args.impl == "reference":
         return reference_arm(args, world, rank)
+    if args.profile_iters > 0:
+        return profile_workload(args)
 
     import numpy as np
     import torch

@@ -1113,81 +1113,7 @@ static __global__ void __launch_bounds__(kColThreads)
   }
 }
 
-// alpha = rz / p^T q
-static __global__ void __launch_bounds__(kScalarThreads)
-    k_scalar_alpha(int B, int nblk, const double* __restrict__ pq_part, ColState st) {
-  pdl_entry();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int col = w; col < B; col += kScalarThreads / 32) {
-    if (!st.active[col]) {
-      if (lane == 0) st.alpha[col] = 0.0;
-      continue;
-    }
-    const double pq = warp_sum_parts(pq_part, nblk, B, col);
-    if (lane != 0) continue;
-    st.iters[col] += 1;
-    if (!isfinite(pq)) {
-      st.status[col] = ST_NONFINITE;
-      st.active[col] = 0;
-      st.alpha[col] = 0.0;
-    } else if (!(pq > 0.0)) {
-      st.status[col] = ST_BREAKDOWN;
-      st.active[col] = 0;
-      st.alpha[col] = 0.0;
-    } else {
-      st.alpha[col] = st.rz[col] / pq;
-    }
-  }
-}
 
-// after x/r update and z = B r: rr, recursive convergence, beta.
-// rel_trigger: reliable-update vote when rr < rel_trigger * rmax (0 = off).
-static __global__ void __launch_bounds__(kScalarThreads)
-    k_scalar_beta(int B, int nblk_rr, const double* __restrict__ rr_part, int nblk_rz,
-                  const double* __restrict__ rz_part, ColState st, int maxit, double rel_trigger) {
-  pdl_entry();
-  __shared__ int cnt[3];
-  if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int col = w; col < B; col += kScalarThreads / 32) {
-    if (!st.active[col]) continue;
-    const double rr = warp_sum_parts(rr_part, nblk_rr, B, col);
-    const double rzn = warp_sum_parts(rz_part, nblk_rz, B, col);
-    if (lane != 0) continue;
-    st.rr[col] = rr;
-    if (!isfinite(rr) || !isfinite(rzn)) {
-      st.status[col] = ST_NONFINITE;
-      st.active[col] = 0;
-      st.beta[col] = 0.0;
-    } else if (rr <= st.tol2cc[col]) {
-      mark_pending(st, col, rzn);
-    } else if (st.iters[col] >= maxit) {
-      st.status[col] = ST_MAXIT;
-      st.active[col] = 0;
-      st.beta[col] = 0.0;
-    } else if (!(rzn > 0.0)) {
-      st.status[col] = ST_BREAKDOWN;
-      st.active[col] = 0;
-      st.beta[col] = 0.0;
-    } else {
-      st.beta[col] = rzn / st.rz[col];
-      st.rz[col] = rzn;
-      if (rel_trigger > 0.0 && rr < rel_trigger * st.rmax[col]) atomicAdd(&cnt[2], 1);
-    }
-  }
-  __syncthreads();
-  for (int col = threadIdx.x; col < B; col += kScalarThreads) {
-    if (st.active[col]) atomicAdd(&cnt[0], 1);
-    if (st.pending[col]) atomicAdd(&cnt[1], 1);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    st.counters[0] = cnt[0];
-    st.counters[1] = cnt[1];
-    st.counters[2] = cnt[2];
-  }
-}
 
 // Sum partials of a column reduction into out[col] (FP64).
 static __global__ void __launch_bounds__(kScalarThreads)
