@@ -332,6 +332,101 @@ int lcmg_apply_normal_noalloc(int device, void* stream, int32_t n_v, int32_t n_h
                               int32_t val_dtype, const double* d, int32_t n_cols,
                               const double* lambda, const double* p, double* q);
 
+/* ---- serving ----------------------------------------------------------
+ * A server keeps forward operators ("problems") resident on one device and
+ * runs the requests submitted against them, each a lambda sweep (the
+ * systems of eq. (normal) for a list of lambda, Sec. 4) or a whole
+ * Algorithm 2 run, on up to max_slots slots.  A slot is a host thread that
+ * drives its own context (own CUDA stream, operator copy, hierarchy and
+ * workspace), so requests running in different slots overlap on the
+ * device.  Admission: in arrival order among the requests that fit, as soon
+ * as a slot is free and the request's device bytes fit in hbm_budget_bytes
+ * next to everything resident.  An idle context of the same problem is
+ * reused (operator, hierarchy and its last solutions stay resident; a
+ * request with warm = 1 and the same lambda list starts from them);
+ * otherwise a context is created, evicting idle contexts least recently
+ * used.  A request larger than the whole budget fails with NOMEM.  Each
+ * request computes what lcmg_solve / lcmg_lcurve_run compute on a fresh
+ * context with the server's params (same kernels, same reduction order),
+ * whatever else runs.  The paper has no counterpart: this is the service
+ * form of its lambda sweep.  All calls are thread-safe. */
+typedef struct lcmg_server lcmg_server;
+
+typedef struct {
+  int32_t n_v, n_h;          /* image grid (defines L)                         */
+  int32_t kind;              /* 0: CSR matrix A; 1: PSF stencil                 */
+  int64_t m;                 /* CSR: rows of A                                 */
+  const int64_t* row_ptr;    /* CSR, copied: m + 1                             */
+  const int32_t* col;        /* CSR, copied: nnz                               */
+  const void* val;           /* CSR, copied: nnz FP32 (val_dtype 0) or FP64 (1) */
+  int32_t val_dtype;
+  int32_t kh, kw;            /* PSF: odd sides                                  */
+  const double* psf;         /* PSF, copied: kh x kw row-major                  */
+} lcmg_problem;
+
+typedef struct {
+  int32_t problem;           /* id from lcmg_server_add_problem                 */
+  int32_t n_lambda;
+  const double* lambda;      /* increasing, > 0; copied at submit               */
+  const double* b;           /* m values (n for a PSF problem); copied          */
+  double tol;                /* relative residual; 0 = the server's params.tol   */
+  int32_t max_outer;         /* 0: one sweep over lambda (D = I);
+                                >= 1: Algorithm 2 with at most this many outer
+                                iterations (needs n_lambda >= 3)                */
+  int32_t warm;              /* sweep: 1 = start from the resident solutions of
+                                the last sweep of the same problem and lambda
+                                list on the reused context, if any             */
+} lcmg_request;
+
+typedef struct {
+  int32_t state;             /* lcmg_status of the request (OK, NOMEM, CUDA, ...) */
+  int32_t n_lambda;
+  int32_t n_outer;           /* Algorithm 2: outer iterations run               */
+  int64_t n_solves, n_converged;
+  double t_submit, t_admit, t_done;  /* seconds, the server's monotonic clock  */
+  /* caller-owned outputs (each may be NULL), written by poll / wait:
+     sweep:        x[n_lambda][n], rho, eta[n_lambda], iters, status[n_lambda]
+     Algorithm 2:  x[n] (the selected solution), history[max_outer]          */
+  double* x;
+  double* rho;
+  double* eta;
+  int32_t* iters;
+  int32_t* status;
+  int32_t* history;
+} lcmg_result;
+
+typedef struct {
+  size_t resident_bytes;     /* device bytes counted against the budget         */
+  int32_t contexts, pending, running, peak_running;
+  int64_t admitted, completed, evictions, reuses;
+} lcmg_server_stats;
+
+/* Start a server on `device` with max_slots (1..64) slot threads; p = NULL
+ * takes lcmg_default_params.  Errors: INVALID_ARG, CUDA (no such device). */
+int lcmg_server_create(lcmg_server** out, int device, size_t hbm_budget_bytes, int32_t max_slots,
+                       const lcmg_params* p);
+/* Register a forward operator; *id identifies it in requests.  INVALID_ARG. */
+int lcmg_server_add_problem(lcmg_server* s, const lcmg_problem* pr, int32_t* id);
+/* Queue a request; returns at once with its ticket.  INVALID_ARG. */
+int lcmg_server_submit(lcmg_server* s, const lcmg_request* rq, uint64_t* ticket);
+/* NOT_READY while the request is queued or running; CANCELLED if it was
+ * cancelled; otherwise OK with out filled (out->state is the request's own
+ * outcome).  A ticket is released once OK or CANCELLED has been returned. */
+int lcmg_server_poll(lcmg_server* s, uint64_t ticket, lcmg_result* out);
+/* As poll but blocks until the request ends or timeout_s (<= 0: no limit)
+ * passes (then NOT_READY). */
+int lcmg_server_wait(lcmg_server* s, uint64_t ticket, double timeout_s, lcmg_result* out);
+/* Cancel a queued request (STATE if it already started). */
+int lcmg_server_cancel(lcmg_server* s, uint64_t ticket);
+int lcmg_server_get_stats(lcmg_server* s, lcmg_server_stats* out);
+/* Estimated device bytes of a context of `problem` solving n_cols columns
+ * (what admission counts). */
+int lcmg_server_footprint(lcmg_server* s, int32_t problem, int32_t n_cols, size_t* bytes);
+/* Message of the calling thread's last server failure. */
+const char* lcmg_server_last_error(void);
+/* Cancel queued requests, let running ones finish, free everything. */
+int lcmg_server_destroy(lcmg_server* s);
+
 #ifdef __cplusplus
 }
 #endif

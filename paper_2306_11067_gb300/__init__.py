@@ -4,4 +4,4 @@ The compute path is the CUDA library ``liblcmg.so`` (C ABI in
 ``include/lcmg.h``); ``lcmg`` is its ctypes binding.
 """
 from . import lcmg  # noqa: F401
-from .lcmg import Solver, LcmgError  # noqa: F401
+from .lcmg import Server, Solver, LcmgError  # noqa: F401

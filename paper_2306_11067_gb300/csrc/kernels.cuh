@@ -1030,7 +1030,7 @@ __device__ __forceinline__ double sum_parts(const double* part, int nblk, int B,
 // One block of kColThreads threads per column sums that column's partials
 // (fixed thread stride and tree: deterministic) so the FP64 additions are
 // spread over B multiprocessors.
-constexpr int kColThreads = 128;
+constexpr int kColThreads = 512;
 
 __device__ __forceinline__ double block_sum_parts(const double* part, int nblk, int B, int col) {
   __shared__ double sm[kColThreads / 32];

@@ -23,8 +23,17 @@
 namespace lcmg {
 
 constexpr int kVTile = 8;  // coarse points per tile side
+// threads of a tile block: enough for one point per thread in every phase
+// (the widest window is 22 x 22 on the 5-point finest level and 26 x 26 on
+// the 25-point levels); FP64 25-point blocks stay at 512 (their stencil
+// rows need more than the 64 registers a 1024-thread block allows)
+template <class Op, class T>
+__host__ __device__ constexpr int vtile_threads() {
+  return (Op::kRadius == 1 || sizeof(T) == 8) ? 512 : 1024;
+}
 
-// block sum of v into part[blockIdx.x * B + col]
+// block sum of v into part[blockIdx.x * B + col] (NT threads)
+template <int NT>
 __device__ __forceinline__ void vblock_sum(double v, double* sred, double* part, int B, int col) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -32,16 +41,17 @@ __device__ __forceinline__ void vblock_sum(double v, double* sred, double* part,
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int w = 0; w < kBlock / 32; ++w) s += sred[w];
+    for (int w = 0; w < NT / 32; ++w) s += sred[w];
     part[(int64_t)blockIdx.x * B + col] = s;
   }
 }
 
 template <class Op, class T, int NU>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(vtile_threads<Op, T>())
     k_vdown(Op op, int B, const T* __restrict__ lam2, const T* __restrict__ dinv, const T* __restrict__ r,
             T* __restrict__ zpre, T* __restrict__ rc, int ntx) {
   pdl_entry();
+  constexpr int NTD = vtile_threads<Op, T>();
   constexpr int H = Op::kRadius;
   constexpr int WR = 2 * kVTile + 2;                  // restriction window
   constexpr int WZ = WR + 2 * H;                      // z window
@@ -61,14 +71,14 @@ __global__ void __launch_bounds__(kBlock)
   auto gidx = [&](int i, int j) { return ((int64_t)i + (int64_t)j * nv) * B + col; };
 
   // z1 = D r
-  for (int t = threadIdx.x; t < W1 * W1; t += kBlock) {
+  for (int t = threadIdx.x; t < W1 * W1; t += NTD) {
     const int i = oi + t % W1, j = oj + t / W1;
     s1[t] = inside(i, j) ? dinv[gidx(i, j)] * r[gidx(i, j)] : (T)0;
   }
   __syncthreads();
   // z = z1 + D (r - K z1)
   if (NU == 2) {
-    for (int t = threadIdx.x; t < WZ * WZ; t += kBlock) {
+    for (int t = threadIdx.x; t < WZ * WZ; t += NTD) {
       const int i = zi + t % WZ, j = zj + t / WZ;
       T v = 0;
       if (inside(i, j)) {
@@ -86,7 +96,7 @@ __global__ void __launch_bounds__(kBlock)
   constexpr int WS = (NU == 2) ? WZ : W1;
   const int si = (NU == 2) ? zi : oi, sj = (NU == 2) ? zj : oj;
   // res = r - K z on the restriction window
-  for (int t = threadIdx.x; t < WR * WR; t += kBlock) {
+  for (int t = threadIdx.x; t < WR * WR; t += NTD) {
     const int i = ri + t % WR, j = rj + t / WR;
     T v = 0;
     if (inside(i, j)) {
@@ -98,13 +108,13 @@ __global__ void __launch_bounds__(kBlock)
     sres[t] = v;
   }
   // the pre-smoothed z of the tile's own fine points
-  for (int t = threadIdx.x; t < 4 * kVTile * kVTile; t += kBlock) {
+  for (int t = threadIdx.x; t < 4 * kVTile * kVTile; t += NTD) {
     const int i = 2 * I0 + t % (2 * kVTile), j = 2 * J0 + t / (2 * kVTile);
     if (i < nv && j < nh) zpre[gidx(i, j)] = zs[(i - si) + (j - sj) * WS];
   }
   __syncthreads();
   // r_c = R res
-  for (int t = threadIdx.x; t < kVTile * kVTile; t += kBlock) {
+  for (int t = threadIdx.x; t < kVTile * kVTile; t += NTD) {
     const int I = I0 + t % kVTile, J = J0 + t / kVTile;
     if (I >= nvc || J >= nhc) continue;
     T acc = 0;
@@ -123,18 +133,20 @@ __global__ void __launch_bounds__(kBlock)
 }
 
 template <class Op, class T, int NU>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(vtile_threads<Op, T>())
     k_vup(Op op, int B, const T* __restrict__ lam2, const T* __restrict__ dinv, const T* __restrict__ r,
           const T* __restrict__ ec, const T* __restrict__ zpre, T* __restrict__ zout, int ntx,
           double* __restrict__ part) {
   pdl_entry();
+  constexpr int NTD = vtile_threads<Op, T>();
   constexpr int H = Op::kRadius;
   constexpr int WF = 2 * kVTile;           // the tile's fine points
   constexpr int W0 = WF + 2 * NU * H;      // z0 window
   constexpr int W1 = WF + 2 * H;           // window after the first of two sweeps
   __shared__ T s0[W0 * W0];
   __shared__ T s1[(NU == 2) ? W1 * W1 : 1];
-  __shared__ double sred[kBlock / 32];
+  constexpr int NT = vtile_threads<Op, T>();
+  __shared__ double sred[NT / 32];
   const int col = blockIdx.y;
   const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
   const int nv = op.nv, nh = op.nh, nvc = nv / 2, nhc = nh / 2;
@@ -145,7 +157,7 @@ __global__ void __launch_bounds__(kBlock)
   auto inside = [&](int i, int j) { return i >= 0 && i < nv && j >= 0 && j < nh; };
 
   // z0 = z + P e_c
-  for (int t = threadIdx.x; t < W0 * W0; t += kBlock) {
+  for (int t = threadIdx.x; t < W0 * W0; t += NTD) {
     const int a2 = oi + t % W0, b = oj + t / W0;
     T v = 0;
     if (inside(a2, b)) {
@@ -173,7 +185,7 @@ __global__ void __launch_bounds__(kBlock)
   __syncthreads();
   // first of two sweeps
   if (NU == 2) {
-    for (int t = threadIdx.x; t < W1 * W1; t += kBlock) {
+    for (int t = threadIdx.x; t < W1 * W1; t += NTD) {
       const int i = ai + t % W1, j = aj + t / W1;
       T v = 0;
       if (inside(i, j)) {
@@ -192,7 +204,7 @@ __global__ void __launch_bounds__(kBlock)
   const int si = (NU == 2) ? ai : oi, sj = (NU == 2) ? aj : oj;
   // last sweep on the tile's fine points
   double dacc = 0.0;
-  for (int t = threadIdx.x; t < WF * WF; t += kBlock) {
+  for (int t = threadIdx.x; t < WF * WF; t += NTD) {
     const int i = fi + t % WF, j = fj + t / WF;
     if (!inside(i, j)) continue;
     const int64_t p = (int64_t)i + (int64_t)j * nv;
@@ -204,7 +216,7 @@ __global__ void __launch_bounds__(kBlock)
     zout[p * B + col] = zn;
     dacc += to_d(rv) * to_d(zn);
   }
-  if (part) vblock_sum(dacc, sred, part, B, col);
+  if (part) vblock_sum<NT>(dacc, sred, part, B, col);
 }
 
 }  // namespace lcmg

@@ -52,6 +52,31 @@ class lcmg_stats(C.Structure):
                 ("op_launches", C.c_int64), ("op_bytes", C.c_int64), ("fused_ctas", C.c_int32)]
 
 
+class lcmg_problem(C.Structure):
+    _fields_ = [("n_v", C.c_int32), ("n_h", C.c_int32), ("kind", C.c_int32), ("m", C.c_int64),
+                ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p), ("val_dtype", C.c_int32),
+                ("kh", C.c_int32), ("kw", C.c_int32), ("psf", C.c_void_p)]
+
+
+class lcmg_request(C.Structure):
+    _fields_ = [("problem", C.c_int32), ("n_lambda", C.c_int32), ("lambda_", C.c_void_p), ("b", C.c_void_p),
+                ("tol", C.c_double), ("max_outer", C.c_int32), ("warm", C.c_int32)]
+
+
+class lcmg_result(C.Structure):
+    _fields_ = [("state", C.c_int32), ("n_lambda", C.c_int32), ("n_outer", C.c_int32),
+                ("n_solves", C.c_int64), ("n_converged", C.c_int64),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("x", C.c_void_p), ("rho", C.c_void_p), ("eta", C.c_void_p), ("iters", C.c_void_p),
+                ("status", C.c_void_p), ("history", C.c_void_p)]
+
+
+class lcmg_server_stats(C.Structure):
+    _fields_ = [("resident_bytes", C.c_size_t), ("contexts", C.c_int32), ("pending", C.c_int32),
+                ("running", C.c_int32), ("peak_running", C.c_int32), ("admitted", C.c_int64),
+                ("completed", C.c_int64), ("evictions", C.c_int64), ("reuses", C.c_int64)]
+
+
 _lib = None
 _P = C.c_void_p
 _I32 = C.c_int32
@@ -90,6 +115,16 @@ _SIGS = {
     "lcmg_get_diag": (C.c_int, [_P, _P]),
     "lcmg_apply_normal_noalloc": (C.c_int, [C.c_int, _P, _I32, _I32, _I64, _P, _P, _P, _P, _P, _P, _I32, _P,
                                             _I32, _P, _P, _P]),
+    "lcmg_server_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_size_t, _I32, C.POINTER(lcmg_params)]),
+    "lcmg_server_add_problem": (C.c_int, [_P, C.POINTER(lcmg_problem), _PI32]),
+    "lcmg_server_submit": (C.c_int, [_P, C.POINTER(lcmg_request), C.POINTER(C.c_uint64)]),
+    "lcmg_server_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(lcmg_result)]),
+    "lcmg_server_wait": (C.c_int, [_P, C.c_uint64, _D, C.POINTER(lcmg_result)]),
+    "lcmg_server_cancel": (C.c_int, [_P, C.c_uint64]),
+    "lcmg_server_get_stats": (C.c_int, [_P, C.POINTER(lcmg_server_stats)]),
+    "lcmg_server_footprint": (C.c_int, [_P, _I32, _I32, C.POINTER(C.c_size_t)]),
+    "lcmg_server_last_error": (C.c_char_p, []),
+    "lcmg_server_destroy": (C.c_int, [_P]),
 }
 
 
@@ -370,6 +405,115 @@ class Solver:
             _N_CACHE.pop(self.ctx.value, None)
             lcmg_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+def _scheck(st: int):
+    if st != LCMG_OK:
+        raise LcmgError(st, lib().lcmg_server_last_error().decode())
+
+
+class Server:
+    """Serving front end: lcmg_server_* (admission by HBM footprint, slot
+    threads with their own contexts and streams, resident operators)."""
+
+    def __init__(self, device=0, hbm_budget=8 << 30, slots=4, **params):
+        p = lcmg_default_params()
+        for k, v in params.items():
+            setattr(p, k, v)
+        self.params = p
+        h = _P()
+        _scheck(lib().lcmg_server_create(C.byref(h), device, int(hbm_budget), slots, C.byref(p)))
+        self.h = h
+        self._probs = {}
+        self._reqs = {}
+
+    def add_csr(self, n_v, n_h, A):
+        rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
+        ci = np.ascontiguousarray(A.col, dtype=np.int32)
+        if A.val.dtype == np.float32:
+            va, dt = np.ascontiguousarray(A.val), 0
+        else:
+            va, dt = _f64(A.val), 1
+        pr = lcmg_problem(n_v=n_v, n_h=n_h, kind=0, m=A.m, row_ptr=_ptr(rp), col=_ptr(ci), val=_ptr(va),
+                          val_dtype=dt)
+        i = C.c_int32()
+        _scheck(lib().lcmg_server_add_problem(self.h, C.byref(pr), C.byref(i)))
+        self._probs[i.value] = (n_v * n_h, A.m)
+        return i.value
+
+    def add_psf(self, n_v, n_h, psf):
+        p = _f64(psf)
+        pr = lcmg_problem(n_v=n_v, n_h=n_h, kind=1, m=n_v * n_h, kh=p.shape[0], kw=p.shape[1], psf=_ptr(p))
+        i = C.c_int32()
+        _scheck(lib().lcmg_server_add_problem(self.h, C.byref(pr), C.byref(i)))
+        self._probs[i.value] = (n_v * n_h, n_v * n_h)
+        return i.value
+
+    def submit(self, problem, lambdas, b, tol=0.0, max_outer=0, warm=0):
+        lam = _f64(lambdas)
+        bb = _f64(b)
+        rq = lcmg_request(problem=problem, n_lambda=lam.size, lambda_=_ptr(lam), b=_ptr(bb), tol=tol,
+                          max_outer=max_outer, warm=warm)
+        t = C.c_uint64()
+        _scheck(lib().lcmg_server_submit(self.h, C.byref(rq), C.byref(t)))
+        self._reqs[t.value] = (problem, lam.size, max_outer)
+        return t.value
+
+    def _result(self, ticket, fn):
+        problem, nl, mo = self._reqs[ticket]
+        n, _ = self._probs[problem]
+        x = np.empty((nl, n) if mo == 0 else n)
+        rho, eta = np.empty(nl), np.empty(nl)
+        its, st = np.empty(nl, np.int32), np.empty(nl, np.int32)
+        hist = np.zeros(max(mo, 1), np.int32)
+        out = lcmg_result(x=_ptr(x), rho=_ptr(rho) if mo == 0 else None, eta=_ptr(eta) if mo == 0 else None,
+                          iters=_ptr(its) if mo == 0 else None, status=_ptr(st) if mo == 0 else None,
+                          history=_ptr(hist) if mo > 0 else None)
+        code = fn(C.byref(out))
+        if code == LCMG_ERR_NOT_READY:
+            return None
+        del self._reqs[ticket]
+        if code != LCMG_OK:
+            raise LcmgError(code, lib().lcmg_server_last_error().decode())
+        r = dict(state=out.state, t_submit=out.t_submit, t_admit=out.t_admit, t_done=out.t_done,
+                 n_solves=out.n_solves, n_converged=out.n_converged, x=x)
+        if mo == 0:
+            r.update(rho=rho, eta=eta, iters=its, status=st)
+        else:
+            r.update(history=list(hist[:out.n_outer]), n_outer=out.n_outer)
+        return r
+
+    def poll(self, ticket):
+        return self._result(ticket, lambda o: lib().lcmg_server_poll(self.h, ticket, o))
+
+    def wait(self, ticket, timeout=0.0):
+        return self._result(ticket, lambda o: lib().lcmg_server_wait(self.h, ticket, timeout, o))
+
+    def cancel(self, ticket):
+        code = lib().lcmg_server_cancel(self.h, ticket)
+        return code
+
+    def stats(self):
+        s = lcmg_server_stats()
+        _scheck(lib().lcmg_server_get_stats(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def footprint(self, problem, n_cols):
+        v = C.c_size_t()
+        _scheck(lib().lcmg_server_footprint(self.h, problem, n_cols, C.byref(v)))
+        return v.value
+
+    def close(self):
+        if self.h:
+            lib().lcmg_server_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

@@ -58,3 +58,15 @@ def test_corner_argument_errors():
     assert e.value.status == L.LCMG_ERR_INVALID_ARG
     with pytest.raises(L.LcmgError):
         L.lcmg_lcurve_corner([1.0, -2.0, 3.0], [3.0, 2.0, 1.0])
+
+
+def test_server_rejects_bad_arguments_without_a_device():
+    """Argument checks of the serving entry points run before any CUDA call."""
+    import ctypes as C
+    h = C.c_void_p()
+    p = L.lcmg_default_params()
+    assert L.lib().lcmg_server_create(C.byref(h), 0, 1 << 30, 0, C.byref(p)) == L.LCMG_ERR_INVALID_ARG
+    assert L.lib().lcmg_server_create(C.byref(h), 0, 0, 2, C.byref(p)) == L.LCMG_ERR_INVALID_ARG
+    assert L.lib().lcmg_server_create(None, 0, 1 << 30, 2, C.byref(p)) == L.LCMG_ERR_INVALID_ARG
+    assert b"bad arguments" in L.lib().lcmg_server_last_error()
+    assert L.lib().lcmg_server_destroy(None) == L.LCMG_OK
