@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--oracle-sample", type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-mix latency leg")
+    ap.add_argument("--serve-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiler workload: one lambda of the workload, this many PCG iterations, no JSON line")
     return ap.parse_args()
@@ -193,6 +195,76 @@ def recorded_traffic():
         return None
 
 
+# Served mix (a reduced form of the Poisson request stream): 40% CT and 60%
+# deblurring, image sides drawn uniformly from the sizes below, each request
+# a 16-lambda sweep logspace(-5, 0, 16) of its own seeded phantom at its own
+# noise level U[0.5%, 5%], arriving as a seeded Poisson process at 0.8x the
+# capacity measured on a burst of the same mix.
+SERVE_CT = ((128, 90, 182), (256, 179, 364))   # side, angles, bins
+SERVE_BLUR = (128, 256, 512)                    # side; PSF 9 x 9, sigma 1.5
+SERVE_REQUESTS = 40
+SERVE_SLOTS = 4
+
+
+def serving_leg(device):
+    """p50 / p99 latency (submit -> result) and throughput of the served mix."""
+    import numpy as np
+    import problemgen as pg
+    from paper_2306_11067_gb300 import lcmg as L
+    g = pg.rng(7)
+    srv = L.Server(device=device, hbm_budget=64 << 30, slots=SERVE_SLOTS, precision=L.PREC_MIXED,
+                   mode=L.MODE_BATCHED, tol=1e-6, maxit=10000)
+    psf = pg.gaussian_psf(4, 1.5)
+    probs = []  # (pid, kind, N, forward)
+    for N, na, nb in SERVE_CT:
+        A = pg.ct_csr(N, na, nb)
+        probs.append((srv.add_csr(N, N, A), "ct", N, A.to_scipy()))
+    for N in SERVE_BLUR:
+        probs.append((srv.add_psf(N, N, psf), "blur", N, None))
+    lams = np.logspace(-5, 0, 16)
+
+    def make_request(k):
+        ct = g.uniform() < 0.4
+        cand = [p for p in probs if (p[1] == "ct") == ct]
+        pid, kind, N, A = cand[int(g.integers(len(cand)))]
+        img = pg.phantom_mixed(N, N, 10, 3000 + k, lo=0.1, hi=1.0)
+        b = (A @ img.ravel(order="F")) if kind == "ct" else pg.blur_apply(img, psf).ravel(order="F")
+        return pid, pg.add_noise(b, float(g.uniform(0.005, 0.05)), 5000 + k)
+
+    # capacity on a burst of 2 x slots requests
+    burst = [make_request(k) for k in range(2 * SERVE_SLOTS)]
+    t0 = time.perf_counter()
+    tick = [srv.submit(pid, lams, b) for pid, b in burst]
+    done = [srv.wait(t) for t in tick]
+    cap = len(done) / (time.perf_counter() - t0)
+    # the Poisson stream
+    rate = 0.8 * cap
+    reqs = [make_request(100 + k) for k in range(SERVE_REQUESTS)]
+    gaps = g.exponential(1.0 / rate, SERVE_REQUESTS)
+    t0 = time.perf_counter()
+    tick, t_next = [], t0
+    for (pid, b), gap in zip(reqs, gaps):
+        t_next += gap
+        delay = t_next - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tick.append(srv.submit(pid, lams, b))
+    res = [srv.wait(t) for t in tick]
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = np.array([r["t_done"] - r["t_submit"] for r in res]) * 1e3
+    conv = int(sum(r["n_converged"] for r in res))
+    return {"requests": SERVE_REQUESTS, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "lambda_solves_per_s": conv / wall, "converged": conv, "systems": 16 * SERVE_REQUESTS,
+            "arrival_rate_per_s": rate, "burst_capacity_per_s": cap, "slots": SERVE_SLOTS,
+            "peak_running": st["peak_running"], "context_reuses": st["reuses"],
+            "mix": "40% CT (128^2: 90x182 rays, 256^2: 179x364) / 60% deblurring (128^2, 256^2, 512^2; "
+                   "PSF 9x9 sigma 1.5); 16 lambda = logspace(-5, 0, 16) per request, noise U[0.5%, 5%]; "
+                   "seeded Poisson arrivals at 0.8x burst capacity; mixed precision, batched, tol 1e-6"}
+
+
 def profile_workload(args):
     """A short run for profiler captures: the workload's operator and
     hierarchy, one lambda (the middle of the grid) solved from zero for
@@ -222,6 +294,9 @@ def main():
         return reference_arm(args, world, rank)
     if args.profile_iters > 0:
         return profile_workload(args)
+    if args.serve_only:
+        print(json.dumps(serving_leg(int(os.environ.get("LOCAL_RANK", "0")))))
+        return
 
     import numpy as np
     import torch
@@ -367,6 +442,14 @@ def main():
         except Exception as ex:  # reported, not fatal
             cpu = {"value": None, "unit": "lambda-solves/s", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
 
+    # ---------------- served mix: p50 / p99 latency (rank 0, N = 1) -------
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        try:
+            serving = serving_leg(local)
+        except Exception as ex:  # reported, not fatal
+            serving = {"failed": str(ex)}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "lambda-solves/s", "n_gpus": world,
@@ -386,6 +469,7 @@ def main():
             "roofline": roofline,
             "cpu_baseline": cpu,
             "plain_fp64": plain,
+            "serving": serving,
             "clocks": clocks,
         }
         print(json.dumps(line))
