@@ -146,9 +146,11 @@ const char* lcmg_last_error(void);
 const char* lcmg_version(void);
 
 /* Create a context on CUDA device `device` that launches on `stream` (a
- * cudaStream_t).  With stream = NULL the context creates a blocking stream
- * of its own (ordered with the legacy default stream, and capturable into
- * CUDA graphs, which the legacy stream is not).  p may be NULL (defaults).
+ * cudaStream_t).  With stream = NULL the context creates a non-blocking
+ * stream of its own (capturable into CUDA graphs, and not synchronised with
+ * the legacy default stream, so contexts driven from several host threads
+ * never join each other's captures).  Every copy the library makes runs on
+ * the context's stream.  p may be NULL (defaults).
  * Errors: INVALID_ARG (bad device or parameters), CUDA. */
 int lcmg_create(lcmg_ctx** ctx, int device, void* stream, const lcmg_params* p);
 

@@ -147,6 +147,19 @@ namespace lcmg {
 
 static void set_err(const std::string& s) { g_err = s; }
 
+// Copies and fills go on the context's stream and are waited for there:
+// the legacy default stream would synchronise implicitly with every
+// blocking stream of the process, including a stream that another thread
+// is capturing into a CUDA graph (several contexts serve in parallel).
+static void copy_sync(cudaStream_t s, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind) {
+  LCMG_CUDA(cudaMemcpyAsync(dst, src, bytes, kind, s));
+  LCMG_CUDA(cudaStreamSynchronize(s));
+}
+static void fill_sync(cudaStream_t s, void* dst, int v, size_t bytes) {
+  LCMG_CUDA(cudaMemsetAsync(dst, v, bytes, s));
+  LCMG_CUDA(cudaStreamSynchronize(s));
+}
+
 // SpMM arguments for A (trans false) or A^T over ld interleaved columns
 static SpmmArgs csr_args(const lcmg_ctx& c, bool trans, int ld) {
   SpmmArgs a{};
@@ -177,7 +190,8 @@ static void check_spmm_err(lcmg_ctx& c) {
 
 // Chunks of consecutive rows with at most kChunkNnz nonzeros and at most
 // kChunkRows rows; a row with more than kChunkNnz nonzeros is its own chunk.
-static int64_t build_chunks(const int64_t* rp, int64_t rows, DevBuf<int32_t>& d_row, DevBuf<int64_t>& d_nz) {
+static int64_t build_chunks(const int64_t* rp, int64_t rows, DevBuf<int32_t>& d_row, DevBuf<int64_t>& d_nz,
+                            cudaStream_t s) {
   std::vector<int32_t> row;
   std::vector<int64_t> nz;
   int64_t r = 0;
@@ -192,8 +206,8 @@ static int64_t build_chunks(const int64_t* rp, int64_t rows, DevBuf<int32_t>& d_
   row.push_back((int32_t)rows);
   nz.push_back(rp[rows]);
   const int64_t nck = (int64_t)row.size() - 1;
-  LCMG_CUDA(cudaMemcpy(d_row.need(row.size()), row.data(), sizeof(int32_t) * row.size(), cudaMemcpyHostToDevice));
-  LCMG_CUDA(cudaMemcpy(d_nz.need(nz.size()), nz.data(), sizeof(int64_t) * nz.size(), cudaMemcpyHostToDevice));
+  copy_sync(s, d_row.need(row.size()), row.data(), sizeof(int32_t) * row.size(), cudaMemcpyHostToDevice);
+  copy_sync(s, d_nz.need(nz.size()), nz.data(), sizeof(int64_t) * nz.size(), cudaMemcpyHostToDevice);
   return nck;
 }
 // for entry points defined in other translation units
@@ -335,7 +349,7 @@ static void ensure_work(lcmg_ctx& c, int B) {
   c.s_counters.need(4);
   if (!c.tickets.p) {
     c.tickets.need(4);
-    LCMG_CUDA(cudaMemset(c.tickets.p, 0, 4 * sizeof(int)));
+    fill_sync(c.stream, c.tickets.p, 0, 4 * sizeof(int));
   }
   if (!c.h_counters) LCMG_CUDA(cudaMallocHost(&c.h_counters, 4 * sizeof(int)));
   c.Bcap = std::max(c.Bcap, B);
@@ -546,7 +560,7 @@ struct Batch {
     // the host copy of lam2 must stay valid until the copies complete
     LCMG_CUDA(cudaStreamSynchronize(s));
     std::vector<int> info(B);
-    LCMG_CUDA(cudaMemcpy(info.data(), c.s_info.p, sizeof(int) * B, cudaMemcpyDeviceToHost));
+    copy_sync(c.stream, info.data(), c.s_info.p, sizeof(int) * B, cudaMemcpyDeviceToHost);
     for (int j = 0; j < B; ++j)
       if (info[j] != 0) throw ArgError("coarsest-level Cholesky failed (pivot " + std::to_string(info[j]) + ")");
   }
@@ -1269,8 +1283,10 @@ int lcmg_create(lcmg_ctx** out, int device, void* stream, const lcmg_params* p) 
   auto* c = new lcmg_ctx();
   c->device = device;
   c->stream = static_cast<cudaStream_t>(stream);
-  if (!c->stream) {  // a blocking stream of our own: ordered with the legacy stream, capturable
-    LCMG_CUDA(cudaStreamCreate(&c->stream));
+  if (!c->stream) {
+    // a stream of our own, non-blocking: no implicit synchronisation with
+    // the legacy stream, so other threads' work never joins our captures
+    LCMG_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
     c->own_stream = true;
   }
   c->prm = prm;
@@ -1278,7 +1294,7 @@ int lcmg_create(lcmg_ctx** out, int device, void* stream, const lcmg_params* p) 
   LCMG_CUDA(cudaGetDeviceProperties(&prop, device));
   c->sms = prop.multiProcessorCount;
   c->maxblk = std::min(lcmg::kMaxBlocks, c->sms * 8);
-  LCMG_CUDA(cudaMemset(c->spmm_err.need(1), 0, sizeof(int)));
+  lcmg::fill_sync(c->stream, c->spmm_err.need(1), 0, sizeof(int));
   // opt the staged SpMM kernels into their shared memory here, outside any
   // stream capture
   lcmg::prepare_spmm_staged();
@@ -1320,7 +1336,7 @@ int lcmg_set_grid(lcmg_ctx* ctx, int32_t n_v, int32_t n_h) {
   ctx->ne = (int64_t)n_h * (n_v - 1) + (int64_t)(n_h - 1) * n_v;
   ctx->fwd = 0;
   std::vector<double> ones(ctx->ne, 1.0);
-  LCMG_CUDA(cudaMemcpy(ctx->d.need(ctx->ne), ones.data(), sizeof(double) * ctx->ne, cudaMemcpyHostToDevice));
+  lcmg::copy_sync(ctx->stream, ctx->d.need(ctx->ne), ones.data(), sizeof(double) * ctx->ne, cudaMemcpyHostToDevice);
   lcmg::refresh_fine(*ctx);
   LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
   API_END
@@ -1363,32 +1379,32 @@ int lcmg_set_forward_csr(lcmg_ctx* ctx, int64_t m, int64_t n, const int64_t* row
   ctx->vdtype = val_dtype;
   cudaStream_t s = ctx->stream;
   // row pointers padded: a staged copy of rp may read one entry past rp[m]
-  LCMG_CUDA(cudaMemcpy(ctx->rp.need(m + 1 + lcmg::kCsrPad), row_ptr, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice));
-  LCMG_CUDA(cudaMemcpy(ctx->ci.need(nnz + lcmg::kCsrPad), col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
-  LCMG_CUDA(cudaMemcpy(ctx->rpT.need(n + 1 + lcmg::kCsrPad), rpT.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice));
-  LCMG_CUDA(cudaMemcpy(ctx->ciT.need(nnz + lcmg::kCsrPad), ciT.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
+  lcmg::copy_sync(ctx->stream, ctx->rp.need(m + 1 + lcmg::kCsrPad), row_ptr, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice);
+  lcmg::copy_sync(ctx->stream, ctx->ci.need(nnz + lcmg::kCsrPad), col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
+  lcmg::copy_sync(ctx->stream, ctx->rpT.need(n + 1 + lcmg::kCsrPad), rpT.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
+  lcmg::copy_sync(ctx->stream, ctx->ciT.need(nnz + lcmg::kCsrPad), ciT.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
   std::vector<float> tmpf(nnz);
   if (val_dtype == 0) {
-    LCMG_CUDA(cudaMemcpy(ctx->v32.need(nnz + lcmg::kCsrPad), vf, sizeof(float) * nnz, cudaMemcpyHostToDevice));
+    lcmg::copy_sync(ctx->stream, ctx->v32.need(nnz + lcmg::kCsrPad), vf, sizeof(float) * nnz, cudaMemcpyHostToDevice);
   } else {
-    LCMG_CUDA(cudaMemcpy(ctx->v64.need(nnz + lcmg::kCsrPad), vd, sizeof(double) * nnz, cudaMemcpyHostToDevice));
-    LCMG_CUDA(cudaMemcpy(ctx->vT64.need(nnz + lcmg::kCsrPad), vT.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
+    lcmg::copy_sync(ctx->stream, ctx->v64.need(nnz + lcmg::kCsrPad), vd, sizeof(double) * nnz, cudaMemcpyHostToDevice);
+    lcmg::copy_sync(ctx->stream, ctx->vT64.need(nnz + lcmg::kCsrPad), vT.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice);
     for (int64_t k = 0; k < nnz; ++k) tmpf[k] = (float)vd[k];
-    LCMG_CUDA(cudaMemcpy(ctx->v32.need(nnz + lcmg::kCsrPad), tmpf.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice));
+    lcmg::copy_sync(ctx->stream, ctx->v32.need(nnz + lcmg::kCsrPad), tmpf.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice);
   }
   for (int64_t k = 0; k < nnz; ++k) tmpf[k] = (float)vT[k];
-  LCMG_CUDA(cudaMemcpy(ctx->vT32.need(nnz + lcmg::kCsrPad), tmpf.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice));
+  lcmg::copy_sync(ctx->stream, ctx->vT32.need(nnz + lcmg::kCsrPad), tmpf.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice);
   // zero padding after the last nonzero (read by the 16-byte vector loads)
-  LCMG_CUDA(cudaMemset(ctx->ci.p + nnz, 0, sizeof(int32_t) * lcmg::kCsrPad));
-  LCMG_CUDA(cudaMemset(ctx->ciT.p + nnz, 0, sizeof(int32_t) * lcmg::kCsrPad));
-  LCMG_CUDA(cudaMemset(ctx->v32.p + nnz, 0, sizeof(float) * lcmg::kCsrPad));
-  LCMG_CUDA(cudaMemset(ctx->vT32.p + nnz, 0, sizeof(float) * lcmg::kCsrPad));
+  lcmg::fill_sync(ctx->stream, ctx->ci.p + nnz, 0, sizeof(int32_t) * lcmg::kCsrPad);
+  lcmg::fill_sync(ctx->stream, ctx->ciT.p + nnz, 0, sizeof(int32_t) * lcmg::kCsrPad);
+  lcmg::fill_sync(ctx->stream, ctx->v32.p + nnz, 0, sizeof(float) * lcmg::kCsrPad);
+  lcmg::fill_sync(ctx->stream, ctx->vT32.p + nnz, 0, sizeof(float) * lcmg::kCsrPad);
   if (val_dtype == 1) {
-    LCMG_CUDA(cudaMemset(ctx->v64.p + nnz, 0, sizeof(double) * lcmg::kCsrPad));
-    LCMG_CUDA(cudaMemset(ctx->vT64.p + nnz, 0, sizeof(double) * lcmg::kCsrPad));
+    lcmg::fill_sync(ctx->stream, ctx->v64.p + nnz, 0, sizeof(double) * lcmg::kCsrPad);
+    lcmg::fill_sync(ctx->stream, ctx->vT64.p + nnz, 0, sizeof(double) * lcmg::kCsrPad);
   }
-  ctx->nck = lcmg::build_chunks(row_ptr, m, ctx->ck_row, ctx->ck_nz);
-  ctx->nckT = lcmg::build_chunks(rpT.data(), n, ctx->ckT_row, ctx->ckT_nz);
+  ctx->nck = lcmg::build_chunks(row_ptr, m, ctx->ck_row, ctx->ck_nz, ctx->stream);
+  ctx->nckT = lcmg::build_chunks(rpT.data(), n, ctx->ckT_row, ctx->ckT_nz, ctx->stream);
   // diag(A^T A): sums of squares along the rows of A^T
   const int g = (int)std::min<int64_t>((n * 32 + lcmg::kBlock - 1) / lcmg::kBlock, ctx->maxblk);
   if (val_dtype == 1)
@@ -1416,9 +1432,9 @@ int lcmg_set_forward_stencil(lcmg_ctx* ctx, int32_t kh, int32_t kw, const double
   ctx->rv = kh / 2;
   ctx->rh = kw / 2;
   ctx->m = ctx->n;
-  LCMG_CUDA(cudaMemcpy(ctx->psf64.need(kh * kw), psf, sizeof(double) * kh * kw, cudaMemcpyHostToDevice));
+  lcmg::copy_sync(ctx->stream, ctx->psf64.need(kh * kw), psf, sizeof(double) * kh * kw, cudaMemcpyHostToDevice);
   std::vector<float> pf(psf, psf + kh * kw);
-  LCMG_CUDA(cudaMemcpy(ctx->psf32.need(kh * kw), pf.data(), sizeof(float) * kh * kw, cudaMemcpyHostToDevice));
+  lcmg::copy_sync(ctx->stream, ctx->psf32.need(kh * kw), pf.data(), sizeof(float) * kh * kw, cudaMemcpyHostToDevice);
   lcmg::PsfArgs pa{};
   pa.nv = ctx->nv; pa.nh = ctx->nh; pa.rv = ctx->rv; pa.rh = ctx->rh; pa.psf = ctx->psf64.p;
   const int g = (int)std::min<int64_t>((ctx->n + lcmg::kBlock - 1) / lcmg::kBlock, ctx->maxblk);
@@ -1440,7 +1456,7 @@ static void set_weights_common(lcmg_ctx* ctx, const double* d, int64_t n_edges, 
   if (!dev) {
     for (int64_t e = 0; e < n_edges; ++e)
       if (!(d[e] > 0.0) || !std::isfinite(d[e])) throw lcmg::ArgError("weights must be positive and finite");
-    LCMG_CUDA(cudaMemcpy(ctx->d.need(n_edges), d, sizeof(double) * n_edges, cudaMemcpyHostToDevice));
+    lcmg::copy_sync(ctx->stream, ctx->d.need(n_edges), d, sizeof(double) * n_edges, cudaMemcpyHostToDevice);
   } else {
     LCMG_CUDA(cudaMemcpyAsync(ctx->d.need(n_edges), d, sizeof(double) * n_edges, cudaMemcpyDeviceToDevice,
                               ctx->stream));
@@ -1469,7 +1485,7 @@ int lcmg_get_weights(lcmg_ctx* ctx, double* d_out, int64_t n_edges) {
   NEED_CTX();
   if (n_edges != ctx->ne || !d_out) throw lcmg::ArgError("bad output buffer");
   LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
-  LCMG_CUDA(cudaMemcpy(d_out, ctx->d.p, sizeof(double) * n_edges, cudaMemcpyDeviceToHost));
+  lcmg::copy_sync(ctx->stream, d_out, ctx->d.p, sizeof(double) * n_edges, cudaMemcpyDeviceToHost);
   API_END
 }
 
@@ -1525,7 +1541,7 @@ int lcmg_solve(lcmg_ctx* ctx, int32_t n_lambda, const double* lambda, int32_t n_
   xd.need((size_t)total * ctx->n);
   if (x0) {
     x0d.need((size_t)total * ctx->n);
-    LCMG_CUDA(cudaMemcpy(x0d.p, x0, sizeof(double) * total * ctx->n, cudaMemcpyHostToDevice));
+    lcmg::copy_sync(ctx->stream, x0d.p, x0, sizeof(double) * total * ctx->n, cudaMemcpyHostToDevice);
   }
   lcmg::solve_all(*ctx, n_lambda, lambda, n_rhs, x0 ? x0d.p : nullptr, xd.p, resid_norm, seminorm, iters, status);
   LCMG_CUDA(cudaMemcpyAsync(x, xd.p, sizeof(double) * total * ctx->n, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1568,11 +1584,11 @@ int lcmg_update_weights(lcmg_ctx* ctx, const double* x_star, double q, double d_
   LCMG_CUDA(cudaSetDevice(ctx->device));
   lcmg::DevBuf<double>& xs = ctx->stage_x;
   xs.need(ctx->n);
-  LCMG_CUDA(cudaMemcpy(xs.p, x_star, sizeof(double) * ctx->n, cudaMemcpyHostToDevice));
+  lcmg::copy_sync(ctx->stream, xs.p, x_star, sizeof(double) * ctx->n, cudaMemcpyHostToDevice);
   lcmg::update_weights_dev(*ctx, xs.p, q, d_min);
   if (ctx->fwd) lcmg::build_hierarchy(*ctx);
   LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
-  if (d_out) LCMG_CUDA(cudaMemcpy(d_out, ctx->d.p, sizeof(double) * ctx->ne, cudaMemcpyDeviceToHost));
+  if (d_out) lcmg::copy_sync(ctx->stream, d_out, ctx->d.p, sizeof(double) * ctx->ne, cudaMemcpyDeviceToHost);
   API_END
 }
 
@@ -1587,7 +1603,7 @@ int lcmg_lcurve_run_dev(lcmg_ctx* ctx, int32_t m_lambda, const double* lambda, c
   lcmg::require_ready(*ctx);
   // Algorithm 2 starts from D = I
   std::vector<double> ones(ctx->ne, 1.0);
-  LCMG_CUDA(cudaMemcpy(ctx->d.need(ctx->ne), ones.data(), sizeof(double) * ctx->ne, cudaMemcpyHostToDevice));
+  lcmg::copy_sync(ctx->stream, ctx->d.need(ctx->ne), ones.data(), sizeof(double) * ctx->ne, cudaMemcpyHostToDevice);
   lcmg::refresh_fine(*ctx);
   lcmg::build_hierarchy(*ctx);
   lcmg::upload_b(*ctx, 1, b_dev, true);
@@ -1609,15 +1625,15 @@ int lcmg_lcurve_run(lcmg_ctx* ctx, int32_t m_lambda, const double* lambda, const
   lcmg::DevBuf<double>& xd = ctx->stage_x;
   bd.need(ctx->m);
   xd.need(ctx->n);
-  LCMG_CUDA(cudaMemcpy(bd.p, b, sizeof(double) * ctx->m, cudaMemcpyHostToDevice));
+  lcmg::copy_sync(ctx->stream, bd.p, b, sizeof(double) * ctx->m, cudaMemcpyHostToDevice);
   std::vector<double> ones(ctx->ne, 1.0);
-  LCMG_CUDA(cudaMemcpy(ctx->d.need(ctx->ne), ones.data(), sizeof(double) * ctx->ne, cudaMemcpyHostToDevice));
+  lcmg::copy_sync(ctx->stream, ctx->d.need(ctx->ne), ones.data(), sizeof(double) * ctx->ne, cudaMemcpyHostToDevice);
   lcmg::refresh_fine(*ctx);
   lcmg::build_hierarchy(*ctx);
   lcmg::upload_b(*ctx, 1, bd.p, true);
   lcmg::lcurve_run_impl(*ctx, m_lambda, lambda, max_outer, xd.p, lambda_idx_history, n_outer, n_solves,
                         n_converged);
-  LCMG_CUDA(cudaMemcpy(x_out, xd.p, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost));
+  lcmg::copy_sync(ctx->stream, x_out, xd.p, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost);
   API_END
 }
 
@@ -1640,7 +1656,7 @@ int lcmg_apply_normal_dev(lcmg_ctx* ctx, int32_t n_cols, const double* lambda, c
   lcmg::ensure_work(*ctx, B);
   std::vector<double> l2(B);
   for (int j = 0; j < B; ++j) l2[j] = lambda[j] * lambda[j];
-  LCMG_CUDA(cudaMemcpy(ctx->lam2.p, l2.data(), sizeof(double) * B, cudaMemcpyHostToDevice));
+  lcmg::copy_sync(ctx->stream, ctx->lam2.p, l2.data(), sizeof(double) * B, cudaMemcpyHostToDevice);
   const int g = lcmg::grid_for(ctx->n, B, ctx->maxblk);
   klaunch(lcmg::k_planar_to_inter, dim3(g), dim3(lcmg::kBlock), 0, ctx->stream, ctx->n, B, x_dev, ctx->x64.p);
   LCMG_LAUNCHED();
@@ -1705,8 +1721,8 @@ int lcmg_get_level(lcmg_ctx* ctx, int32_t k, int32_t* n_v, int32_t* n_h, double*
   if (n_h) *n_h = L.nh;
   LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
   if (k > 0) {
-    if (gl) LCMG_CUDA(cudaMemcpy(gl, L.gl.p, sizeof(double) * lcmg::kStencil * L.n, cudaMemcpyDeviceToHost));
-    if (ga) LCMG_CUDA(cudaMemcpy(ga, L.ga.p, sizeof(double) * lcmg::kStencil * L.n, cudaMemcpyDeviceToHost));
+    if (gl) lcmg::copy_sync(ctx->stream, gl, L.gl.p, sizeof(double) * lcmg::kStencil * L.n, cudaMemcpyDeviceToHost);
+    if (ga) lcmg::copy_sync(ctx->stream, ga, L.ga.p, sizeof(double) * lcmg::kStencil * L.n, cudaMemcpyDeviceToHost);
   }
   API_END
 }
@@ -1725,7 +1741,7 @@ int lcmg_get_diag(lcmg_ctx* ctx, double* diag_out) {
   NEED_CTX();
   if (ctx->fwd == 0 || !diag_out) throw lcmg::ArgError("forward operator not set or null output");
   LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
-  LCMG_CUDA(cudaMemcpy(diag_out, ctx->diag.p, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost));
+  lcmg::copy_sync(ctx->stream, diag_out, ctx->diag.p, sizeof(double) * ctx->n, cudaMemcpyDeviceToHost);
   API_END
 }
 

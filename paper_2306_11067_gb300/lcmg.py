@@ -484,6 +484,8 @@ class Server:
             raise LcmgError(code, lib().lcmg_server_last_error().decode())
         r = dict(state=out.state, t_submit=out.t_submit, t_admit=out.t_admit, t_done=out.t_done,
                  n_solves=out.n_solves, n_converged=out.n_converged, x=x)
+        if out.state != LCMG_OK:
+            r["error"] = lib().lcmg_server_last_error().decode()
         if mo == 0:
             r.update(rho=rho, eta=eta, iters=its, status=st)
         else:

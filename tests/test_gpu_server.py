@@ -80,7 +80,7 @@ def test_served_mix_equals_alone(mode):
     srv.close()
     assert st["completed"] == len(reqs) and st["peak_running"] >= 2
     for (i, lams, mo, _), r in zip(reqs, results):
-        assert r["state"] == L.LCMG_OK
+        assert r["state"] == L.LCMG_OK, r.get("error")
         assert r["t_submit"] <= r["t_admit"] <= r["t_done"]
         _, n_v, n_h, kind, op, b = probs[i]
         ref = _alone(n_v, n_h, kind, op, b, lams, mo, params)
