@@ -172,8 +172,8 @@ def kernel_fingerprint():
     i = src.index("    k_spmv1(")
     j = src.index("\n}\n", i)
     lsrc = open(LAUNCH_SRC).read()
-    a = lsrc.index("static int run1(")
-    b = lsrc.index("\n}\n", a)
+    a = lsrc.index("static int run1v(")
+    b = lsrc.index("\n}\n", lsrc.index("static int run1(", a))
     return hashlib.sha256((src[i:j] + lsrc[a:b]).encode()).hexdigest()[:16]
 
 
@@ -264,7 +264,7 @@ def serving_leg(device):
             "mix": "40% CT (128^2: 90x182 rays, 256^2: 179x364) / 60% deblurring (128^2, 256^2, 512^2; "
                    "PSF 9x9 sigma 1.5); 16 lambda = logspace(-5, 0, 16) per request, noise U[0.5%, 5%]; "
                    "seeded Poisson arrivals at 0.8x burst capacity; mixed precision, batched, tol 1e-6, "
-                   "maxit %d" % SERVE_MAXIT}
+                   "maxit " + str(SERVE_MAXIT)}
 
 
 def profile_workload(args):

@@ -82,7 +82,7 @@ typedef enum {
 typedef struct {
   int32_t levels;       /* multigrid levels incl. the finest; 0 = coarsen by 2 while
                            both sides are even and one exceeds coarse_max            */
-  int32_t coarse_max;   /* side limit of the coarsest grid for levels = 0 (default 8)  */
+  int32_t coarse_max;   /* side limit of the coarsest grid for levels = 0 (default 16) */
   int32_t nu;           /* pre- = post-smoothing sweeps (default 2; equal counts keep
                            the V-cycle symmetric so CG applies)                      */
   int32_t smoother;     /* lcmg_smoother (default l1-Jacobi)                         */
@@ -131,6 +131,17 @@ typedef struct {
                            and continue from the current search direction
                            (residual replacement); 0 = restart with p = z
                            (default)                                            */
+  int32_t autotune;     /* 1 = on the first solve of each batch width, time the
+                           one-column SpMV configurations of the two operator
+                           passes and both V-cycle forms on this context's
+                           operator and keep the fastest (results may then
+                           differ from an untuned context in the last bits:
+                           the sums are taken in another order); 0 = fixed
+                           defaults (default)                                   */
+  int32_t spmv_variant; /* one-column SpMV configuration of both operator passes
+                           (unless autotuned): 0 = per-pass default (32 lanes x
+                           4 nonzeros for A p, 8 x 8 for the transposed pass);
+                           1 = 32 x 4, 2 = 16 x 8, 3 = 8 x 8                    */
 } lcmg_params;
 
 typedef struct lcmg_ctx lcmg_ctx;
@@ -274,6 +285,11 @@ typedef struct {
   int64_t op_launches;
   int64_t op_bytes;
   int32_t fused_ctas;   /* CTAs of the cluster running the fused iteration, 0 if unused */
+  int32_t tuned_spmv_a, tuned_spmv_at;  /* SpMV configuration of the passes
+                           (SpmmArgs variant: 1 = 32 lanes x 4, 2 = 16 x 8,
+                           3 = 8 x 8; 0 = default) used by the last batch     */
+  int32_t tuned_vfuse;  /* V-cycle form of the last batch: 1 fused, 0 per step,
+                           -1 the params.vfuse rule                              */
 } lcmg_stats;
 int lcmg_get_stats(lcmg_ctx* ctx, lcmg_stats* out);
 

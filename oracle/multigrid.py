@@ -67,7 +67,7 @@ def level_shapes(n_v: int, n_h: int, levels: int):
     return shapes
 
 
-def default_levels(n_v: int, n_h: int, coarse_max: int = 8) -> int:
+def default_levels(n_v: int, n_h: int, coarse_max: int = 16) -> int:
     """Coarsen by 2 while both sides are even and some side exceeds coarse_max."""
     lv, a, b = 1, n_v, n_h
     while (a > coarse_max or b > coarse_max) and a % 2 == 0 and b % 2 == 0:

@@ -28,7 +28,7 @@ class Params:
     smoother: str = "l1"
     omega: float = 2.0 / 3.0
     levels: int | None = None
-    coarse_max: int = 8
+    coarse_max: int = 16
     q: float = 2.0
     d_min: float = 1e-3
     tol: float = 1e-6

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -78,6 +79,13 @@ constexpr int kMaxBlocks = 2048;
 // V-cycle (its blocks read one column each: wider batches read strided)
 constexpr int kVfuseAutoB = 4;
 
+// Choices of the autotuner for one batch width (params.autotune): the
+// one-column SpMV configuration of each operator pass (SpmmArgs::variant)
+// and the V-cycle form (1 = two kernels per level, 0 = one per step).
+struct Tuned {
+  int var_a = 0, var_at = 0, vfuse = -1;
+};
+
 }  // namespace lcmg
 
 using namespace lcmg;
@@ -105,6 +113,7 @@ struct lcmg_ctx {
   DevBuf<int64_t> ck_nz, ckT_nz;
   int64_t nck = 0, nckT = 0;
   DevBuf<int> spmm_err;  // set by a staged SpMM whose stage wait gave up
+  std::map<int, lcmg::Tuned> tuned;  // autotuner choices per (batch width, precision)
   int rv = 0, rh = 0;
   DevBuf<double> psf64;
   DevBuf<float> psf32;
@@ -229,6 +238,8 @@ static void check_params(const lcmg_params& p) {
   if (p.staged != 0 && p.staged != 1) throw ArgError("staged must be 0 or 1");
   if (p.vfuse < 0 || p.vfuse > 2) throw ArgError("vfuse must be 0, 1 or 2");
   if (p.keep_direction != 0 && p.keep_direction != 1) throw ArgError("keep_direction must be 0 or 1");
+  if (p.autotune != 0 && p.autotune != 1) throw ArgError("autotune must be 0 or 1");
+  if (p.spmv_variant < 0 || p.spmv_variant > 3) throw ArgError("spmv_variant must be 0..3");
 }
 
 static int sum_blocks(int nb) { return std::max(1, std::min(nb, kMaxBlocks)); }
@@ -378,7 +389,19 @@ struct Batch {
   cudaStream_t s;
   int nlev;
 
-  Batch(lcmg_ctx& c_, int B_) : c(c_), B(B_), s(c_.stream), nlev((int)c_.lev.size()) {}
+  // autotuned or forced choices (0 / -1: the defaults)
+  int var_a = 0, var_at = 0, vf_force = -1;
+  int tune_key() const { return 2 * B + (std::is_same<T, float>::value ? 1 : 0); }
+
+  Batch(lcmg_ctx& c_, int B_) : c(c_), B(B_), s(c_.stream), nlev((int)c_.lev.size()) {
+    var_a = var_at = c.prm.spmv_variant;
+    auto it = c.tuned.find(tune_key());
+    if (c.prm.autotune && it != c.tuned.end()) {
+      var_a = it->second.var_a;
+      var_at = it->second.var_at;
+      vf_force = it->second.vfuse;
+    }
+  }
 
   T* tp(DevBuf<char>& b) { return reinterpret_cast<T*>(b.p); }
   const T* lam2T() { return reinterpret_cast<const T*>(c.lam2T.p); }
@@ -490,7 +513,7 @@ struct Batch {
     for (int k = 1; k < nlev; ++k) { rhs[k] = tp(c.lw[k].rhs); zz[k] = tp(c.lw[k].z); }
     // (the finest level's tiles hold the r.z partials: at most kMaxBlocks)
     const int64_t tiles0 = (int64_t)((c.lev[0].nv / 2 + kVTile - 1) / kVTile) * ((c.lev[0].nh / 2 + kVTile - 1) / kVTile);
-    const bool vf = c.prm.vfuse == 2 || (c.prm.vfuse == 1 && B <= kVfuseAutoB);
+    const bool vf = vf_force >= 0 ? vf_force == 1 : (c.prm.vfuse == 2 || (c.prm.vfuse == 1 && B <= kVfuseAutoB));
     if (vf && (nu == 1 || nu == 2) && c.prm.tail_points <= 0 && tiles0 <= kMaxBlocks) {
       // two kernels per level: pre-smoothed z of level k goes to t[k]
       for (int k = 0; k + 1 < nlev; ++k)
@@ -686,6 +709,62 @@ struct Batch {
     }
   }
 
+  // Autotuner (params.autotune): on the first batch of width B, time the
+  // one-column SpMV configurations of each operator pass and both V-cycle
+  // forms on this context's operator and hierarchy (CUDA events, 3 runs
+  // after one warm-up, on scratch vectors), keep the fastest per width.
+  void autotune() {
+    if (!c.prm.autotune || c.tuned.count(tune_key()) || c.prm.fused) return;
+    Tuned t;
+    LCMG_CUDA(cudaMemsetAsync(c.p.p, 0, sizeof(T) * c.n * B, s));
+    LCMG_CUDA(cudaMemsetAsync(c.r.p, 0, sizeof(T) * c.n * B, s));
+    cudaEvent_t e0, e1;
+    LCMG_CUDA(cudaEventCreate(&e0));
+    LCMG_CUDA(cudaEventCreate(&e1));
+    auto time = [&](auto&& fn) {
+      fn();
+      LCMG_CUDA(cudaEventRecord(e0, s));
+      for (int i = 0; i < 3; ++i) fn();
+      LCMG_CUDA(cudaEventRecord(e1, s));
+      LCMG_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      LCMG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      return ms;
+    };
+    auto apply = [&] { apply_K(tp(c.p), tp(c.q), c.part_pq.p); };
+    if (c.fwd == 1 && B == 1) {
+      // transposed pass at its default while A's configurations are timed,
+      // then A at its winner while the transposed pass's are timed
+      float best = 1e30f;
+      for (int v = 1; v <= 3; ++v) {
+        var_a = v;
+        const float ms = time(apply);
+        if (ms < best) { best = ms; t.var_a = v; }
+      }
+      var_a = t.var_a;
+      best = 1e30f;
+      for (int v = 1; v <= 3; ++v) {
+        var_at = v;
+        const float ms = time(apply);
+        if (ms < best) { best = ms; t.var_at = v; }
+      }
+      var_at = t.var_at;
+    }
+    const int nu = c.prm.nu;
+    if (nlev >= 2 && (nu == 1 || nu == 2) && c.prm.tail_points <= 0) {
+      float best = 1e30f;
+      for (int f = 0; f <= 1; ++f) {
+        vf_force = f;
+        const float ms = time([&] { vcycle(tp(c.r), tp(c.z), c.part_rz.p); });
+        if (ms < best) { best = ms; t.vfuse = f; }
+      }
+      vf_force = t.vfuse;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c.tuned[tune_key()] = t;
+  }
+
   // Run PCG on the batch whose x64 (initial guesses) and c64 (right-hand
   // sides A^T b) are set.  Returns the number of batch iterations.
   int64_t run(const std::vector<double>& lam) {
@@ -696,6 +775,10 @@ struct Batch {
       ~PdlScope() { pdl_flag() = prev; }
     } pdl_scope(c.prm.pdl == 1);
     setup(lam);
+    autotune();
+    c.stats.tuned_spmv_a = var_a;
+    c.stats.tuned_spmv_at = var_at;
+    c.stats.tuned_vfuse = vf_force;
     ColState st = colstate(c);
     // ||c||^2 and the true initial residual
     const int g = grid_for(c.n, B, c.maxblk);
@@ -835,6 +918,8 @@ int Batch<T>::apply_K(const T* P, T* Q, double* part, const ScalarFold* fold, bo
   if (c.fwd == 1) {
     SpmmArgs a = args(false, B);
     SpmmArgs at = args(true, B);
+    a.variant = var_a;
+    at.variant = var_at;
     if (std::is_same<T, float>::value) {
       launch_spmm<float, float, float, 0>(a, c.v32.p, reinterpret_cast<const float*>(P), reinterpret_cast<float*>(Y),
                                           view<float>(c, 0).fine_op(), nullptr, nullptr, nullptr, nullptr,
@@ -1243,7 +1328,7 @@ void lcmg_default_params(lcmg_params* p) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));
   p->levels = 0;
-  p->coarse_max = 8;
+  p->coarse_max = 16;
   p->nu = 2;
   p->smoother = LCMG_SMOOTH_L1_JACOBI;
   p->omega = 2.0 / 3.0;
@@ -1263,6 +1348,8 @@ void lcmg_default_params(lcmg_params* p) {
   p->staged = 0;
   p->vfuse = 1;
   p->keep_direction = 0;
+  p->autotune = 0;
+  p->spmv_variant = 0;
 }
 
 const char* lcmg_last_error(void) { return lcmg::g_err.c_str(); }
@@ -1335,6 +1422,7 @@ int lcmg_set_grid(lcmg_ctx* ctx, int32_t n_v, int32_t n_h) {
   ctx->n = (int64_t)n_v * n_h;
   ctx->ne = (int64_t)n_h * (n_v - 1) + (int64_t)(n_h - 1) * n_v;
   ctx->fwd = 0;
+  ctx->tuned.clear();
   std::vector<double> ones(ctx->ne, 1.0);
   lcmg::copy_sync(ctx->stream, ctx->d.need(ctx->ne), ones.data(), sizeof(double) * ctx->ne, cudaMemcpyHostToDevice);
   lcmg::refresh_fine(*ctx);
@@ -1417,6 +1505,7 @@ int lcmg_set_forward_csr(lcmg_ctx* ctx, int64_t m, int64_t n, const int64_t* row
   LCMG_CUDA(cudaStreamSynchronize(s));
   ctx->fwd = 1;
   ctx->hier_ok = false;
+  ctx->tuned.clear();
   API_END
 }
 
@@ -1444,6 +1533,7 @@ int lcmg_set_forward_stencil(lcmg_ctx* ctx, int32_t kh, int32_t kw, const double
   LCMG_LAUNCHED();
   LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->fwd = 2;
+  ctx->tuned.clear();
   ctx->hier_ok = false;
   API_END
 }

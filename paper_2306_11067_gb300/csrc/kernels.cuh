@@ -411,6 +411,8 @@ struct SpmmArgs {
   const int64_t* ck_nz;   // nck + 1 first nonzeros (rp[ck_row[c]])
   int64_t nck;
   int* err;               // set to 1 when a staging wait gives up
+  int variant;            // one-column kernel (k_spmv1): 0 = the pass's default,
+                          // 1 = 32 lanes x 4, 2 = 16 lanes x 8, 3 = 8 lanes x 8
 };
 
 template <class V, class T, class TO, int G, int CPG, int MODE>

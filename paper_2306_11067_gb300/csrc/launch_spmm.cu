@@ -54,14 +54,11 @@ static int resident_grid(K kern, int threads, size_t smem) {
   return nb * sms;
 }
 
-// One column: k_spmv1 with the per-pass configuration measured fastest.
-template <class V, class T, class TO, int MODE>
-static int run1(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop, const T* P,
-                const T* C, const double* lam2, const double* bvec, double* part, int max_blocks,
-                cudaStream_t s, const ScalarFold* fold) {
-  constexpr bool kT = (MODE == 1 || MODE == 3);  // transposed pass with the fine-level epilogue
-  constexpr int U = kT ? 8 : 4;
-  constexpr int LPR = kT ? 8 : 32;
+// One column: k_spmv1 with U nonzeros per lane and LPR lanes per row.
+template <class V, class T, class TO, int MODE, int U, int LPR>
+static int run1v(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop, const T* P,
+                 const T* C, const double* lam2, const double* bvec, double* part, int max_blocks,
+                 cudaStream_t s, const ScalarFold* fold) {
   auto k = k_spmv1<V, T, TO, MODE, U, LPR, true>;
   int64_t blocks = resident_grid(k, kBlock, 0);
   const int64_t need = (a.rows * LPR + kBlock - 1) / kBlock;
@@ -72,6 +69,20 @@ static int run1(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<
           fold ? *fold : ScalarFold{});
   LCMG_LAUNCHED();
   return (int)blocks;
+}
+
+// The pass's configuration: a.variant, or by default (measured on GB300,
+// 256^2 CT) 32 lanes x 4 for y = A p and 8 lanes x 8 for the transposed
+// pass, whose fine-level epilogue runs on one lane per row.
+template <class V, class T, class TO, int MODE>
+static int run1(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop, const T* P,
+                const T* C, const double* lam2, const double* bvec, double* part, int max_blocks,
+                cudaStream_t s, const ScalarFold* fold) {
+  constexpr bool kT = (MODE == 1 || MODE == 3);
+  const int v = a.variant != 0 ? a.variant : (kT ? 3 : 1);
+  if (v == 2) return run1v<V, T, TO, MODE, 8, 16>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
+  if (v == 3) return run1v<V, T, TO, MODE, 8, 8>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
+  return run1v<V, T, TO, MODE, 4, 32>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
 }
 
 template <class V, class T, class TO, int G, int CPG, int MODE>

@@ -42,14 +42,17 @@ class lcmg_params(C.Structure):
                 ("fold", C.c_int32),
                 ("staged", C.c_int32),
                 ("vfuse", C.c_int32),
-                ("keep_direction", C.c_int32)]
+                ("keep_direction", C.c_int32),
+                ("autotune", C.c_int32),
+                ("spmv_variant", C.c_int32)]
 
 
 class lcmg_stats(C.Structure):
     _fields_ = [("column_iterations", C.c_int64), ("batch_iterations", C.c_int64),
                 ("kernel_launches", C.c_int64), ("iterate_ms", C.c_double),
                 ("op_ms_a", C.c_double), ("op_ms_at", C.c_double),
-                ("op_launches", C.c_int64), ("op_bytes", C.c_int64), ("fused_ctas", C.c_int32)]
+                ("op_launches", C.c_int64), ("op_bytes", C.c_int64), ("fused_ctas", C.c_int32),
+                ("tuned_spmv_a", C.c_int32), ("tuned_spmv_at", C.c_int32), ("tuned_vfuse", C.c_int32)]
 
 
 class lcmg_problem(C.Structure):

@@ -53,7 +53,7 @@ def test_vfused_vcycle_matches_oracle(smoother, n_v, n_h, levels, nu, precision)
 
 
 def test_vfused_matches_per_step_kernels():
-    """Same V-cycle through both paths on a 256 x 256 grid (6 levels, the
+    """Same V-cycle through both paths on a 256 x 256 grid (5 levels, the
     benchmark hierarchy): FP64 results agree to rounding."""
     n = 256
     A = sp.identity(n * n, format="csr") * 0.5
@@ -66,7 +66,7 @@ def test_vfused_matches_per_step_kernels():
         s = Solver(n, n, vfuse=vf)
         s.set_forward_csr(Acsr)
         s.set_weights(d)
-        assert L.lcmg_num_levels(s.ctx) == 6
+        assert L.lcmg_num_levels(s.ctx) == 5
         rd = torch.tensor(R, device="cuda", dtype=torch.float64)
         zd = torch.empty_like(rd)
         L.lcmg_apply_vcycle_dev(s.ctx, lams, rd, zd)

@@ -144,10 +144,13 @@ def test_l1_jacobi_is_convergent():
 
 
 def test_default_levels_rule():
-    assert mg.default_levels(256, 256) == 6      # 256 -> 8
-    assert mg.default_levels(256, 256, 16) == 5  # 256 -> 16
-    assert mg.default_levels(32, 32) == 3        # 32 -> 8
-    assert mg.default_levels(40, 24) == 4        # 40 -> 20 -> 10 -> 5 (24 -> 12 -> 6 -> 3)
+    assert mg.default_levels(256, 256) == 5      # 256 -> 16
+    assert mg.default_levels(256, 256, 8) == 6   # 256 -> 8
+    assert mg.default_levels(512, 512) == 6      # 512 -> 16
+    assert mg.default_levels(32, 32) == 2        # 32 -> 16
+    assert mg.default_levels(32, 32, 8) == 3     # 32 -> 8
+    assert mg.default_levels(40, 24) == 3        # 40 -> 20 -> 10 (24 -> 12 -> 6)
+    assert mg.default_levels(40, 24, 4) == 4     # 40 -> 20 -> 10 -> 5
     assert mg.default_levels(33, 32) == 1        # odd side: no coarsening
     with pytest.raises(ValueError):
         mg.level_shapes(12, 12, 4)               # 12 -> 6 -> 3 -> (odd)
