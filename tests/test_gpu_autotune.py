@@ -52,7 +52,7 @@ def test_autotuned_solves_reach_oracle_and_keep_their_choice(nlam):
     P = pg.make_problem("ct256", size=64)
     d = np.ones(ops.n_edges(64, 64))
     lams = np.array([0.05, 0.3, 2.0])[:nlam]
-    s = Solver(64, 64, autotune=1, precision=L.PREC_MIXED, tol=1e-10, maxit=20000)
+    s = Solver(64, 64, autotune=1, precision=L.PREC_MIXED, tol=1e-12, maxit=20000)
     s.set_forward_csr(P.A)
     out = s.solve(lams, P.b[:, 0])
     st1 = s.stats()
