@@ -142,6 +142,11 @@ typedef struct {
                            (unless autotuned): 0 = per-pass default (32 lanes x
                            4 nonzeros for A p, 8 x 8 for the transposed pass);
                            1 = 32 x 4, 2 = 16 x 8, 3 = 8 x 8                    */
+  int32_t stop_rule;    /* outer loop of Algorithm 2: 0 = stop after three equal
+                           selections (Sec. 3.5, default); 1 = stop once
+                           ||L x*||_2 decreases from one outer iteration to the
+                           next (the heuristic of Gazzola et al. that Sec. 3.5
+                           compares against); x_out is then the last selection */
 } lcmg_params;
 
 typedef struct lcmg_ctx lcmg_ctx;

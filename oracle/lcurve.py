@@ -89,3 +89,10 @@ def lambda_window(m: int, i_prev: int):
 def should_stop(history) -> bool:
     """history: selected 1-based lambda indices, one per outer iteration."""
     return len(history) >= 3 and history[-1] == history[-2] == history[-3]
+
+
+def should_stop_lx(lx_history) -> bool:
+    """The heuristic of Gazzola et al. that Sec. 3.5 compares against: stop
+    once ||L x^(*,l)||_2 has decreased from outer iteration l-1 to l.
+    lx_history: ||L x*||_2 per outer iteration."""
+    return len(lx_history) >= 2 and lx_history[-1] < lx_history[-2]

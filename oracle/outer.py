@@ -6,8 +6,9 @@ Sec. 3.4), build the multigrid hierarchy for the current weights D^(l)
 lambda in the window from the largest to the smallest, each warm-started
 from the previous lambda's solution and the first from x^(*, l-1) (zero at
 l = 1) (Sec. 3.3), evaluate the L-curve and select its corner, stop when
-three consecutive selections agree (Sec. 3.5), else update the weights by
-eq. (g).  D^(1) = I (Sec. 2).
+three consecutive selections agree (Sec. 3.5; or, with stop_rule = 1, when
+||L x*||_2 decreases between outer iterations, the heuristic Sec. 3.5
+compares against), else update the weights by eq. (g).  D^(1) = I (Sec. 2).
 """
 from __future__ import annotations
 
@@ -33,6 +34,7 @@ class Params:
     d_min: float = 1e-3
     tol: float = 1e-6
     maxit: int = 10000
+    stop_rule: int = 0     # 0: three equal selections (Sec. 3.5); 1: ||L x*|| decreases
 
 
 @dataclass
@@ -81,6 +83,7 @@ class RunResult:
     history: list
     records: list = field(default_factory=list)
     d: np.ndarray | None = None
+    lx: list = field(default_factory=list)   # ||L x*||_2 per outer iteration
 
 
 def lcurve_run(problem, params: Params, rhs_index: int = 0, max_outer: int = 15,
@@ -92,7 +95,7 @@ def lcurve_run(problem, params: Params, rhs_index: int = 0, max_outer: int = 15,
     c = ops.rhs(S.F, b)
     d = np.ones(ops.n_edges(S.n_v, S.n_h))
     x_star = np.zeros(S.F.n)
-    hist, recs = [], []
+    hist, recs, lx = [], [], []
     for ell in range(1, max_outer + 1):
         lo, hi = lcurve.lambda_window(m, hist[-1] if hist else 0)
         hier = hierarchy(S, d, params)
@@ -111,7 +114,10 @@ def lcurve_run(problem, params: Params, rhs_index: int = 0, max_outer: int = 15,
         hist.append(sel)
         x_star = xs[sel - lo]
         recs.append(OuterRecord((lo, hi), lam_all[lo - 1:hi], rho, eta, its, sts, sel))
-        if lcurve.should_stop(hist):
+        lx.append(float(np.linalg.norm(S.L @ x_star)))
+        if params.stop_rule == 1 and lcurve.should_stop_lx(lx):
+            break
+        if params.stop_rule == 0 and lcurve.should_stop(hist):
             break
         d = lcurve.update_weights(d, S.L, x_star, params.q, params.d_min)
-    return RunResult(x_star, hist, recs, d)
+    return RunResult(x_star, hist, recs, d, lx)

@@ -113,6 +113,8 @@ struct lcmg_ctx {
   DevBuf<int64_t> ck_nz, ckT_nz;
   int64_t nck = 0, nckT = 0;
   DevBuf<int> spmm_err;  // set by a staged SpMM whose stage wait gave up
+  DevBuf<double> ones;   // n ones (unweighted gradient norm)
+  bool ones_ok = false;
   std::map<int, lcmg::Tuned> tuned;  // autotuner choices per (batch width, precision)
   int rv = 0, rh = 0;
   DevBuf<double> psf64;
@@ -240,6 +242,7 @@ static void check_params(const lcmg_params& p) {
   if (p.keep_direction != 0 && p.keep_direction != 1) throw ArgError("keep_direction must be 0 or 1");
   if (p.autotune != 0 && p.autotune != 1) throw ArgError("autotune must be 0 or 1");
   if (p.spmv_variant < 0 || p.spmv_variant > 3) throw ArgError("spmv_variant must be 0..3");
+  if (p.stop_rule != 0 && p.stop_rule != 1) throw ArgError("stop_rule must be 0 or 1");
 }
 
 static int sum_blocks(int nb) { return std::max(1, std::min(nb, kMaxBlocks)); }
@@ -1222,6 +1225,24 @@ struct StatsScope {
   ~StatsScope() { c.stats.kernel_launches = launch_counter() - l0; }
 };
 
+// ||L x||_2 of one device vector (unweighted gradient)
+static double grad_norm(lcmg_ctx& c, const double* x) {
+  double* ones = c.ones.need(c.n);
+  if (!c.ones_ok) {
+    std::vector<double> h(c.n, 1.0);
+    copy_sync(c.stream, ones, h.data(), sizeof(double) * c.n, cudaMemcpyHostToDevice);
+    c.ones_ok = true;
+  }
+  const int g = grid_for(c.n, 1, c.maxblk);
+  klaunch(k_seminorm, dim3(g), dim3(kBlock), 0, c.stream, c.nv, c.nh, 1, ones, ones, x, c.part_x.p);
+  LCMG_LAUNCHED();
+  klaunch(k_sum_parts, dim3(1), dim3(kScalarThreads), 0, c.stream, 1, g, c.part_x.p, c.s_out.p);
+  LCMG_LAUNCHED();
+  double v = 0.0;
+  copy_sync(c.stream, &v, c.s_out.p, sizeof(double), cudaMemcpyDeviceToHost);
+  return std::sqrt(v);
+}
+
 static void lcurve_run_impl(lcmg_ctx& c, int m, const double* lam, int max_outer, double* x_out_dev,
                             int* hist, int* n_outer, int64_t* n_solves, int64_t* n_conv) {
   check_lambdas(m, lam);
@@ -1235,6 +1256,7 @@ static void lcurve_run_impl(lcmg_ctx& c, int m, const double* lam, int max_outer
   LCMG_CUDA(cudaMemsetAsync(xstar.p, 0, sizeof(double) * n, c.stream));
   std::vector<int> solved(m, 0);
   std::vector<int> h;
+  std::vector<double> lx;  // ||L x*||_2 per outer iteration (stop_rule 1)
   int64_t ns = 0, nconv = 0;
   int ell = 0;
   for (ell = 1; ell <= max_outer; ++ell) {
@@ -1280,7 +1302,12 @@ static void lcurve_run_impl(lcmg_ctx& c, int m, const double* lam, int max_outer
     LCMG_CUDA(cudaMemcpyAsync(xstar.p, xwin.p + (int64_t)(sel - lo) * n, sizeof(double) * n,
                               cudaMemcpyDeviceToDevice, c.stream));
     const int L = (int)h.size();
-    if (L >= 3 && h[L - 1] == h[L - 2] && h[L - 2] == h[L - 3]) break;
+    if (c.prm.stop_rule == 1) {
+      lx.push_back(grad_norm(c, xstar.p));
+      if (L >= 2 && lx[L - 1] < lx[L - 2]) break;
+    } else if (L >= 3 && h[L - 1] == h[L - 2] && h[L - 2] == h[L - 3]) {
+      break;
+    }
     if (ell == max_outer) break;
     update_weights_dev(c, xstar.p, c.prm.q, c.prm.d_min);
   }
@@ -1350,6 +1377,7 @@ void lcmg_default_params(lcmg_params* p) {
   p->keep_direction = 0;
   p->autotune = 0;
   p->spmv_variant = 0;
+  p->stop_rule = 0;
 }
 
 const char* lcmg_last_error(void) { return lcmg::g_err.c_str(); }
@@ -1423,6 +1451,7 @@ int lcmg_set_grid(lcmg_ctx* ctx, int32_t n_v, int32_t n_h) {
   ctx->ne = (int64_t)n_h * (n_v - 1) + (int64_t)(n_h - 1) * n_v;
   ctx->fwd = 0;
   ctx->tuned.clear();
+  ctx->ones_ok = false;
   std::vector<double> ones(ctx->ne, 1.0);
   lcmg::copy_sync(ctx->stream, ctx->d.need(ctx->ne), ones.data(), sizeof(double) * ctx->ne, cudaMemcpyHostToDevice);
   lcmg::refresh_fine(*ctx);

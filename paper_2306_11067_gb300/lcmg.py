@@ -44,7 +44,8 @@ class lcmg_params(C.Structure):
                 ("vfuse", C.c_int32),
                 ("keep_direction", C.c_int32),
                 ("autotune", C.c_int32),
-                ("spmv_variant", C.c_int32)]
+                ("spmv_variant", C.c_int32),
+                ("stop_rule", C.c_int32)]
 
 
 class lcmg_stats(C.Structure):

@@ -115,6 +115,20 @@ def gaussian_psf(radius: int, sigma: float) -> np.ndarray:
     return psf / psf.sum()
 
 
+def separable_psf(n_v: int, n_h: int, band_v: int = 7, band_h: int = 8, s_v: float = 1.25,
+                  s_h: float = 1.5) -> np.ndarray:
+    """Anisotropic separable blur of the deblurring experiment (Sec. 4): the
+    product of a vertical and a horizontal 1-D Gaussian, each truncated to
+    |offset| < band and with width s * side / 64 pixels, each normalised so
+    that its two-sided sum is 1.  Returns the (2 band_v - 1) x (2 band_h - 1)
+    PSF (vertical offsets along rows)."""
+    def one_d(band, sigma):
+        half = np.exp(-(np.arange(band, dtype=np.float64) ** 2) / (2.0 * sigma * sigma))
+        half /= 2.0 * half.sum() - half[0]
+        return np.concatenate([half[:0:-1], half])
+    return np.outer(one_d(band_v, s_v * n_v / 64.0), one_d(band_h, s_h * n_h / 64.0))
+
+
 def blur_apply(img: np.ndarray, psf: np.ndarray) -> np.ndarray:
     """(A x)(i, j) = sum_{u,v} psf[u+r_v, v+r_h] x(i+u, j+v), zero outside."""
     from scipy.ndimage import correlate
@@ -311,10 +325,15 @@ def make_problem(name: str, size: int | None = None, n_rhs: int | None = None) -
         kind = "csr"
     elif w["op"] == "blur":
         psf = gaussian_psf(w["radius"], w["sigma"])
+    elif w["op"] == "blur_aniso":
+        psf = separable_psf(N, N)
     elif w["op"] == "ct":
-        na = w["angles"] if size is None else max(8, round(w["angles"] * N / w["side"]))
         nb = w["bins"] if size is None else int(2 * math.ceil(N * 1.42 / 2) - 1)
-        A = ct_csr(N, na, nb, dtype=np.float32)
+        if "angles_deg" in w:  # fixed angle set, whatever the size
+            A = ct_csr(N, len(w["angles_deg"]), nb, dtype=np.float32, angles_deg=w["angles_deg"])
+        else:
+            na = w["angles"] if size is None else max(8, round(w["angles"] * N / w["side"]))
+            A = ct_csr(N, na, nb, dtype=np.float32)
     xs, bs = [], []
     for r in range(nr):
         seed = w["seed"] + r
@@ -357,6 +376,16 @@ WORKLOADS = {
                       phantom="mixed", count=8, seed=2, n_rhs=4, noise=0.01,
                       noise_seed=1002, lam_lo=-5.0, lam_hi=0.0, n_lambda=32, levels=6,
                       tol=1e-6, max_outer=5),
+    # Workload variants of Sec. 4: limited-angle CT (angles 0, 2, ..., 130
+    # degrees) and deblurring with the anisotropic separable blur, both on
+    # piecewise-constant phantoms standing in for the paper's grains image.
+    "ct256_limited": dict(side=256, kind="csr", op="ct", angles=66, bins=363,
+                          angles_deg=[2.0 * a for a in range(66)], phantom="mixed", count=20,
+                          seed=11, noise=0.01, noise_seed=1011, lam_lo=-4.0, lam_hi=0.0,
+                          n_lambda=20, levels=0, tol=1e-6, max_outer=15),
+    "deblur256_aniso": dict(side=256, kind="stencil", op="blur_aniso", phantom="mixed", count=20,
+                            seed=12, noise=0.01, noise_seed=1012, lam_lo=-5.0, lam_hi=0.0,
+                            n_lambda=32, levels=0, tol=1e-6, max_outer=15),
     # 2048x2048 deblurring, 31x31 Gaussian sigma 5, 64 lambdas in [1e-6, 1],
     # 10 levels, 2% noise.
     "deblur2048": dict(side=2048, kind="stencil", op="blur", radius=15, sigma=5.0,

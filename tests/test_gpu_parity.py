@@ -385,3 +385,39 @@ def test_fold_and_pdl_paths_reach_oracle(fold, pdl, precision):
                                mg.VCycle(H, lam), tol=1e-12, maxit=20000)
             assert out["status"][0, j] == 0
             assert _rel(out["x"][0, j], x) <= bound
+
+
+@pytest.mark.parametrize("mode", [L.MODE_SEQUENTIAL, L.MODE_BATCHED])
+def test_lcurve_run_lx_stop_rule_matches_oracle(mode):
+    """stop_rule 1 (stop once ||L x*|| decreases): the same selections, the
+    same stopping iteration and the same final solution as the oracle."""
+    P = pg.make_problem("deblur32_csr", size=16)
+    lams = np.logspace(-4, 1, 14)
+    ref = outer.lcurve_run(P, outer.Params(levels=2, tol=1e-12, stop_rule=1), max_outer=8, lambdas=lams)
+    s = _solver(P, levels=2, tol=1e-12, stop_rule=1, mode=mode, maxit=20000)
+    r = s.lcurve_run(lams, P.b[:, 0], max_outer=8)
+    s.close()
+    assert [int(h) for h in r["history"]] == ref.history
+    assert _rel(r["x"], ref.x) <= 1e-8
+
+
+@pytest.mark.parametrize("name,N", [("ct256_limited", 40), ("deblur256_aniso", 32)])
+@pytest.mark.parametrize("precision,bound", [(L.PREC_FP64, 1e-8), (L.PREC_MIXED, 1e-6)])
+def test_workload_variants_solve_parity(name, N, precision, bound):
+    """Limited-angle CT and the anisotropic separable blur (Sec. 4 variants)."""
+    P = pg.make_problem(name, size=N)
+    d = pg.random_weights(ops.n_edges(N, N), 8, d_min=0.05)
+    lams = np.array([0.01, 0.2])
+    s = _solver(P, levels=3, tol=1e-12, precision=precision, maxit=20000)
+    s.set_weights(d)
+    out = s.solve(lams, P.b[:, 0])
+    s.close()
+    F = ops.make_forward(P)
+    Lg = ops.gradient(N, N)
+    H = mg.build_hierarchy(mg.weighted_laplacian(Lg, d), sp.diags(F.diag_AtA()), N, N, 3)
+    c = ops.rhs(F, P.b[:, 0])
+    for j, lam in enumerate(lams):
+        x, *_ = krylov.pcg(lambda v: ops.normal_apply(F, Lg, d, lam, v), c, None, mg.VCycle(H, lam),
+                           tol=1e-12, maxit=20000)
+        assert out["status"][0, j] == 0
+        assert _rel(out["x"][0, j], x) <= bound

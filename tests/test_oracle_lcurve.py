@@ -123,5 +123,13 @@ def test_should_stop():
     assert lcurve.should_stop([3, 3, 3])
     assert not lcurve.should_stop([3, 4, 4])
     assert not lcurve.should_stop([2, 2])
+
+
+def test_should_stop_lx_stops_at_the_first_decrease():
+    assert not lcurve.should_stop_lx([5.0])
+    assert not lcurve.should_stop_lx([5.0, 5.0])        # equal is not a decrease
+    assert not lcurve.should_stop_lx([5.0, 6.0])
+    assert lcurve.should_stop_lx([5.0, 6.0, 5.9])
+    assert lcurve.should_stop_lx([5.0, 4.0])
     assert lcurve.should_stop([1, 2, 2, 2])
     assert not lcurve.should_stop([5, 5, 6, 6])

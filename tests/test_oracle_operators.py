@@ -129,3 +129,30 @@ def test_blur_csr_explicit_entry():
             assert A[row, (i + u) + (j + v) * 5] == psf[u + 1, v + 1]
     # zero boundary: pixel (0, 0) has only the 2 x 2 in-range neighbours
     assert sorted(A[0][A[0] != 0]) == [4.0, 5.0, 7.0, 8.0]
+
+
+def test_separable_psf_definition():
+    """The anisotropic blur of the deblurring experiment: separable (rank 1),
+    symmetric, each 1-D factor a truncated Gaussian of width s * side / 64
+    whose two-sided sum is 1."""
+    n_v, n_h = 64, 128
+    psf = pg.separable_psf(n_v, n_h)
+    assert psf.shape == (13, 15)
+    assert np.allclose(psf, psf[::-1, :]) and np.allclose(psf, psf[:, ::-1])
+    sv = np.linalg.svd(psf, compute_uv=False)
+    assert sv[1] <= 1e-14 * sv[0]
+    kv, kh = psf.sum(axis=1), psf.sum(axis=0)
+    assert abs(kv.sum() - 1.0) <= 1e-14 and abs(kh.sum() - 1.0) <= 1e-14
+    sig_v, sig_h = 1.25 * n_v / 64, 1.5 * n_h / 64
+    for k, sig, c in ((kv, sig_v, 6), (kh, sig_h, 7)):
+        for off in range(1, c + 1):
+            assert abs(k[c + off] / k[c] - np.exp(-off * off / (2 * sig * sig))) <= 1e-14
+
+
+def test_limited_angle_ct_workload():
+    P = pg.make_problem("ct256_limited", size=32)
+    nb = P.A.m // 66
+    assert P.A.m == 66 * nb and P.n == 32 * 32
+    # angles 0 .. 130 degrees: the 66th angle's rays differ from the 0-degree ones
+    A = P.A.to_scipy()
+    assert A[:nb].nnz > 0 and A[65 * nb:].nnz > 0

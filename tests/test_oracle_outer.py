@@ -17,6 +17,7 @@ import pytest
 import problemgen as pg
 from oracle import outer
 from oracle import lcurve
+from oracle import operators as ops
 
 
 def test_rho_eta_monotone_in_lambda():
@@ -66,3 +67,18 @@ def test_generator_ct_cavalieri():
     inside = np.abs(s) < N / 2
     assert np.allclose(r[0, inside], N)
     assert A.col.dtype == np.int32 and A.val.dtype == np.float32
+
+
+def test_outer_loop_lx_rule():
+    """stop_rule 1: the run ends at the first outer iteration whose
+    ||L x*||_2 is below the previous one (or at max_outer), and the
+    recorded norms are those of the selected solutions."""
+    P = pg.make_problem("deblur32_csr", size=16)
+    lams = np.logspace(-4, 1, 14)
+    r = outer.lcurve_run(P, outer.Params(levels=2, tol=1e-8, stop_rule=1), max_outer=8, lambdas=lams)
+    assert len(r.lx) == len(r.history)
+    for k in range(1, len(r.lx) - 1):
+        assert r.lx[k] >= r.lx[k - 1]
+    assert lcurve.should_stop_lx(r.lx) or len(r.lx) == 8
+    Lg = ops.gradient(16, 16)
+    assert abs(np.linalg.norm(Lg @ r.x) - r.lx[-1]) <= 1e-12 * r.lx[-1]
