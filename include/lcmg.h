@@ -147,6 +147,15 @@ typedef struct {
                            ||L x*||_2 decreases from one outer iteration to the
                            next (the heuristic of Gazzola et al. that Sec. 3.5
                            compares against); x_out is then the last selection */
+  int32_t precond;      /* 0 = PCG with the V-cycle on lam^2 L^T D^2 L + diag(A^T A)
+                           (default); 1 = the paper's own method (Sec. 3.2-3.3):
+                           FGMRES preconditioned by a V(2,1) cycle on the whole
+                           normal operator with one-sided coarse operators
+                           A_{k+1} = A_k P_k, Jacobi-preconditioned CG relaxation
+                           and an exact coarsest solve; CSR forward operators,
+                           FP64, one lambda at a time (lcmg_apply_vcycle_dev then
+                           applies this cycle)                                   */
+  int32_t gmres_restart; /* FGMRES basis size before a restart (1..2000; 200)     */
 } lcmg_params;
 
 typedef struct lcmg_ctx lcmg_ctx;

@@ -19,6 +19,7 @@
 #include "launch.h"
 #include "spmm_staged.cuh"
 #include "vfused.cuh"
+#include "paper_mg.cuh"
 #include "mega.cuh"
 #include "tail.cuh"
 #include "tail_launch.h"
@@ -74,6 +75,21 @@ struct LevelWork {
   DevBuf<char> rhs, z, t, res, dinv;  // T-typed, n_k x B
 };
 
+// One level of the paper's one-sided hierarchy (params.precond = 1):
+// A_k (rows of A, n_k columns) and its transpose, FP64, and diag(A_k^T A_k).
+// Level 0 uses the forward operator itself.
+struct PmLevel {
+  int64_t nnz = 0;
+  DevBuf<int64_t> rp, rpT;
+  DevBuf<int32_t> ci, ciT;
+  DevBuf<double> v, vT, dA;
+};
+
+// One-column workspace of a level of the paper's cycle.
+struct PmWork {
+  DevBuf<double> b, x, r, z, p, q, t, y, dinv, pa, pb, ppq;
+};
+
 constexpr int kMaxBlocks = 2048;
 // widest batch for which params.vfuse = 1 picks the two-kernels-per-level
 // V-cycle (its blocks read one column each: wider batches read strided)
@@ -116,6 +132,12 @@ struct lcmg_ctx {
   DevBuf<double> ones;   // n ones (unweighted gradient norm)
   bool ones_ok = false;
   std::map<int, lcmg::Tuned> tuned;  // autotuner choices per (batch width, precision)
+  // the paper's own preconditioner (params.precond = 1)
+  std::vector<lcmg::PmLevel> pm;
+  std::vector<lcmg::PmWork> pmw;
+  DevBuf<double> pm_AtAc;            // dense A_c^T A_c of the coarsest level
+  int pm_levels = 0;                 // levels the one-sided hierarchy was built for (0: none)
+  DevBuf<double> pm_V, pm_Z, pm_w, pm_r, pm_h, pm_part, pm_y;
   int rv = 0, rh = 0;
   DevBuf<double> psf64;
   DevBuf<float> psf32;
@@ -243,6 +265,8 @@ static void check_params(const lcmg_params& p) {
   if (p.autotune != 0 && p.autotune != 1) throw ArgError("autotune must be 0 or 1");
   if (p.spmv_variant < 0 || p.spmv_variant > 3) throw ArgError("spmv_variant must be 0..3");
   if (p.stop_rule != 0 && p.stop_rule != 1) throw ArgError("stop_rule must be 0 or 1");
+  if (p.precond != 0 && p.precond != 1) throw ArgError("precond must be 0 or 1");
+  if (p.gmres_restart < 1 || p.gmres_restart > 2000) throw ArgError("gmres_restart must be 1..2000");
 }
 
 static int sum_blocks(int nb) { return std::max(1, std::min(nb, kMaxBlocks)); }
@@ -1015,6 +1039,403 @@ static void compute_rhs(lcmg_ctx& c, int nrhs) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// The paper's own preconditioner and Krylov method (params.precond = 1,
+// Sec. 3.2-3.3): multigrid on the whole normal operator with the one-sided
+// coarse operators A_{k+1} = A_k P_k (M_k^T M_k is the Galerkin stencil
+// G_L^k already held for the default preconditioner), V(2,1) with
+// Jacobi-preconditioned CG relaxation, an exact coarsest solve of
+// A_c^T A_c + lam^2 G_L^c, and right-preconditioned flexible GMRES.  FP64,
+// one column at a time (the paper's lambda chain).
+// ---------------------------------------------------------------------------
+constexpr int kPmNu1 = 2, kPmNu2 = 1;  // CG relaxation steps before / after the coarse correction
+
+struct HostCsr {
+  int64_t rows = 0, cols = 0;
+  std::vector<int64_t> rp;
+  std::vector<int32_t> ci;
+  std::vector<double> v;
+};
+
+// weight of coarse cell I in the cell-centred linear interpolation to fine
+// cell a (nc coarse cells; an outside neighbour's weight goes to the parent)
+static double interp_w(int a, int I, int nc) {
+  const int d = a - 2 * I;
+  if (d == 0) return I == 0 ? 1.0 : 0.75;
+  if (d == 1) return I == nc - 1 ? 1.0 : 0.75;
+  if (d == -1 || d == 2) return 0.25;
+  return 0.0;
+}
+
+// A P for P = P_h (x) P_v from the nv/2 x nh/2 grid to the nv x nh grid;
+// each row is accumulated in the order of its nonzeros, then sorted
+static HostCsr times_p(const HostCsr& A, int nv, int nh) {
+  const int nvc = nv / 2, nhc = nh / 2;
+  HostCsr Bm;
+  Bm.rows = A.rows;
+  Bm.cols = (int64_t)nvc * nhc;
+  Bm.rp.assign(A.rows + 1, 0);
+  std::vector<double> acc(Bm.cols, 0.0);
+  std::vector<int64_t> mark(Bm.cols, -1);
+  std::vector<int32_t> touched;
+  for (int64_t r = 0; r < A.rows; ++r) {
+    touched.clear();
+    for (int64_t k = A.rp[r]; k < A.rp[r + 1]; ++k) {
+      const int c = A.ci[k];
+      const double v = A.v[k];
+      const int j = c / nv, i = c - j * nv;
+      const int Is[2] = {i >> 1, (i & 1) ? (i >> 1) + 1 : (i >> 1) - 1};
+      const int Js[2] = {j >> 1, (j & 1) ? (j >> 1) + 1 : (j >> 1) - 1};
+      for (int u = 0; u < 2; ++u) {
+        const int J = Js[u];
+        if (J < 0 || J >= nhc) continue;
+        const double wj = interp_w(j, J, nhc);
+        for (int t = 0; t < 2; ++t) {
+          const int I = Is[t];
+          if (I < 0 || I >= nvc) continue;
+          const int32_t col = I + J * nvc;
+          if (mark[col] != r) {
+            mark[col] = r;
+            acc[col] = 0.0;
+            touched.push_back(col);
+          }
+          acc[col] += v * (wj * interp_w(i, I, nvc));
+        }
+      }
+    }
+    std::sort(touched.begin(), touched.end());
+    for (int32_t col : touched) {
+      Bm.ci.push_back(col);
+      Bm.v.push_back(acc[col]);
+    }
+    Bm.rp[r + 1] = (int64_t)Bm.ci.size();
+  }
+  return Bm;
+}
+
+static HostCsr transpose(const HostCsr& A) {
+  HostCsr T;
+  T.rows = A.cols;
+  T.cols = A.rows;
+  T.rp.assign(A.cols + 1, 0);
+  for (int32_t c : A.ci) T.rp[c + 1]++;
+  for (int64_t i = 0; i < A.cols; ++i) T.rp[i + 1] += T.rp[i];
+  T.ci.resize(A.ci.size());
+  T.v.resize(A.v.size());
+  std::vector<int64_t> pos(T.rp.begin(), T.rp.end() - 1);
+  for (int64_t r = 0; r < A.rows; ++r)
+    for (int64_t k = A.rp[r]; k < A.rp[r + 1]; ++k) {
+      const int64_t d = pos[A.ci[k]]++;
+      T.ci[d] = (int32_t)r;
+      T.v[d] = A.v[k];
+    }
+  return T;
+}
+
+static void pm_build(lcmg_ctx& c) {
+  ensure_hierarchy(c);
+  const int L = (int)c.lev.size();
+  if (c.pm_levels == L) return;
+  if (c.fwd != 1) throw ArgError("the paper's preconditioner needs a CSR forward operator");
+  if (L < 2) throw ArgError("the paper's preconditioner needs at least 2 levels");
+  cudaStream_t s = c.stream;
+  HostCsr A;
+  A.rows = c.m;
+  A.cols = c.n;
+  A.rp.resize(c.m + 1);
+  A.ci.resize(c.nnz);
+  A.v.resize(c.nnz);
+  copy_sync(s, A.rp.data(), c.rp.p, sizeof(int64_t) * (c.m + 1), cudaMemcpyDeviceToHost);
+  copy_sync(s, A.ci.data(), c.ci.p, sizeof(int32_t) * c.nnz, cudaMemcpyDeviceToHost);
+  if (c.vdtype == 1) {
+    copy_sync(s, A.v.data(), c.v64.p, sizeof(double) * c.nnz, cudaMemcpyDeviceToHost);
+  } else {
+    std::vector<float> vf(c.nnz);
+    copy_sync(s, vf.data(), c.v32.p, sizeof(float) * c.nnz, cudaMemcpyDeviceToHost);
+    for (int64_t k = 0; k < c.nnz; ++k) A.v[k] = vf[k];
+  }
+  c.pm.clear();
+  c.pm.resize(L);
+  for (int k = 1; k < L; ++k) {
+    A = times_p(A, c.lev[k - 1].nv, c.lev[k - 1].nh);
+    HostCsr T = transpose(A);
+    PmLevel& P = c.pm[k];
+    P.nnz = (int64_t)A.ci.size();
+    copy_sync(s, P.rp.need(A.rows + 1 + kCsrPad), A.rp.data(), sizeof(int64_t) * (A.rows + 1), cudaMemcpyHostToDevice);
+    copy_sync(s, P.ci.need(P.nnz + kCsrPad), A.ci.data(), sizeof(int32_t) * P.nnz, cudaMemcpyHostToDevice);
+    copy_sync(s, P.v.need(P.nnz + kCsrPad), A.v.data(), sizeof(double) * P.nnz, cudaMemcpyHostToDevice);
+    copy_sync(s, P.rpT.need(T.rows + 1 + kCsrPad), T.rp.data(), sizeof(int64_t) * (T.rows + 1), cudaMemcpyHostToDevice);
+    copy_sync(s, P.ciT.need(P.nnz + kCsrPad), T.ci.data(), sizeof(int32_t) * P.nnz, cudaMemcpyHostToDevice);
+    copy_sync(s, P.vT.need(P.nnz + kCsrPad), T.v.data(), sizeof(double) * P.nnz, cudaMemcpyHostToDevice);
+    const int64_t nk = c.lev[k].n;
+    const int g = (int)std::min<int64_t>((nk * 32 + kBlock - 1) / kBlock, c.maxblk);
+    klaunch(k_diag_ata<double>, dim3(g), dim3(kBlock), 0, s, nk, P.rpT.p, P.vT.p, P.dA.need(nk));
+    LCMG_LAUNCHED();
+    if (k == L - 1) {  // dense A_c^T A_c, rows of A_c in order
+      const int64_t nc = nk;
+      std::vector<double> AtA((size_t)nc * nc, 0.0);
+      for (int64_t r = 0; r < A.rows; ++r)
+        for (int64_t a = A.rp[r]; a < A.rp[r + 1]; ++a)
+          for (int64_t b2 = A.rp[r]; b2 < A.rp[r + 1]; ++b2)
+            AtA[(size_t)A.ci[a] * nc + A.ci[b2]] += A.v[a] * A.v[b2];
+      copy_sync(s, c.pm_AtAc.need(nc * nc), AtA.data(), sizeof(double) * nc * nc, cudaMemcpyHostToDevice);
+    }
+  }
+  c.pmw.clear();
+  c.pmw.resize(L);
+  for (int k = 0; k < L; ++k) {
+    PmWork& W = c.pmw[k];
+    const int64_t nk = c.lev[k].n;
+    W.b.need(nk); W.x.need(nk);
+    if (k + 1 < L) {
+      for (auto* b : {&W.r, &W.z, &W.p, &W.q, &W.t, &W.dinv}) b->need(nk);
+      W.y.need(c.m);
+      for (auto* b : {&W.pa, &W.pb, &W.ppq}) b->need(kMaxBlocks);
+    }
+  }
+  LCMG_CUDA(cudaStreamSynchronize(s));
+  c.pm_levels = L;
+}
+
+struct PaperMG {
+  lcmg_ctx& c;
+  cudaStream_t s;
+  int L;
+  explicit PaperMG(lcmg_ctx& c_) : c(c_), s(c_.stream), L((int)c_.lev.size()) {}
+
+  int grid(int k) const { return grid_for(c.lev[k].n, 1, c.maxblk); }
+  GLOp glop(int k) const { return GLOp{c.lev[k].nv, c.lev[k].nh, c.lev[k].n, c.lev[k].gl.p}; }
+  FineOp<double> fop() const { return view<double>(c, 0).fine_op(); }
+
+  // y = A_k x, t = A_k^T y
+  void passes(int k, const double* x, double* y, double* t) {
+    const FineOp<double> f = fop();
+    if (k == 0) {
+      SpmmArgs a = csr_args(c, false, 1), at = csr_args(c, true, 1);
+      if (c.vdtype == 1) {
+        launch_spmm<double, double, double, 0>(a, c.v64.p, x, y, f, nullptr, nullptr, nullptr, nullptr, nullptr, c.maxblk, s);
+        launch_spmm<double, double, double, 0>(at, c.vT64.p, y, t, f, nullptr, nullptr, nullptr, nullptr, nullptr, c.maxblk, s);
+      } else {
+        launch_spmm<float, double, double, 0>(a, c.v32.p, x, y, f, nullptr, nullptr, nullptr, nullptr, nullptr, c.maxblk, s);
+        launch_spmm<float, double, double, 0>(at, c.vT32.p, y, t, f, nullptr, nullptr, nullptr, nullptr, nullptr, c.maxblk, s);
+      }
+      return;
+    }
+    const PmLevel& P = c.pm[k];
+    SpmmArgs a{};
+    a.rows = c.m; a.rp = P.rp.p; a.ci = P.ci.p; a.B = 1; a.nb = 1; a.nl = 1; a.nrhs = 1;
+    SpmmArgs at = a;
+    at.rows = c.lev[k].n; at.rp = P.rpT.p; at.ci = P.ciT.p;
+    launch_spmm<double, double, double, 0>(a, P.v.p, x, y, f, nullptr, nullptr, nullptr, nullptr, nullptr, c.maxblk, s);
+    launch_spmm<double, double, double, 0>(at, P.vT.p, y, t, f, nullptr, nullptr, nullptr, nullptr, nullptr, c.maxblk, s);
+  }
+  // MODE 0: q = K_k x with partials of x.q; MODE 1: q = b - K_k x
+  template <int MODE>
+  void apply(int k, const double* x, const double* b, double* q, double* part) {
+    PmWork& W = c.pmw[k];
+    passes(k, x, W.y.p, W.t.p);
+    const int g = grid(k);
+    if (k == 0)
+      klaunch(k_pm_lap_add<FineOp<double>, MODE>, dim3(g), dim3(kBlock), 0, s, fop(), c.lev[k].n, c.lam2.p, x, W.t.p, b, q, part);
+    else
+      klaunch(k_pm_lap_add<GLOp, MODE>, dim3(g), dim3(kBlock), 0, s, glop(k), c.lev[k].n, c.lam2.p, x, W.t.p, b, q, part);
+    LCMG_LAUNCHED();
+  }
+  // `steps` CG steps on K_k x = b; zero_x: from x = 0, else from x with r = b - K x
+  void relax(int k, const double* b, double* x, int steps, bool zero_x) {
+    PmWork& W = c.pmw[k];
+    const int64_t n = c.lev[k].n;
+    const int g = grid(k);
+    if (!zero_x) apply<1>(k, x, b, W.r.p, nullptr);
+    klaunch(k_pm_cg_init, dim3(g), dim3(kBlock), 0, s, n, zero_x ? 1 : 0, b, W.dinv.p, x, W.r.p, W.z.p, W.p.p, W.pa.p);
+    LCMG_LAUNCHED();
+    double* cur = W.pa.p;
+    double* nxt = W.pb.p;
+    for (int st = 0; st < steps; ++st) {
+      apply<0>(k, W.p.p, nullptr, W.q.p, W.ppq.p);
+      klaunch(k_pm_cg_xr, dim3(g), dim3(kBlock), 0, s, n, cur, g, W.ppq.p, g, W.p.p, W.q.p, W.dinv.p, x, W.r.p,
+              W.z.p, nxt);
+      LCMG_LAUNCHED();
+      if (st + 1 < steps) {
+        klaunch(k_pm_cg_p, dim3(g), dim3(kBlock), 0, s, n, nxt, cur, g, W.z.p, W.p.p);
+        LCMG_LAUNCHED();
+      }
+      std::swap(cur, nxt);
+    }
+  }
+  // x = V-cycle(b) on level k (zero initial guess)
+  void cycle(int k, const double* b, double* x) {
+    if (k == L - 1) {
+      launch_coarse_solve<double>((int)c.lev[k].n, 1, c.kinv.p, b, x, s);
+      return;
+    }
+    PmWork& W = c.pmw[k];
+    PmWork& Wc = c.pmw[k + 1];
+    relax(k, b, x, kPmNu1, true);
+    apply<1>(k, x, b, W.r.p, nullptr);
+    launch_restrict<double>(c.lev[k + 1].nv, c.lev[k + 1].nh, 1, W.r.p, Wc.b.p, c.maxblk, s);
+    cycle(k + 1, Wc.b.p, Wc.x.p);
+    launch_prolong_add<double>(c.lev[k + 1].nv, c.lev[k + 1].nh, 1, Wc.x.p, x, c.maxblk, s);
+    relax(k, b, x, kPmNu2, false);
+  }
+  // per lambda: Jacobi diagonals and the coarsest factorisation
+  void setup(double lam) {
+    const double l2 = lam * lam;
+    copy_sync(s, c.lam2.p, &l2, sizeof(double), cudaMemcpyHostToDevice);
+    for (int k = 0; k + 1 < L; ++k) {
+      const int g = grid(k);
+      const double* dA = k == 0 ? c.diag.p : c.pm[k].dA.p;
+      if (k == 0)
+        klaunch(k_pm_dinv<FineOp<double>>, dim3(g), dim3(kBlock), 0, s, fop(), c.lev[0].n, c.lam2.p, dA, c.pmw[0].dinv.p);
+      else
+        klaunch(k_pm_dinv<GLOp>, dim3(g), dim3(kBlock), 0, s, glop(k), c.lev[k].n, c.lam2.p, dA, c.pmw[k].dinv.p);
+      LCMG_LAUNCHED();
+    }
+    const int64_t nc = c.lev[L - 1].n;
+    const int gd = (int)std::min<int64_t>((nc * nc + kBlock - 1) / kBlock, c.maxblk);
+    klaunch(k_pm_dense, dim3(gd), dim3(kBlock), 0, s, glop(L - 1), c.lam2.p, c.pm_AtAc.p, c.Mw.p);
+    LCMG_LAUNCHED();
+    klaunch(k_cholesky_inverse, dim3(1), dim3(kBlock), 0, s, (int)nc, c.Mw.p, c.Ww.p, c.kinv.p, c.s_info.p);
+    LCMG_LAUNCHED();
+    int info = 0;
+    copy_sync(s, &info, c.s_info.p, sizeof(int), cudaMemcpyDeviceToHost);
+    if (info != 0) throw ArgError("coarsest-level Cholesky failed (pivot " + std::to_string(info) + ")");
+  }
+  double dot(const double* a, const double* b) {
+    const int g = grid_for(c.n, 1, c.maxblk);
+    klaunch(k_col_dot<double>, dim3(g), dim3(kBlock), 0, s, c.n, 1, a, b, c.part_x.p);
+    LCMG_LAUNCHED();
+    klaunch(k_sum_parts, dim3(1), dim3(kScalarThreads), 0, s, 1, g, c.part_x.p, c.s_out.p);
+    LCMG_LAUNCHED();
+    double v = 0.0;
+    copy_sync(s, &v, c.s_out.p, sizeof(double), cudaMemcpyDeviceToHost);
+    return v;
+  }
+  // h[0 .. cnt) = V[0 .. cnt)^T w, then w -= V h (one classical Gram-Schmidt pass)
+  void cgs_pass(int cnt, double* w, double* h) {
+    const int64_t n = c.n;
+    const int nbd = (int)std::min<int64_t>((n + kBlock - 1) / kBlock, 128);
+    klaunch(k_pm_multidot, dim3(nbd, cnt), dim3(kBlock), 0, s, n, cnt, c.pm_V.p, n, w, c.pm_part.p);
+    LCMG_LAUNCHED();
+    klaunch(k_pm_sum_rows, dim3((cnt + kBlock / 32 - 1) / (kBlock / 32)), dim3(kBlock), 0, s, cnt, nbd, c.pm_part.p, h, 0);
+    LCMG_LAUNCHED();
+    klaunch(k_pm_orth, dim3(grid_for(n, 1, c.maxblk)), dim3(kBlock), 0, s, n, cnt, c.pm_V.p, n, h, w);
+    LCMG_LAUNCHED();
+  }
+
+  // FGMRES on K x = c for the batch's single column (x in c.x64, c in
+  // c.c64); writes its iteration count and status to s_iters / s_status
+  void run(double lam) {
+    if (c.prm.precision != LCMG_PREC_FP64) throw ArgError("the paper's preconditioner runs in FP64 (precision = FP64)");
+    pm_build(c);
+    L = (int)c.lev.size();
+    const int64_t n = c.n;
+    const int m = c.prm.gmres_restart;
+    c.pm_V.need((size_t)(m + 1) * n);
+    c.pm_Z.need((size_t)m * n);
+    c.pm_w.need(n);
+    c.pm_r.need(n);
+    c.pm_h.need(2 * (m + 2));
+    c.pm_part.need((size_t)(m + 1) * 128);
+    c.pm_y.need(m);
+    setup(lam);
+    cudaEvent_t e0, e1;
+    LCMG_CUDA(cudaEventCreate(&e0));
+    LCMG_CUDA(cudaEventCreate(&e1));
+    LCMG_CUDA(cudaEventRecord(e0, s));
+    double* x = c.x64.p;
+    const double* cv = c.c64.p;
+    const double cn = std::sqrt(dot(cv, cv));
+    const double tol = c.prm.tol;
+    const int maxit = c.prm.maxit;
+    int it = 0, st = LCMG_MAXIT;
+    if (cn == 0.0) {
+      fill_sync(s, x, 0, sizeof(double) * n);
+      st = LCMG_CONVERGED;
+    }
+    std::vector<double> H, g, cs, sn, hA(m + 2), hB(m + 2);
+    while (cn != 0.0) {
+      apply<1>(0, x, cv, c.pm_r.p, nullptr);
+      const double beta = std::sqrt(dot(c.pm_r.p, c.pm_r.p));
+      if (!std::isfinite(beta)) { st = LCMG_NONFINITE; break; }
+      if (beta <= tol * cn) { st = LCMG_CONVERGED; break; }
+      if (it >= maxit) { st = LCMG_MAXIT; break; }
+      const int mm = std::min(m, maxit - it);
+      klaunch(k_pm_scale, dim3(grid_for(n, 1, c.maxblk)), dim3(kBlock), 0, s, n, 1.0 / beta, (const double*)c.pm_r.p, c.pm_V.p);
+      LCMG_LAUNCHED();
+      H.assign((size_t)(mm + 1) * mm, 0.0);
+      g.assign(mm + 1, 0.0);
+      cs.assign(mm, 0.0);
+      sn.assign(mm, 0.0);
+      g[0] = beta;
+      auto Hc = [&](int i, int j) -> double& { return H[(size_t)i * mm + j]; };
+      int jd = 0;
+      bool breakdown = false, nonfinite = false;
+      for (int j = 0; j < mm; ++j) {
+        double* vj = c.pm_V.p + (int64_t)j * n;
+        double* zj = c.pm_Z.p + (int64_t)j * n;
+        cycle(0, vj, zj);
+        apply<0>(0, zj, nullptr, c.pm_w.p, c.pmw[0].ppq.p);
+        ++it;
+        cgs_pass(j + 1, c.pm_w.p, c.pm_h.p);
+        cgs_pass(j + 1, c.pm_w.p, c.pm_h.p + (m + 2));
+        copy_sync(s, hA.data(), c.pm_h.p, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost);
+        copy_sync(s, hB.data(), c.pm_h.p + (m + 2), sizeof(double) * (j + 1), cudaMemcpyDeviceToHost);
+        for (int i = 0; i <= j; ++i) Hc(i, j) = hA[i] + hB[i];
+        const double hn = std::sqrt(dot(c.pm_w.p, c.pm_w.p));
+        Hc(j + 1, j) = hn;
+        for (int i = 0; i <= j + 1; ++i)
+          if (!std::isfinite(Hc(i, j))) nonfinite = true;
+        if (nonfinite) break;
+        if (hn > 0.0) {
+          klaunch(k_pm_scale, dim3(grid_for(n, 1, c.maxblk)), dim3(kBlock), 0, s, n, 1.0 / hn,
+                  (const double*)c.pm_w.p, c.pm_V.p + (int64_t)(j + 1) * n);
+          LCMG_LAUNCHED();
+        }
+        for (int i = 0; i < j; ++i) {  // earlier rotations
+          const double t = cs[i] * Hc(i, j) + sn[i] * Hc(i + 1, j);
+          Hc(i + 1, j) = -sn[i] * Hc(i, j) + cs[i] * Hc(i + 1, j);
+          Hc(i, j) = t;
+        }
+        const double den = std::hypot(Hc(j, j), Hc(j + 1, j));
+        if (den == 0.0) { breakdown = true; break; }
+        cs[j] = Hc(j, j) / den;
+        sn[j] = Hc(j + 1, j) / den;
+        Hc(j, j) = den;
+        Hc(j + 1, j) = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        jd = j + 1;
+        if (std::fabs(g[j + 1]) <= tol * cn) break;
+      }
+      if (nonfinite) { st = LCMG_NONFINITE; break; }
+      if (jd > 0) {
+        std::vector<double> y(jd);
+        for (int i = jd - 1; i >= 0; --i) {  // back substitution
+          double t = g[i];
+          for (int k2 = i + 1; k2 < jd; ++k2) t -= Hc(i, k2) * y[k2];
+          y[i] = t / Hc(i, i);
+        }
+        copy_sync(s, c.pm_y.p, y.data(), sizeof(double) * jd, cudaMemcpyHostToDevice);
+        klaunch(k_pm_combine, dim3(grid_for(n, 1, c.maxblk)), dim3(kBlock), 0, s, n, jd, (const double*)c.pm_Z.p, n,
+                (const double*)c.pm_y.p, x);
+        LCMG_LAUNCHED();
+      }
+      if (breakdown && jd == 0) { st = LCMG_BREAKDOWN; break; }
+    }
+    LCMG_CUDA(cudaEventRecord(e1, s));
+    LCMG_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c.stats.iterate_ms += ms;
+    c.stats.batch_iterations += it;
+    copy_sync(s, c.s_iters.p, &it, sizeof(int), cudaMemcpyHostToDevice);
+    copy_sync(s, c.s_status.p, &st, sizeof(int), cudaMemcpyHostToDevice);
+  }
+};
+
 // Solve the columns cols (each = (lambda index li, rhs index ri)) as one
 // batch.  x0p: planar initial guesses per column (device, may be null) ;
 // outputs planar per column.
@@ -1027,6 +1448,12 @@ static void solve_columns(lcmg_ctx& c, const std::vector<ColSpec>& cols, int nrh
                           const std::vector<const double*>& x0, const std::vector<double*>& xout,
                           double* rho, double* eta, int* iters, int* status) {
   const int B = (int)cols.size();
+  if (c.prm.precond == 1 && B > 1) {  // the paper's method: one column at a time
+    for (int j = 0; j < B; ++j)
+      solve_columns(c, {cols[j]}, nrhs, {x0[j]}, {xout[j]}, rho ? rho + j : nullptr, eta ? eta + j : nullptr,
+                    iters ? iters + j : nullptr, status ? status + j : nullptr);
+    return;
+  }
   ensure_work(c, B);
   cudaStream_t s = c.stream;
   // column pointer tables and the column -> right-hand-side map
@@ -1049,7 +1476,9 @@ static void solve_columns(lcmg_ctx& c, const std::vector<ColSpec>& cols, int nrh
   LCMG_CUDA(cudaStreamSynchronize(s));  // host tables must outlive the copies
   std::vector<double> lam(B);
   for (int j = 0; j < B; ++j) lam[j] = cols[j].lam;
-  if (c.prm.precision == LCMG_PREC_FP64) {
+  if (c.prm.precond == 1) {
+    PaperMG(c).run(lam[0]);
+  } else if (c.prm.precision == LCMG_PREC_FP64) {
     Batch<double> b(c, B);
     b.run(lam);
   } else {
@@ -1378,6 +1807,8 @@ void lcmg_default_params(lcmg_params* p) {
   p->autotune = 0;
   p->spmv_variant = 0;
   p->stop_rule = 0;
+  p->precond = 0;
+  p->gmres_restart = 200;
 }
 
 const char* lcmg_last_error(void) { return lcmg::g_err.c_str(); }
@@ -1452,6 +1883,7 @@ int lcmg_set_grid(lcmg_ctx* ctx, int32_t n_v, int32_t n_h) {
   ctx->fwd = 0;
   ctx->tuned.clear();
   ctx->ones_ok = false;
+  ctx->pm_levels = 0;
   std::vector<double> ones(ctx->ne, 1.0);
   lcmg::copy_sync(ctx->stream, ctx->d.need(ctx->ne), ones.data(), sizeof(double) * ctx->ne, cudaMemcpyHostToDevice);
   lcmg::refresh_fine(*ctx);
@@ -1535,6 +1967,7 @@ int lcmg_set_forward_csr(lcmg_ctx* ctx, int64_t m, int64_t n, const int64_t* row
   ctx->fwd = 1;
   ctx->hier_ok = false;
   ctx->tuned.clear();
+  ctx->pm_levels = 0;
   API_END
 }
 
@@ -1563,6 +1996,7 @@ int lcmg_set_forward_stencil(lcmg_ctx* ctx, int32_t kh, int32_t kw, const double
   LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->fwd = 2;
   ctx->tuned.clear();
+  ctx->pm_levels = 0;
   ctx->hier_ok = false;
   API_END
 }
@@ -1802,6 +2236,16 @@ int lcmg_apply_vcycle_dev(lcmg_ctx* ctx, int32_t n_cols, const double* lambda, c
   const int B = n_cols;
   lcmg::ensure_work(*ctx, B);
   std::vector<double> lam(lambda, lambda + B);
+  if (ctx->prm.precond == 1) {  // the paper's V(2,1), one column at a time, FP64
+    lcmg::pm_build(*ctx);
+    lcmg::PaperMG pmg(*ctx);
+    for (int j = 0; j < B; ++j) {
+      pmg.setup(lam[j]);
+      pmg.cycle(0, r_dev + (int64_t)j * ctx->n, z_dev + (int64_t)j * ctx->n);
+    }
+    LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
+    return LCMG_OK;
+  }
   const int g = lcmg::grid_for(ctx->n, B, ctx->maxblk);
   if (ctx->prm.precision == LCMG_PREC_FP64) {
     lcmg::Batch<double> b(*ctx, B);

@@ -45,7 +45,8 @@ class lcmg_params(C.Structure):
                 ("keep_direction", C.c_int32),
                 ("autotune", C.c_int32),
                 ("spmv_variant", C.c_int32),
-                ("stop_rule", C.c_int32)]
+                ("stop_rule", C.c_int32),
+                ("precond", C.c_int32), ("gmres_restart", C.c_int32)]
 
 
 class lcmg_stats(C.Structure):
