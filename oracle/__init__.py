@@ -16,6 +16,12 @@ What it computes (paper sections in brackets):
                        [Sec. 3.1], cell-centred bilinear P, l1-Jacobi smoothing,
                        a dense Cholesky solve on the coarsest level.
   * ``krylov``      -- preconditioned CG on the normal equations.
+  * ``paper_mg``    -- the paper's own cycle: one-sided hierarchies
+                       A_{k+1} = A_k P_k, M_{k+1} = M_k P_k, diagonally
+                       preconditioned CG relaxation, V(2,1), flexible GMRES
+                       [Sec. 3.2, 3.3].
+  * ``amg``         -- classical AMG coarsening of L^T D^2 L: strength,
+                       two-pass C/F split, interpolation [Sec. 3.1].
   * ``lcurve``      -- L-curve values, the corner, the weight update of eq. (g),
                        the lambda window and the outer stopping rule [Sec. 3.3,
                        3.4, 3.5, Algorithm 2].
@@ -29,4 +35,4 @@ Parity pins: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute force or the paper's definitions; none is
 "parity unpinned".
 """
-from . import operators, multigrid, krylov, lcurve, outer, closed_forms  # noqa: F401
+from . import operators, multigrid, krylov, lcurve, outer, closed_forms, paper_mg, amg  # noqa: F401

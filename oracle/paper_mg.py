@@ -19,12 +19,15 @@ coarsest level is solved exactly.  Because CG relaxation makes the cycle a
 nonlinear operator, the outer solver is flexible GMRES (Sec. 3.3).
 
 Readings of this build:
-  * P_k is the cell-centred bilinear interpolation of the geometric
-    hierarchy (oracle.multigrid.prolongation); the paper's classical AMG
-    interpolation is a separate item;
+  * P_k is either the cell-centred bilinear interpolation of the geometric
+    hierarchy (oracle.multigrid.prolongation) or the paper's classical AMG
+    interpolation of G_L = L^T D^2 L (oracle.amg, Sec. 3.1), which depends
+    on D and so is rebuilt for every weight vector;
   * restriction R_k = P_k^T, gamma = 1, zero initial guess on coarse levels;
-  * FGMRES is right-preconditioned with modified Gram-Schmidt Arnoldi and
-    Givens rotations; the tolerance is the relative residual
+  * FGMRES is right-preconditioned with Givens rotations and modified
+    Gram-Schmidt Arnoldi (orth="mgs"), or classical Gram-Schmidt applied
+    twice (orth="cgs2"; the two agree in exact arithmetic, and at small
+    lambda their step counts differ by ~5-10% through rounding alone); the tolerance is the relative residual
     ||c - K x||_2 <= tol ||c||_2 of the normal equations, judged on the
     Arnoldi estimate and confirmed on the true residual, from which the
     iteration restarts if it is not met; the basis is restarted after
@@ -42,6 +45,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 
 from . import multigrid as mg
+from . import amg
 from .krylov import CONVERGED, MAXIT, BREAKDOWN, NONFINITE
 
 
@@ -79,6 +83,20 @@ def build_one_sided(A, L, d, n_v, n_h, levels) -> OneSided:
     dA = [np.asarray(Ak.multiply(Ak).sum(axis=0)).ravel() for Ak in As]
     dM = [np.asarray(Mk.multiply(Mk).sum(axis=0)).ravel() for Mk in Ms]
     return OneSided(shapes, As, Ms, Ps, dA, dM)
+
+
+def build_one_sided_amg(A, L, d, max_levels=20, max_coarse=256) -> OneSided:
+    """As build_one_sided with the classical AMG interpolation of
+    G_L = L^T D^2 L (Sec. 3.2); level shapes are (n_k, 1)."""
+    Ks, Ps, _ = amg.hierarchy(mg.weighted_laplacian(L, np.asarray(d, dtype=np.float64)), max_levels, max_coarse)
+    As = [sp.csr_matrix(A, dtype=np.float64)]
+    Ms = [(sp.diags(np.asarray(d, dtype=np.float64)) @ L).tocsr()]
+    for P in Ps:
+        As.append((As[-1] @ P).tocsr())
+        Ms.append((Ms[-1] @ P).tocsr())
+    dA = [np.asarray(Ak.multiply(Ak).sum(axis=0)).ravel() for Ak in As]
+    dM = [np.asarray(Mk.multiply(Mk).sum(axis=0)).ravel() for Mk in Ms]
+    return OneSided([(K.shape[0], 1) for K in Ks], As, Ms, Ps, dA, dM)
 
 
 def pcg_steps(apply_K, dinv, x, b, steps):
@@ -133,7 +151,7 @@ class PaperVCycle:
         return self.cycle(0, np.asarray(r, dtype=np.float64))
 
 
-def fgmres(apply_K, c, x0=None, apply_M=None, tol=1e-6, maxit=10000, restart=200):
+def fgmres(apply_K, c, x0=None, apply_M=None, tol=1e-6, maxit=10000, restart=200, orth="mgs"):
     """Right-preconditioned flexible GMRES.  Returns (x, iterations, status,
     relres); ``iterations`` counts applications of K inside the Arnoldi
     loop (initial and true residuals excluded)."""
@@ -168,9 +186,15 @@ def fgmres(apply_K, c, x0=None, apply_M=None, tol=1e-6, maxit=10000, restart=200
             Z[:, j] = M(V[:, j])
             w = apply_K(Z[:, j])
             it += 1
-            for i in range(j + 1):                       # modified Gram-Schmidt
-                H[i, j] = V[:, i] @ w
-                w = w - H[i, j] * V[:, i]
+            if orth == "mgs":                            # modified Gram-Schmidt
+                for i in range(j + 1):
+                    H[i, j] = V[:, i] @ w
+                    w = w - H[i, j] * V[:, i]
+            else:                                        # classical, twice
+                for _ in range(2):
+                    h = V[:, : j + 1].T @ w
+                    w = w - V[:, : j + 1] @ h
+                    H[: j + 1, j] += h
             H[j + 1, j] = np.linalg.norm(w)
             if not np.all(np.isfinite(H[: j + 2, j])):
                 return x, it, NONFINITE, np.nan
@@ -200,10 +224,14 @@ def fgmres(apply_K, c, x0=None, apply_M=None, tol=1e-6, maxit=10000, restart=200
 
 
 def solve(F, L, d, n_v, n_h, levels, c, lam, x0=None, tol=1e-6, maxit=10000, nu1=2, nu2=1,
-          restart=200):
-    """FGMRES with the paper's V-cycle on eq. (normal) for one lambda."""
+          restart=200, coarsening="geometric", max_coarse=256, orth="mgs"):
+    """FGMRES with the paper's V-cycle on eq. (normal) for one lambda;
+    with coarsening="amg", `levels` is the largest number of levels."""
     A = explicit_forward(F)
-    h = build_one_sided(A, L, d, n_v, n_h, levels)
+    if coarsening == "amg":
+        h = build_one_sided_amg(A, L, d, levels, max_coarse)
+    else:
+        h = build_one_sided(A, L, d, n_v, n_h, levels)
     V = PaperVCycle(h, lam, nu1, nu2)
     K = lambda v: V.K(0, v)
-    return fgmres(K, c, x0, V, tol, maxit, restart)
+    return fgmres(K, c, x0, V, tol, maxit, restart, orth)

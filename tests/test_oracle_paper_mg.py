@@ -55,8 +55,9 @@ def test_pcg_steps_terminate_and_decrease_the_energy_error():
     assert all(e1 <= e0 * (1 + 1e-12) for e0, e1 in zip(errs, errs[1:]))
 
 
+@pytest.mark.parametrize("orth", ["mgs", "cgs2"])
 @pytest.mark.parametrize("k", [1, 3, 7])
-def test_fgmres_residual_is_the_krylov_minimum(k):
+def test_fgmres_residual_is_the_krylov_minimum(k, orth):
     """Unpreconditioned, no restart: after k steps the residual is the
     least-squares minimum over x0 + span{r0, K r0, ..., K^(k-1) r0}."""
     g = pg.rng(9)
@@ -64,7 +65,7 @@ def test_fgmres_residual_is_the_krylov_minimum(k):
     K = g.standard_normal((n, n)) + 6 * np.eye(n)             # nonsymmetric
     c = g.standard_normal(n)
     x0 = g.standard_normal(n)
-    x, it, st, rel = pm.fgmres(lambda v: K @ v, c, x0, None, tol=0.0, maxit=k, restart=50)
+    x, it, st, rel = pm.fgmres(lambda v: K @ v, c, x0, None, tol=0.0, maxit=k, restart=50, orth=orth)
     assert it == k
     r0 = c - K @ x0
     basis = np.column_stack([np.linalg.matrix_power(K, i) @ r0 for i in range(k)])
@@ -73,14 +74,15 @@ def test_fgmres_residual_is_the_krylov_minimum(k):
     assert abs(np.linalg.norm(c - K @ x) - best) <= 1e-9 * np.linalg.norm(r0)
 
 
-def test_fgmres_with_the_exact_inverse_takes_one_step():
+@pytest.mark.parametrize("orth", ["mgs", "cgs2"])
+def test_fgmres_with_the_exact_inverse_takes_one_step(orth):
     g = pg.rng(2)
     n = 15
     Q = g.standard_normal((n, n))
     K = Q @ Q.T + np.eye(n)
     c = g.standard_normal(n)
     Kinv = np.linalg.inv(K)
-    x, it, st, rel = pm.fgmres(lambda v: K @ v, c, None, lambda v: Kinv @ v, tol=1e-12, maxit=10)
+    x, it, st, rel = pm.fgmres(lambda v: K @ v, c, None, lambda v: Kinv @ v, tol=1e-12, maxit=10, orth=orth)
     assert st == krylov.CONVERGED and it == 1
 
 
