@@ -36,7 +36,7 @@ WORKLOAD = "ct256"
 WORKLOAD_DESC = ("ct256: 256x256 parallel-beam CT, 180 angles x 363 bins exact ray-length CSR "
                  "(FP32 values, int32 indices), 10 seeded ellipses, 1% noise, 20 lambdas "
                  "logspace(-4, 0), Algorithm 2 (max 15 outer iterations, three-equal stop, "
-                 "largest-lambda-first warm-start chain), rel-res 1e-6, 6-level V(2,2) l1-Jacobi")
+                 "largest-lambda-first warm-start chain), rel-res 1e-6, 5-level V(2,2) l1-Jacobi")
 METRIC = "lambda-solves/s at rel-res 1e-6"
 KERNEL_SRC = os.path.join(ROOT, "paper_2306_11067_gb300", "csrc", "kernels.cuh")
 LAUNCH_SRC = os.path.join(ROOT, "paper_2306_11067_gb300", "csrc", "launch_spmm.cu")
@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--oracle-sample", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-serve", action="store_true", help="skip the served-mix latency leg")
     ap.add_argument("--serve-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--compare-precond", action="store_true",
+                    help="time the lambda sweep of one outer iteration with the default preconditioner (FP64 and "
+                         "mixed) and the paper's own (geometric and classical AMG interpolation, FP64) at 64^2, "
+                         "128^2, 256^2; one JSON line per arm, no bench line")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiler workload: one lambda of the workload, this many PCG iterations, no JSON line")
     return ap.parse_args()
@@ -172,7 +176,7 @@ def kernel_fingerprint():
     i = src.index("    k_spmv1(")
     j = src.index("\n}\n", i)
     lsrc = open(LAUNCH_SRC).read()
-    a = lsrc.index("static int run1v(")
+    a = lsrc.index("static int run1c(")
     b = lsrc.index("\n}\n", lsrc.index("static int run1(", a))
     return hashlib.sha256((src[i:j] + lsrc[a:b]).encode()).hexdigest()[:16]
 
@@ -282,6 +286,42 @@ def profile_workload(args):
     s.close()
 
 
+def compare_precond():
+    """Sequential chain over the workload's lambdas (tol 1e-6, one
+    right-hand side) for each preconditioner arm in FP64, and the default
+    one in mixed precision (the benchmark's path): sweep time after a
+    warm-up solve that builds the hierarchies, FGMRES / PCG steps, time per
+    step."""
+    import numpy as np
+    import problemgen as pg
+    from paper_2306_11067_gb300 import lcmg as L
+    F64, MIX = L.PREC_FP64, L.PREC_MIXED
+    arms = [("pcg-default", dict(precond=0, precision=F64)), ("paper-geometric", dict(precond=1, precision=F64)),
+            ("paper-amg", dict(precond=1, coarsening=1, precision=F64)),
+            ("pcg-default-mixed", dict(precond=0, precision=MIX))]
+    for N in (64, 128, 256):
+        P = pg.make_problem(WORKLOAD, size=None if N == 256 else N)
+        b = P.b[:, 0]
+        for name, kw in arms:
+            s = L.Solver(N, N, mode=L.MODE_SEQUENTIAL, tol=1e-6, maxit=10000, **kw)
+            s.set_forward_csr(P.A)
+            t0 = time.perf_counter()
+            s.solve(P.lambdas[-2:], b)
+            t_warm = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            out = s.solve(P.lambdas, b)
+            dt = time.perf_counter() - t0
+            st = s.stats()
+            its = out["iters"][0]
+            levels = (L.lcmg_amg_levels(s.ctx).tolist() if kw.get("coarsening") else L.lcmg_num_levels(s.ctx))
+            print(json.dumps({"arm": name, "n": N, "precision": "fp64" if kw["precision"] == F64 else "mixed", "lambdas": int(len(P.lambdas)), "sweep_s": round(dt, 3),
+                              "warmup_s": round(t_warm, 3), "steps": int(its.sum()),
+                              "us_per_step": round(st["iterate_ms"] * 1e3 / max(st["batch_iterations"], 1), 1),
+                              "status": sorted(set(int(v) for v in out["status"][0])), "levels": levels}),
+                  flush=True)
+            s.close()
+
+
 # ---------------------------------------------------------------------------
 def main():
     args = parse()
@@ -296,6 +336,8 @@ def main():
         return reference_arm(args, world, rank)
     if args.profile_iters > 0:
         return profile_workload(args)
+    if args.compare_precond:
+        return compare_precond()
     if args.serve_only:
         print(json.dumps(serving_leg(int(os.environ.get("LOCAL_RANK", "0")))))
         return
@@ -413,7 +455,8 @@ def main():
     peak, peak_kind = measured_hbm_peak()
     achieved = (op_bytes / (op_ms / 1e3) / 1e9) if op_ms > 0 else None
     roofline = {
-        "kernel": "k_spmm (both operator passes: y = A p, then q = A^T y + lam^2 L^T W L p with p.q)",
+        "kernel": ("k_spmv1 (the one-column SpMV, both operator passes: y = A p with int32 columns, then "
+                   "q = A^T y + lam^2 L^T W L p with p.q and 16-bit column offsets)"),
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": (achieved / peak) if achieved else None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
         "traffic": recorded_traffic(),

@@ -153,9 +153,27 @@ typedef struct {
                            normal operator with one-sided coarse operators
                            A_{k+1} = A_k P_k, Jacobi-preconditioned CG relaxation
                            and an exact coarsest solve; CSR forward operators,
-                           FP64, one lambda at a time (lcmg_apply_vcycle_dev then
-                           applies this cycle)                                   */
+                           FP64 (precision = FP64; INVALID_ARG otherwise), one
+                           lambda at a time (lcmg_apply_vcycle_dev then
+                           applies this cycle)                              */
   int32_t gmres_restart; /* FGMRES basis size before a restart (1..2000; 200)     */
+  int32_t coarsening;   /* interpolation of the paper's method (precond = 1):
+                           0 = geometric cell-centred bilinear P on the grid
+                           (default); 1 = classical AMG of Sec. 3.1 on
+                           L^T D^2 L (strength theta = 0.25, the two-pass C/F
+                           split, the paper's interpolation formula), rebuilt
+                           on the host for every weight vector; `levels` is
+                           then the largest level count (0 = no limit)      */
+  int32_t amg_coarse_max; /* classical AMG: coarsen while a level has more
+                           points than this (2..2048; 256); the last level is
+                           solved densely                                   */
+  int32_t compact_cols; /* one-column transposed pass (q = A^T y + ...): 1 = read
+                           column indices as 16-bit offsets from a per-row base
+                           (6 instead of 8 bytes per FP32 nonzero; built by
+                           set_forward_csr when every row of A and A^T spans
+                           fewer than 65,536 columns, else int32 indices are
+                           read; default); 0 = always int32.  Results are
+                           bitwise identical                                 */
 } lcmg_params;
 
 typedef struct lcmg_ctx lcmg_ctx;
@@ -255,6 +273,42 @@ int lcmg_update_weights(lcmg_ctx* ctx, const double* x_star, double q, double d_
                         double* d_out);
 int lcmg_update_weights_dev(lcmg_ctx* ctx, const double* x_star_dev, double q,
                             double d_min);
+
+/* Classical AMG coarsening (Sec. 3.1) of an n x n matrix K in host memory
+ * (CSR: row_ptr[n+1], column indices sorted within each row, FP64 values);
+ * no device use.  j != i is a strong connection of row i when
+ * -k_ij > theta * max_{m != i}(-k_im) * (1 + 1e-10) (a tie is weak; the paper
+ * takes theta = 0.25).  First pass: greedy, largest number of strongly
+ * dependent points first (ties: smallest index); a new C point's unsorted
+ * dependants become F; each unsorted strong connection of a new F point gains
+ * one.  Second pass, F points in increasing order: a strong F connection j of
+ * i without a strong connection into i's strong C points C_i becomes C
+ * tentatively (and joins C_i); a second such j makes i itself C instead.
+ * cf[i] (n, caller-owned) = 1 for a C point, 0 for an F point.
+ * Errors: INVALID_ARG for n < 1, a null pointer, a column out of range or
+ * rows not sorted. */
+int lcmg_rs_split(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                  double theta, int8_t* cf);
+
+/* Interpolation of the split cf (as lcmg_rs_split returns, same K and
+ * theta) by the formula of Sec. 3.1:
+ *   w_ij = -(k_ij + sum_{m in F_i^s} k_im k_mj / sum_{l in C_i} k_ml)
+ *          / (k_ii + sum_{m in F_i^w} k_im)
+ * for the strong C connections j of an F point i (F_i^s its strong F
+ * connections, F_i^w its other neighbours; a strong F connection whose sum
+ * over C_i is zero counts with F_i^w); a C point injects.  Coarse points are
+ * numbered in increasing fine index.  Output: P as CSR (p_row_ptr[n+1],
+ * p_col / p_val with room for `cap` entries, caller-owned); *nnz = the
+ * number of entries.  Errors: INVALID_ARG as lcmg_rs_split, or cap < *nnz
+ * (then only *nnz is written). */
+int lcmg_rs_interp(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                   double theta, const int8_t* cf, int64_t cap, int64_t* p_row_ptr,
+                   int32_t* p_col, double* p_val, int64_t* nnz);
+
+/* Level sizes of the classical AMG hierarchy the context last built
+ * (coarsening = 1, after a solve): sizes[k] for k < min(cap, levels),
+ * *n_levels = the level count.  Errors: STATE if none was built. */
+int lcmg_amg_levels(lcmg_ctx* ctx, int32_t cap, int64_t* sizes, int32_t* n_levels);
 
 /* Lambda window of Algorithm 2 (1-based, inclusive): i_prev = 0 marks the
  * first outer iteration (window 1..m); otherwise

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblcmg.so")
-SOURCES = ["capi.cu", "launch_spmm.cu", "launch_level.cu", "noalloc.cu", "mega.cu", "tail.cu", "server.cu"]
+SOURCES = ["capi.cu", "launch_spmm.cu", "launch_level.cu", "noalloc.cu", "mega.cu", "tail.cu", "server.cu",
+           "rs_amg.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -47,7 +48,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     objs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + headers):
             jobs.append([nvcc()] + _flags() + ["-c", s, "-o", o])
@@ -65,7 +66,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
             if verbose and msg:
                 print(msg, file=sys.stderr)
     if force or jobs or not os.path.exists(LIB):
-        link = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", LIB] + objs
+        link = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", LIB] + objs + ["-lpthread"]
         run(link)
     return LIB
 

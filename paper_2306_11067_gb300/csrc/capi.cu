@@ -20,6 +20,7 @@
 #include "spmm_staged.cuh"
 #include "vfused.cuh"
 #include "paper_mg.cuh"
+#include "rs_amg.h"
 #include "mega.cuh"
 #include "tail.cuh"
 #include "tail_launch.h"
@@ -85,6 +86,16 @@ struct PmLevel {
   DevBuf<double> v, vT, dA;
 };
 
+// A level of the classical AMG hierarchy on the device (params.coarsening =
+// 1): P_k (n_k x n_{k+1}) and P_k^T as CSR, and G_L^k = M_k^T M_k as CSR with
+// its diagonal (levels k >= 1).
+struct AmLevel {
+  int64_t n = 0;
+  DevBuf<int64_t> prp, ptrp, grp;
+  DevBuf<int32_t> pci, ptci, gci;
+  DevBuf<double> pv, ptv, gv, gdiag;
+};
+
 // One-column workspace of a level of the paper's cycle.
 struct PmWork {
   DevBuf<double> b, x, r, z, p, q, t, y, dinv, pa, pb, ppq;
@@ -129,6 +140,11 @@ struct lcmg_ctx {
   DevBuf<int64_t> ck_nz, ckT_nz;
   int64_t nck = 0, nckT = 0;
   DevBuf<int> spmm_err;  // set by a staged SpMM whose stage wait gave up
+  // 16-bit column offsets from a per-row base (A and A^T), when every row's
+  // column span fits: read by the one-column SpMV
+  DevBuf<uint16_t> c16, c16T;
+  DevBuf<int32_t> rbase, rbaseT;
+  bool c16_ok = false;
   DevBuf<double> ones;   // n ones (unweighted gradient norm)
   bool ones_ok = false;
   std::map<int, lcmg::Tuned> tuned;  // autotuner choices per (batch width, precision)
@@ -137,6 +153,9 @@ struct lcmg_ctx {
   std::vector<lcmg::PmWork> pmw;
   DevBuf<double> pm_AtAc;            // dense A_c^T A_c of the coarsest level
   int pm_levels = 0;                 // levels the one-sided hierarchy was built for (0: none)
+  std::vector<lcmg::AmLevel> am;     // classical AMG levels (params.coarsening = 1)
+  bool am_ok = false;                // am and pm hold the AMG hierarchy of the current D
+  DevBuf<double> pm_GLc;             // dense G_L^c of the coarsest AMG level
   DevBuf<double> pm_V, pm_Z, pm_w, pm_r, pm_h, pm_part, pm_y;
   int rv = 0, rh = 0;
   DevBuf<double> psf64;
@@ -200,6 +219,10 @@ static SpmmArgs csr_args(const lcmg_ctx& c, bool trans, int ld) {
   a.rp = trans ? c.rpT.p : c.rp.p;
   a.ci = trans ? c.ciT.p : c.ci.p;
   a.B = ld; a.c0 = 0; a.nb = ld; a.nl = 1; a.nrhs = 1;
+  if (c.c16_ok && c.prm.compact_cols && !c.prm.staged) {
+    a.c16 = trans ? c.c16T.p : c.c16.p;
+    a.rbase = trans ? c.rbaseT.p : c.rbase.p;
+  }
   if (c.prm.staged) {
     a.ck_row = trans ? c.ckT_row.p : c.ck_row.p;
     a.ck_nz = trans ? c.ckT_nz.p : c.ck_nz.p;
@@ -267,6 +290,9 @@ static void check_params(const lcmg_params& p) {
   if (p.stop_rule != 0 && p.stop_rule != 1) throw ArgError("stop_rule must be 0 or 1");
   if (p.precond != 0 && p.precond != 1) throw ArgError("precond must be 0 or 1");
   if (p.gmres_restart < 1 || p.gmres_restart > 2000) throw ArgError("gmres_restart must be 1..2000");
+  if (p.coarsening != 0 && p.coarsening != 1) throw ArgError("coarsening must be 0 or 1");
+  if (p.compact_cols != 0 && p.compact_cols != 1) throw ArgError("compact_cols must be 0 or 1");
+  if (p.amg_coarse_max < 2 || p.amg_coarse_max > 2048) throw ArgError("amg_coarse_max must be 2..2048");
 }
 
 static int sum_blocks(int nb) { return std::max(1, std::min(nb, kMaxBlocks)); }
@@ -275,7 +301,9 @@ static int sum_blocks(int nb) { return std::max(1, std::min(nb, kMaxBlocks)); }
 // Hierarchy
 // ---------------------------------------------------------------------------
 static int level_count(const lcmg_ctx& c) {
-  if (c.prm.levels > 0) return c.prm.levels;
+  // with classical AMG `levels` bounds the AMG hierarchy; the geometric one
+  // (used by the default preconditioner) then takes its default depth
+  if (c.prm.levels > 0 && c.prm.coarsening == 0) return c.prm.levels;
   int lv = 1, a = c.nv, b = c.nh;
   while ((a > c.prm.coarse_max || b > c.prm.coarse_max) && a % 2 == 0 && b % 2 == 0) {
     a /= 2; b /= 2; ++lv;
@@ -292,6 +320,7 @@ static void refresh_fine(lcmg_ctx& c) {
   klaunch(k_convert<double, float>, dim3(g), dim3(kBlock), 0, c.stream, c.n, c.we.p, c.we32.need(c.n));
   LCMG_LAUNCHED();
   c.hier_ok = false;
+  c.am_ok = false;  // classical AMG coarsens L^T D^2 L: rebuilt for every D
 }
 
 static void build_hierarchy(lcmg_ctx& c) {
@@ -927,9 +956,11 @@ static void op_bytes(const lcmg_ctx& c, int B, int64_t* first, int64_t* second) 
   const int64_t sT = sizeof(T), sB = B;
   if (c.fwd == 1) {
     const int64_t sV = (std::is_same<T, float>::value || c.vdtype == 0) ? 4 : 8;
-    const int64_t mat = c.nnz * (sV + 4);
-    *first = mat + (c.m + 1) * 8 + c.n * sB * sT + c.m * sB * sT;
-    *second = mat + (c.n + 1) * 8 + c.m * sB * sT + 2 * c.n * sB * sT + 2 * c.n * sT + c.n * sB * sT;
+    // the one-column transposed pass reads 16-bit column offsets and a base per row
+    const bool c16 = B == 1 && c.c16_ok && c.prm.compact_cols && !c.prm.staged;
+    *first = c.nnz * (sV + 4) + (c.m + 1) * 8 + c.n * sB * sT + c.m * sB * sT;
+    *second = c.nnz * (sV + (c16 ? 2 : 4)) + (c.n + 1) * 8 + (c16 ? c.n * 4 : 0) + c.m * sB * sT +
+              2 * c.n * sB * sT + 2 * c.n * sT + c.n * sB * sT;
   } else {
     *first = 2 * c.n * sB * sT;
     *second = 3 * c.n * sB * sT + 2 * c.n * sT;
@@ -1050,12 +1081,6 @@ static void compute_rhs(lcmg_ctx& c, int nrhs) {
 // ---------------------------------------------------------------------------
 constexpr int kPmNu1 = 2, kPmNu2 = 1;  // CG relaxation steps before / after the coarse correction
 
-struct HostCsr {
-  int64_t rows = 0, cols = 0;
-  std::vector<int64_t> rp;
-  std::vector<int32_t> ci;
-  std::vector<double> v;
-};
 
 // weight of coarse cell I in the cell-centred linear interpolation to fine
 // cell a (nc coarse cells; an outside neighbour's weight goes to the parent)
@@ -1113,31 +1138,9 @@ static HostCsr times_p(const HostCsr& A, int nv, int nh) {
   return Bm;
 }
 
-static HostCsr transpose(const HostCsr& A) {
-  HostCsr T;
-  T.rows = A.cols;
-  T.cols = A.rows;
-  T.rp.assign(A.cols + 1, 0);
-  for (int32_t c : A.ci) T.rp[c + 1]++;
-  for (int64_t i = 0; i < A.cols; ++i) T.rp[i + 1] += T.rp[i];
-  T.ci.resize(A.ci.size());
-  T.v.resize(A.v.size());
-  std::vector<int64_t> pos(T.rp.begin(), T.rp.end() - 1);
-  for (int64_t r = 0; r < A.rows; ++r)
-    for (int64_t k = A.rp[r]; k < A.rp[r + 1]; ++k) {
-      const int64_t d = pos[A.ci[k]]++;
-      T.ci[d] = (int32_t)r;
-      T.v[d] = A.v[k];
-    }
-  return T;
-}
 
-static void pm_build(lcmg_ctx& c) {
-  ensure_hierarchy(c);
-  const int L = (int)c.lev.size();
-  if (c.pm_levels == L) return;
-  if (c.fwd != 1) throw ArgError("the paper's preconditioner needs a CSR forward operator");
-  if (L < 2) throw ArgError("the paper's preconditioner needs at least 2 levels");
+// host copy of the CSR forward operator A (values in FP64)
+static HostCsr host_forward(lcmg_ctx& c) {
   cudaStream_t s = c.stream;
   HostCsr A;
   A.rows = c.m;
@@ -1154,38 +1157,44 @@ static void pm_build(lcmg_ctx& c) {
     copy_sync(s, vf.data(), c.v32.p, sizeof(float) * c.nnz, cudaMemcpyDeviceToHost);
     for (int64_t k = 0; k < c.nnz; ++k) A.v[k] = vf[k];
   }
-  c.pm.clear();
-  c.pm.resize(L);
-  for (int k = 1; k < L; ++k) {
-    A = times_p(A, c.lev[k - 1].nv, c.lev[k - 1].nh);
-    HostCsr T = transpose(A);
-    PmLevel& P = c.pm[k];
-    P.nnz = (int64_t)A.ci.size();
-    copy_sync(s, P.rp.need(A.rows + 1 + kCsrPad), A.rp.data(), sizeof(int64_t) * (A.rows + 1), cudaMemcpyHostToDevice);
-    copy_sync(s, P.ci.need(P.nnz + kCsrPad), A.ci.data(), sizeof(int32_t) * P.nnz, cudaMemcpyHostToDevice);
-    copy_sync(s, P.v.need(P.nnz + kCsrPad), A.v.data(), sizeof(double) * P.nnz, cudaMemcpyHostToDevice);
-    copy_sync(s, P.rpT.need(T.rows + 1 + kCsrPad), T.rp.data(), sizeof(int64_t) * (T.rows + 1), cudaMemcpyHostToDevice);
-    copy_sync(s, P.ciT.need(P.nnz + kCsrPad), T.ci.data(), sizeof(int32_t) * P.nnz, cudaMemcpyHostToDevice);
-    copy_sync(s, P.vT.need(P.nnz + kCsrPad), T.v.data(), sizeof(double) * P.nnz, cudaMemcpyHostToDevice);
-    const int64_t nk = c.lev[k].n;
-    const int g = (int)std::min<int64_t>((nk * 32 + kBlock - 1) / kBlock, c.maxblk);
-    klaunch(k_diag_ata<double>, dim3(g), dim3(kBlock), 0, s, nk, P.rpT.p, P.vT.p, P.dA.need(nk));
-    LCMG_LAUNCHED();
-    if (k == L - 1) {  // dense A_c^T A_c, rows of A_c in order
-      const int64_t nc = nk;
-      std::vector<double> AtA((size_t)nc * nc, 0.0);
-      for (int64_t r = 0; r < A.rows; ++r)
-        for (int64_t a = A.rp[r]; a < A.rp[r + 1]; ++a)
-          for (int64_t b2 = A.rp[r]; b2 < A.rp[r + 1]; ++b2)
-            AtA[(size_t)A.ci[a] * nc + A.ci[b2]] += A.v[a] * A.v[b2];
-      copy_sync(s, c.pm_AtAc.need(nc * nc), AtA.data(), sizeof(double) * nc * nc, cudaMemcpyHostToDevice);
-    }
+  return A;
+}
+
+// upload the one-sided A_k (k >= 1, n_k columns) with its transpose and
+// diag(A_k^T A_k); on the coarsest level also the dense A_c^T A_c
+static void upload_one_sided(lcmg_ctx& c, int k, const HostCsr& A, bool coarsest) {
+  cudaStream_t s = c.stream;
+  HostCsr T = amg::transpose(A);
+  PmLevel& P = c.pm[k];
+  P.nnz = (int64_t)A.ci.size();
+  copy_sync(s, P.rp.need(A.rows + 1 + kCsrPad), A.rp.data(), sizeof(int64_t) * (A.rows + 1), cudaMemcpyHostToDevice);
+  copy_sync(s, P.ci.need(P.nnz + kCsrPad), A.ci.data(), sizeof(int32_t) * P.nnz, cudaMemcpyHostToDevice);
+  copy_sync(s, P.v.need(P.nnz + kCsrPad), A.v.data(), sizeof(double) * P.nnz, cudaMemcpyHostToDevice);
+  copy_sync(s, P.rpT.need(T.rows + 1 + kCsrPad), T.rp.data(), sizeof(int64_t) * (T.rows + 1), cudaMemcpyHostToDevice);
+  copy_sync(s, P.ciT.need(P.nnz + kCsrPad), T.ci.data(), sizeof(int32_t) * P.nnz, cudaMemcpyHostToDevice);
+  copy_sync(s, P.vT.need(P.nnz + kCsrPad), T.v.data(), sizeof(double) * P.nnz, cudaMemcpyHostToDevice);
+  const int64_t nk = A.cols;
+  const int g = (int)std::min<int64_t>((nk * 32 + kBlock - 1) / kBlock, c.maxblk);
+  klaunch(k_diag_ata<double>, dim3(g), dim3(kBlock), 0, s, nk, P.rpT.p, P.vT.p, P.dA.need(nk));
+  LCMG_LAUNCHED();
+  if (coarsest) {  // dense A_c^T A_c, rows of A_c in order
+    const int64_t nc = nk;
+    std::vector<double> AtA((size_t)nc * nc, 0.0);
+    for (int64_t r = 0; r < A.rows; ++r)
+      for (int64_t a = A.rp[r]; a < A.rp[r + 1]; ++a)
+        for (int64_t b2 = A.rp[r]; b2 < A.rp[r + 1]; ++b2)
+          AtA[(size_t)A.ci[a] * nc + A.ci[b2]] += A.v[a] * A.v[b2];
+    copy_sync(s, c.pm_AtAc.need(nc * nc), AtA.data(), sizeof(double) * nc * nc, cudaMemcpyHostToDevice);
   }
+}
+
+static void alloc_pm_work(lcmg_ctx& c, const std::vector<int64_t>& sizes) {
+  const int L = (int)sizes.size();
   c.pmw.clear();
   c.pmw.resize(L);
   for (int k = 0; k < L; ++k) {
     PmWork& W = c.pmw[k];
-    const int64_t nk = c.lev[k].n;
+    const int64_t nk = sizes[k];
     W.b.need(nk); W.x.need(nk);
     if (k + 1 < L) {
       for (auto* b : {&W.r, &W.z, &W.p, &W.q, &W.t, &W.dinv}) b->need(nk);
@@ -1193,19 +1202,125 @@ static void pm_build(lcmg_ctx& c) {
       for (auto* b : {&W.pa, &W.pb, &W.ppq}) b->need(kMaxBlocks);
     }
   }
+  const size_t nc = (size_t)sizes[L - 1];
+  c.kinv.need(nc * nc); c.Mw.need(nc * nc); c.Ww.need(nc * nc);
+}
+
+template <class I>
+static I* upload(cudaStream_t s, DevBuf<I>& buf, const std::vector<I>& h, size_t pad = 0) {
+  I* d = buf.need(h.size() + pad);
+  copy_sync(s, d, h.data(), sizeof(I) * h.size(), cudaMemcpyHostToDevice);
+  return d;
+}
+
+// The paper's hierarchy with classical AMG (Sec. 3.1-3.2): coarsen
+// G_L = L^T D^2 L on the host, then A_{k+1} = A_k P_k; rebuilt per D.
+static void pm_build_amg(lcmg_ctx& c) {
+  if (c.am_ok) return;
+  if (c.fwd != 1) throw ArgError("the paper's preconditioner needs a CSR forward operator");
+  cudaStream_t s = c.stream;
+  std::vector<double> d(c.ne);
+  copy_sync(s, d.data(), c.d.p, sizeof(double) * c.ne, cudaMemcpyDeviceToHost);
+  const HostCsr K0 = amg::weighted_laplacian(c.nv, c.nh, d.data());
+  const int maxlev = c.prm.levels > 0 ? c.prm.levels : 64;
+  amg::Hierarchy H = amg::hierarchy(K0, maxlev, c.prm.amg_coarse_max, amg::kTheta);
+  const int L = (int)H.K.size();
+  if (L < 2) throw ArgError("classical AMG made no coarse level (grid at most amg_coarse_max points, or levels = 1)");
+  const int64_t nc = H.K[L - 1].rows;
+  if (nc > 2048)
+    throw ArgError("the coarsest classical AMG level has " + std::to_string(nc) +
+                   " points (more than 2048): allow more levels");
+  c.am.clear();
+  c.am.resize(L);
+  std::vector<int64_t> sizes(L);
+  for (int k = 0; k < L; ++k) {
+    AmLevel& a = c.am[k];
+    a.n = sizes[k] = H.K[k].rows;
+    if (k > 0) {
+      const HostCsr& G = H.K[k];
+      std::vector<double> dg(G.rows, 0.0);
+      for (int64_t r = 0; r < G.rows; ++r)
+        for (int64_t q = G.rp[r]; q < G.rp[r + 1]; ++q)
+          if (G.ci[q] == r) dg[r] = G.v[q];
+      upload(s, a.grp, G.rp);
+      upload(s, a.gci, G.ci, 1);
+      upload(s, a.gv, G.v, 1);
+      upload(s, a.gdiag, dg);
+    }
+    if (k + 1 < L) {
+      const HostCsr& P = H.P[k];
+      const HostCsr PT = amg::transpose(P);
+      upload(s, a.prp, P.rp);
+      upload(s, a.pci, P.ci, 1);
+      upload(s, a.pv, P.v, 1);
+      upload(s, a.ptrp, PT.rp);
+      upload(s, a.ptci, PT.ci, 1);
+      upload(s, a.ptv, PT.v, 1);
+    }
+  }
+  {  // dense G_L^c
+    const HostCsr& G = H.K[L - 1];
+    std::vector<double> Gd((size_t)nc * nc, 0.0);
+    for (int64_t r = 0; r < G.rows; ++r)
+      for (int64_t q = G.rp[r]; q < G.rp[r + 1]; ++q) Gd[(size_t)r * nc + G.ci[q]] = G.v[q];
+    upload(s, c.pm_GLc, Gd);
+  }
+  HostCsr A = host_forward(c);
+  c.pm.clear();
+  c.pm.resize(L);
+  for (int k = 1; k < L; ++k) {
+    A = amg::spgemm(A, H.P[k - 1]);
+    upload_one_sided(c, k, A, k == L - 1);
+  }
+  alloc_pm_work(c, sizes);
+  LCMG_CUDA(cudaStreamSynchronize(s));
+  c.am_ok = true;
+  c.pm_levels = 0;  // the geometric one-sided hierarchy is no longer held
+}
+
+static void pm_build(lcmg_ctx& c) {
+  if (c.prm.coarsening == 1) {
+    pm_build_amg(c);
+    return;
+  }
+  ensure_hierarchy(c);
+  const int L = (int)c.lev.size();
+  if (c.pm_levels == L) return;
+  if (c.fwd != 1) throw ArgError("the paper's preconditioner needs a CSR forward operator");
+  if (L < 2) throw ArgError("the paper's preconditioner needs at least 2 levels");
+  cudaStream_t s = c.stream;
+  HostCsr A = host_forward(c);
+  c.pm.clear();
+  c.pm.resize(L);
+  for (int k = 1; k < L; ++k) {
+    A = times_p(A, c.lev[k - 1].nv, c.lev[k - 1].nh);
+    upload_one_sided(c, k, A, k == L - 1);
+  }
+  std::vector<int64_t> sizes(L);
+  for (int k = 0; k < L; ++k) sizes[k] = c.lev[k].n;
+  alloc_pm_work(c, sizes);
   LCMG_CUDA(cudaStreamSynchronize(s));
   c.pm_levels = L;
+  c.am_ok = false;
 }
 
 struct PaperMG {
   lcmg_ctx& c;
   cudaStream_t s;
+  bool amg;
   int L;
-  explicit PaperMG(lcmg_ctx& c_) : c(c_), s(c_.stream), L((int)c_.lev.size()) {}
+  explicit PaperMG(lcmg_ctx& c_)
+      : c(c_), s(c_.stream), amg(c_.prm.coarsening == 1),
+        L(c_.prm.coarsening == 1 ? (int)c_.am.size() : (int)c_.lev.size()) {}
 
-  int grid(int k) const { return grid_for(c.lev[k].n, 1, c.maxblk); }
+  int64_t nk(int k) const { return amg ? c.am[k].n : c.lev[k].n; }
+  int grid(int k) const { return grid_for(nk(k), 1, c.maxblk); }
   GLOp glop(int k) const { return GLOp{c.lev[k].nv, c.lev[k].nh, c.lev[k].n, c.lev[k].gl.p}; }
-  FineOp<double> fop() const { return view<double>(c, 0).fine_op(); }
+  CsrGLOp cglop(int k) const {
+    const AmLevel& a = c.am[k];
+    return CsrGLOp{(int)a.n, a.n, a.grp.p, a.gci.p, a.gv.p, a.gdiag.p};
+  }
+  FineOp<double> fop() const { return FineOp<double>{c.nv, c.nh, c.ws.p, c.we.p, c.diag.p}; }
 
   // y = A_k x, t = A_k^T y
   void passes(int k, const double* x, double* y, double* t) {
@@ -1225,7 +1340,7 @@ struct PaperMG {
     SpmmArgs a{};
     a.rows = c.m; a.rp = P.rp.p; a.ci = P.ci.p; a.B = 1; a.nb = 1; a.nl = 1; a.nrhs = 1;
     SpmmArgs at = a;
-    at.rows = c.lev[k].n; at.rp = P.rpT.p; at.ci = P.ciT.p;
+    at.rows = nk(k); at.rp = P.rpT.p; at.ci = P.ciT.p;
     launch_spmm<double, double, double, 0>(a, P.v.p, x, y, f, nullptr, nullptr, nullptr, nullptr, nullptr, c.maxblk, s);
     launch_spmm<double, double, double, 0>(at, P.vT.p, y, t, f, nullptr, nullptr, nullptr, nullptr, nullptr, c.maxblk, s);
   }
@@ -1236,15 +1351,17 @@ struct PaperMG {
     passes(k, x, W.y.p, W.t.p);
     const int g = grid(k);
     if (k == 0)
-      klaunch(k_pm_lap_add<FineOp<double>, MODE>, dim3(g), dim3(kBlock), 0, s, fop(), c.lev[k].n, c.lam2.p, x, W.t.p, b, q, part);
+      klaunch(k_pm_lap_add<FineOp<double>, MODE>, dim3(g), dim3(kBlock), 0, s, fop(), nk(0), c.lam2.p, x, W.t.p, b, q, part);
+    else if (amg)
+      klaunch(k_pm_lap_add<CsrGLOp, MODE>, dim3(g), dim3(kBlock), 0, s, cglop(k), nk(k), c.lam2.p, x, W.t.p, b, q, part);
     else
-      klaunch(k_pm_lap_add<GLOp, MODE>, dim3(g), dim3(kBlock), 0, s, glop(k), c.lev[k].n, c.lam2.p, x, W.t.p, b, q, part);
+      klaunch(k_pm_lap_add<GLOp, MODE>, dim3(g), dim3(kBlock), 0, s, glop(k), nk(k), c.lam2.p, x, W.t.p, b, q, part);
     LCMG_LAUNCHED();
   }
   // `steps` CG steps on K_k x = b; zero_x: from x = 0, else from x with r = b - K x
   void relax(int k, const double* b, double* x, int steps, bool zero_x) {
     PmWork& W = c.pmw[k];
-    const int64_t n = c.lev[k].n;
+    const int64_t n = nk(k);
     const int g = grid(k);
     if (!zero_x) apply<1>(k, x, b, W.r.p, nullptr);
     klaunch(k_pm_cg_init, dim3(g), dim3(kBlock), 0, s, n, zero_x ? 1 : 0, b, W.dinv.p, x, W.r.p, W.z.p, W.p.p, W.pa.p);
@@ -1266,16 +1383,27 @@ struct PaperMG {
   // x = V-cycle(b) on level k (zero initial guess)
   void cycle(int k, const double* b, double* x) {
     if (k == L - 1) {
-      launch_coarse_solve<double>((int)c.lev[k].n, 1, c.kinv.p, b, x, s);
+      launch_coarse_solve<double>((int)nk(k), 1, c.kinv.p, b, x, s);
       return;
     }
     PmWork& W = c.pmw[k];
     PmWork& Wc = c.pmw[k + 1];
     relax(k, b, x, kPmNu1, true);
     apply<1>(k, x, b, W.r.p, nullptr);
-    launch_restrict<double>(c.lev[k + 1].nv, c.lev[k + 1].nh, 1, W.r.p, Wc.b.p, c.maxblk, s);
-    cycle(k + 1, Wc.b.p, Wc.x.p);
-    launch_prolong_add<double>(c.lev[k + 1].nv, c.lev[k + 1].nh, 1, Wc.x.p, x, c.maxblk, s);
+    if (amg) {
+      const AmLevel& a = c.am[k];
+      klaunch(k_pm_csr_mv<false>, dim3(grid(k + 1)), dim3(kBlock), 0, s, nk(k + 1), a.ptrp.p, a.ptci.p, a.ptv.p,
+              (const double*)W.r.p, Wc.b.p);
+      LCMG_LAUNCHED();
+      cycle(k + 1, Wc.b.p, Wc.x.p);
+      klaunch(k_pm_csr_mv<true>, dim3(grid(k)), dim3(kBlock), 0, s, nk(k), a.prp.p, a.pci.p, a.pv.p,
+              (const double*)Wc.x.p, x);
+      LCMG_LAUNCHED();
+    } else {
+      launch_restrict<double>(c.lev[k + 1].nv, c.lev[k + 1].nh, 1, W.r.p, Wc.b.p, c.maxblk, s);
+      cycle(k + 1, Wc.b.p, Wc.x.p);
+      launch_prolong_add<double>(c.lev[k + 1].nv, c.lev[k + 1].nh, 1, Wc.x.p, x, c.maxblk, s);
+    }
     relax(k, b, x, kPmNu2, false);
   }
   // per lambda: Jacobi diagonals and the coarsest factorisation
@@ -1286,14 +1414,19 @@ struct PaperMG {
       const int g = grid(k);
       const double* dA = k == 0 ? c.diag.p : c.pm[k].dA.p;
       if (k == 0)
-        klaunch(k_pm_dinv<FineOp<double>>, dim3(g), dim3(kBlock), 0, s, fop(), c.lev[0].n, c.lam2.p, dA, c.pmw[0].dinv.p);
+        klaunch(k_pm_dinv<FineOp<double>>, dim3(g), dim3(kBlock), 0, s, fop(), nk(0), c.lam2.p, dA, c.pmw[0].dinv.p);
+      else if (amg)
+        klaunch(k_pm_dinv<CsrGLOp>, dim3(g), dim3(kBlock), 0, s, cglop(k), nk(k), c.lam2.p, dA, c.pmw[k].dinv.p);
       else
-        klaunch(k_pm_dinv<GLOp>, dim3(g), dim3(kBlock), 0, s, glop(k), c.lev[k].n, c.lam2.p, dA, c.pmw[k].dinv.p);
+        klaunch(k_pm_dinv<GLOp>, dim3(g), dim3(kBlock), 0, s, glop(k), nk(k), c.lam2.p, dA, c.pmw[k].dinv.p);
       LCMG_LAUNCHED();
     }
-    const int64_t nc = c.lev[L - 1].n;
+    const int64_t nc = nk(L - 1);
     const int gd = (int)std::min<int64_t>((nc * nc + kBlock - 1) / kBlock, c.maxblk);
-    klaunch(k_pm_dense, dim3(gd), dim3(kBlock), 0, s, glop(L - 1), c.lam2.p, c.pm_AtAc.p, c.Mw.p);
+    if (amg)
+      klaunch(k_pm_dense_add, dim3(gd), dim3(kBlock), 0, s, nc * nc, c.lam2.p, c.pm_AtAc.p, c.pm_GLc.p, c.Mw.p);
+    else
+      klaunch(k_pm_dense, dim3(gd), dim3(kBlock), 0, s, glop(L - 1), c.lam2.p, c.pm_AtAc.p, c.Mw.p);
     LCMG_LAUNCHED();
     klaunch(k_cholesky_inverse, dim3(1), dim3(kBlock), 0, s, (int)nc, c.Mw.p, c.Ww.p, c.kinv.p, c.s_info.p);
     LCMG_LAUNCHED();
@@ -1328,7 +1461,7 @@ struct PaperMG {
   void run(double lam) {
     if (c.prm.precision != LCMG_PREC_FP64) throw ArgError("the paper's preconditioner runs in FP64 (precision = FP64)");
     pm_build(c);
-    L = (int)c.lev.size();
+    L = amg ? (int)c.am.size() : (int)c.lev.size();
     const int64_t n = c.n;
     const int m = c.prm.gmres_restart;
     c.pm_V.need((size_t)(m + 1) * n);
@@ -1809,6 +1942,9 @@ void lcmg_default_params(lcmg_params* p) {
   p->stop_rule = 0;
   p->precond = 0;
   p->gmres_restart = 200;
+  p->coarsening = 0;
+  p->amg_coarse_max = 256;
+  p->compact_cols = 1;
 }
 
 const char* lcmg_last_error(void) { return lcmg::g_err.c_str(); }
@@ -1865,9 +2001,15 @@ int lcmg_set_params(lcmg_ctx* ctx, const lcmg_params* p) {
   NEED_CTX();
   if (!p) throw lcmg::ArgError("null params");
   lcmg::check_params(*p);
-  const bool lev_change = p->levels != ctx->prm.levels || p->coarse_max != ctx->prm.coarse_max;
+  const bool lev_change = p->levels != ctx->prm.levels || p->coarse_max != ctx->prm.coarse_max ||
+                          p->coarsening != ctx->prm.coarsening;
+  const bool amg_change = lev_change || p->amg_coarse_max != ctx->prm.amg_coarse_max;
   ctx->prm = *p;
   if (lev_change) ctx->hier_ok = false;
+  if (amg_change) {
+    ctx->am_ok = false;
+    ctx->pm_levels = 0;
+  }
   API_END
 }
 
@@ -1881,9 +2023,11 @@ int lcmg_set_grid(lcmg_ctx* ctx, int32_t n_v, int32_t n_h) {
   ctx->n = (int64_t)n_v * n_h;
   ctx->ne = (int64_t)n_h * (n_v - 1) + (int64_t)(n_h - 1) * n_v;
   ctx->fwd = 0;
+  ctx->c16_ok = false;
   ctx->tuned.clear();
   ctx->ones_ok = false;
   ctx->pm_levels = 0;
+  ctx->am_ok = false;
   std::vector<double> ones(ctx->ne, 1.0);
   lcmg::copy_sync(ctx->stream, ctx->d.need(ctx->ne), ones.data(), sizeof(double) * ctx->ne, cudaMemcpyHostToDevice);
   lcmg::refresh_fine(*ctx);
@@ -1943,6 +2087,38 @@ int lcmg_set_forward_csr(lcmg_ctx* ctx, int64_t m, int64_t n, const int64_t* row
   }
   for (int64_t k = 0; k < nnz; ++k) tmpf[k] = (float)vT[k];
   lcmg::copy_sync(ctx->stream, ctx->vT32.need(nnz + lcmg::kCsrPad), tmpf.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice);
+  // 16-bit column offsets when every row of A and of A^T spans fewer than
+  // 65,536 columns (base = the row's smallest column)
+  {
+    auto compact = [&](int64_t rows, const int64_t* rp, const int32_t* ci, std::vector<int32_t>& base,
+                       std::vector<uint16_t>& off) {
+      base.assign(rows, 0);
+      off.assign(nnz, 0);
+      for (int64_t r = 0; r < rows; ++r) {
+        if (rp[r + 1] == rp[r]) continue;
+        int32_t mn = ci[rp[r]], mx = mn;
+        for (int64_t k = rp[r]; k < rp[r + 1]; ++k) {
+          mn = std::min(mn, ci[k]);
+          mx = std::max(mx, ci[k]);
+        }
+        if ((int64_t)mx - mn > 65535) return false;
+        base[r] = mn;
+        for (int64_t k = rp[r]; k < rp[r + 1]; ++k) off[k] = (uint16_t)(ci[k] - mn);
+      }
+      return true;
+    };
+    std::vector<int32_t> b1, b2;
+    std::vector<uint16_t> o1, o2;
+    ctx->c16_ok = compact(m, row_ptr, col, b1, o1) && compact(n, rpT.data(), ciT.data(), b2, o2);
+    if (ctx->c16_ok) {
+      lcmg::copy_sync(s, ctx->c16.need(nnz + lcmg::kCsrPad), o1.data(), sizeof(uint16_t) * nnz, cudaMemcpyHostToDevice);
+      lcmg::copy_sync(s, ctx->c16T.need(nnz + lcmg::kCsrPad), o2.data(), sizeof(uint16_t) * nnz, cudaMemcpyHostToDevice);
+      lcmg::copy_sync(s, ctx->rbase.need(m), b1.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice);
+      lcmg::copy_sync(s, ctx->rbaseT.need(n), b2.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+    } else {
+      ctx->c16.release(); ctx->c16T.release(); ctx->rbase.release(); ctx->rbaseT.release();
+    }
+  }
   // zero padding after the last nonzero (read by the 16-byte vector loads)
   lcmg::fill_sync(ctx->stream, ctx->ci.p + nnz, 0, sizeof(int32_t) * lcmg::kCsrPad);
   lcmg::fill_sync(ctx->stream, ctx->ciT.p + nnz, 0, sizeof(int32_t) * lcmg::kCsrPad);
@@ -1968,6 +2144,7 @@ int lcmg_set_forward_csr(lcmg_ctx* ctx, int64_t m, int64_t n, const int64_t* row
   ctx->hier_ok = false;
   ctx->tuned.clear();
   ctx->pm_levels = 0;
+  ctx->am_ok = false;
   API_END
 }
 
@@ -1995,8 +2172,10 @@ int lcmg_set_forward_stencil(lcmg_ctx* ctx, int32_t kh, int32_t kw, const double
   LCMG_LAUNCHED();
   LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->fwd = 2;
+  ctx->c16_ok = false;
   ctx->tuned.clear();
   ctx->pm_levels = 0;
+  ctx->am_ok = false;
   ctx->hier_ok = false;
   API_END
 }
@@ -2116,6 +2295,72 @@ int lcmg_cull_lambdas(int32_t m, int32_t i_prev, int32_t* lo, int32_t* hi) {
   API_BEGIN
   if (m < 1 || i_prev < 0 || i_prev > m || !lo || !hi) throw lcmg::ArgError("bad window arguments");
   lcmg::window(m, i_prev, lo, hi);
+  API_END
+}
+
+namespace lcmg {
+// a square CSR matrix from the caller, checked: rows sorted, columns in range
+static HostCsr host_square_csr(int64_t n, const int64_t* rp, const int32_t* ci, const double* v) {
+  if (n < 1 || n > 2147483647LL || !rp || !ci || !v) throw ArgError("bad matrix arguments");
+  if (rp[0] != 0) throw ArgError("row_ptr[0] must be 0");
+  for (int64_t i = 0; i < n; ++i) {
+    if (rp[i + 1] < rp[i]) throw ArgError("row_ptr must not decrease");
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+      if (ci[k] < 0 || ci[k] >= n) throw ArgError("column index out of range");
+      if (k > rp[i] && ci[k] <= ci[k - 1]) throw ArgError("columns must increase within each row");
+    }
+  }
+  HostCsr K;
+  K.rows = K.cols = n;
+  K.rp.assign(rp, rp + n + 1);
+  K.ci.assign(ci, ci + rp[n]);
+  K.v.assign(v, v + rp[n]);
+  return K;
+}
+}  // namespace lcmg
+
+int lcmg_rs_split(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val, double theta,
+                  int8_t* cf) {
+  API_BEGIN
+  if (!cf || !(theta > 0.0 && theta < 1.0)) throw lcmg::ArgError("null cf or theta outside (0, 1)");
+  const lcmg::HostCsr K = lcmg::host_square_csr(n, row_ptr, col, val);
+  const std::vector<int8_t> s = lcmg::amg::split(lcmg::amg::strength(K, theta), n);
+  std::copy(s.begin(), s.end(), cf);
+  API_END
+}
+
+int lcmg_rs_interp(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val, double theta,
+                   const int8_t* cf, int64_t cap, int64_t* p_row_ptr, int32_t* p_col, double* p_val, int64_t* nnz) {
+  API_BEGIN
+  if (!cf || !nnz || !p_row_ptr || (cap > 0 && (!p_col || !p_val)) || !(theta > 0.0 && theta < 1.0))
+    throw lcmg::ArgError("null output or theta outside (0, 1)");
+  const lcmg::HostCsr K = lcmg::host_square_csr(n, row_ptr, col, val);
+  std::vector<int8_t> c(cf, cf + n);
+  for (int8_t f : c)
+    if (f != lcmg::amg::kC && f != lcmg::amg::kF) throw lcmg::ArgError("cf entries must be 0 or 1");
+  const lcmg::amg::Strength S = lcmg::amg::strength(K, theta);
+  for (int64_t i = 0; i < n; ++i) {  // every F point needs a strong C connection
+    if (c[i] != lcmg::amg::kF) continue;
+    bool has = false;
+    for (int64_t k = S.rp[i]; k < S.rp[i + 1] && !has; ++k) has = c[S.ci[k]] == lcmg::amg::kC;
+    if (!has) throw lcmg::ArgError("F point " + std::to_string(i) + " has no strong C connection");
+  }
+  const lcmg::HostCsr P = lcmg::amg::interpolation(K, S, c);
+  *nnz = (int64_t)P.ci.size();
+  if (cap < *nnz) throw lcmg::ArgError("cap is smaller than the interpolation's entry count");
+  std::copy(P.rp.begin(), P.rp.end(), p_row_ptr);
+  std::copy(P.ci.begin(), P.ci.end(), p_col);
+  std::copy(P.v.begin(), P.v.end(), p_val);
+  API_END
+}
+
+int lcmg_amg_levels(lcmg_ctx* ctx, int32_t cap, int64_t* sizes, int32_t* n_levels) {
+  API_BEGIN
+  NEED_CTX();
+  if (!n_levels || (cap > 0 && !sizes)) throw lcmg::ArgError("null output");
+  if (!ctx->am_ok) throw std::runtime_error("no classical AMG hierarchy has been built for the current weights");
+  *n_levels = (int32_t)ctx->am.size();
+  for (int32_t k = 0; k < cap && k < *n_levels; ++k) sizes[k] = ctx->am[k].n;
   API_END
 }
 
@@ -2239,6 +2484,7 @@ int lcmg_apply_vcycle_dev(lcmg_ctx* ctx, int32_t n_cols, const double* lambda, c
   if (ctx->prm.precond == 1) {  // the paper's V(2,1), one column at a time, FP64
     lcmg::pm_build(*ctx);
     lcmg::PaperMG pmg(*ctx);
+    pmg.L = pmg.amg ? (int)ctx->am.size() : (int)ctx->lev.size();
     for (int j = 0; j < B; ++j) {
       pmg.setup(lam[j]);
       pmg.cycle(0, r_dev + (int64_t)j * ctx->n, z_dev + (int64_t)j * ctx->n);

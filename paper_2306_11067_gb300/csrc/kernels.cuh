@@ -413,6 +413,10 @@ struct SpmmArgs {
   int* err;               // set to 1 when a staging wait gives up
   int variant;            // one-column kernel (k_spmv1): 0 = the pass's default,
                           // 1 = 32 lanes x 4, 2 = 16 lanes x 8, 3 = 8 lanes x 8
+  // one-column kernel: column of nonzero k of row r = rbase[r] + c16[k]
+  // (null: ci), 6 instead of 8 bytes per FP32 nonzero
+  const uint16_t* c16;
+  const int32_t* rbase;
 };
 
 template <class V, class T, class TO, int G, int CPG, int MODE>
@@ -528,8 +532,10 @@ __global__ void __launch_bounds__(kBlock)
 // Measured on GB300 (256^2 CT, 15M nonzeros): y = A p is fastest with 32
 // lanes per row and U = 4; the transposed pass, whose epilogue (L^T W L p
 // and p.q) runs on one lane per row, with 8 lanes per row and U = 8.
+// C16: column indices as 16-bit offsets from a per-row base (a.c16,
+// a.rbase), when every row's column span is below 65,536.
 // ---------------------------------------------------------------------------
-template <class V, class T, class TO, int MODE, int U, int LPR, bool PF>
+template <class V, class T, class TO, int MODE, int U, int LPR, bool PF, bool C16>
 __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? (LPR == 32 ? 8 : 4) : (LPR == 32 ? 5 : 3))
     k_spmv1(SpmmArgs a, const V* __restrict__ va, const T* __restrict__ X, TO* __restrict__ Y,
             FineOp<T> fop, const T* __restrict__ P, const T* __restrict__ C,
@@ -549,9 +555,11 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? (LPR == 32 ? 8 : 4) :
   int64_t wr = warp;
   int64_t r = wr * RPW + hw;
   int64_t k0 = 0, k1 = 0;
+  int rb = 0;
   if (r < a.rows) {
     k0 = a.rp[r];
     k1 = a.rp[r + 1];
+    if (C16) rb = a.rbase[r];
   }
   // every lane of a warp runs the same number of steps (the shuffles below
   // take the whole warp); lanes past the last row compute nothing
@@ -559,9 +567,11 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? (LPR == 32 ? 8 : 4) :
     const int64_t wrn = wr + nwarps;
     const int64_t rn = wrn * RPW + hw;
     int64_t k0n = 0, k1n = 0;
+    int rbn = 0;
     if (PF && rn < a.rows) {
       k0n = a.rp[rn];
       k1n = a.rp[rn + 1];
+      if (C16) rbn = a.rbase[rn];
     }
     T acc = 0;
     for (int64_t kb = k0 + sl; kb < k1; kb += LPR * U) {
@@ -572,7 +582,10 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? (LPR == 32 ? 8 : 4) :
       for (int u = 0; u < U; ++u) {
         const int64_t k = kb + (int64_t)u * LPR;
         const bool ok = k < k1;
-        cu[u] = ok ? __ldcs(a.ci + k) : 0;
+        if (C16)
+          cu[u] = ok ? rb + (int)__ldcs(a.c16 + k) : 0;
+        else
+          cu[u] = ok ? __ldcs(a.ci + k) : 0;
         vu[u] = ok ? (T)__ldcs(va + k) : (T)0;
       }
       T xv[U];
@@ -608,9 +621,11 @@ __global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? (LPR == 32 ? 8 : 4) :
     if (PF) {
       k0 = k0n;
       k1 = k1n;
+      rb = rbn;
     } else if (r < a.rows) {
       k0 = a.rp[r];
       k1 = a.rp[r + 1];
+      if (C16) rb = a.rbase[r];
     }
   }
   if (MODE != 0) {

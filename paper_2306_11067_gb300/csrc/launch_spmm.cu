@@ -54,12 +54,13 @@ static int resident_grid(K kern, int threads, size_t smem) {
   return nb * sms;
 }
 
-// One column: k_spmv1 with U nonzeros per lane and LPR lanes per row.
-template <class V, class T, class TO, int MODE, int U, int LPR>
-static int run1v(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop, const T* P,
+// One column: k_spmv1 with U nonzeros per lane and LPR lanes per row;
+// 16-bit column offsets (C16) for the transposed operator pass when present.
+template <class V, class T, class TO, int MODE, int U, int LPR, bool C16>
+static int run1c(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop, const T* P,
                  const T* C, const double* lam2, const double* bvec, double* part, int max_blocks,
                  cudaStream_t s, const ScalarFold* fold) {
-  auto k = k_spmv1<V, T, TO, MODE, U, LPR, true>;
+  auto k = k_spmv1<V, T, TO, MODE, U, LPR, true, C16>;
   int64_t blocks = resident_grid(k, kBlock, 0);
   const int64_t need = (a.rows * LPR + kBlock - 1) / kBlock;
   if (blocks > need) blocks = need;
@@ -69,6 +70,20 @@ static int run1v(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp
           fold ? *fold : ScalarFold{});
   LCMG_LAUNCHED();
   return (int)blocks;
+}
+
+template <class V, class T, class TO, int MODE, int U, int LPR>
+static int run1v(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop, const T* P,
+                 const T* C, const double* lam2, const double* bvec, double* part, int max_blocks,
+                 cudaStream_t s, const ScalarFold* fold) {
+  // measured on GB300 (ct256): the transposed pass (8 lanes x 8) gains
+  // (38.2 -> 35.3 us per pass); y = A p (32 lanes x 4 under a 32-register
+  // cap) loses (31.1 -> 38.3 us), so it keeps int32 columns
+  if constexpr (MODE == 1) {
+    if (a.c16 != nullptr)
+      return run1c<V, T, TO, MODE, U, LPR, true>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
+  }
+  return run1c<V, T, TO, MODE, U, LPR, false>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
 }
 
 // The pass's configuration: a.variant, or by default (measured on GB300,

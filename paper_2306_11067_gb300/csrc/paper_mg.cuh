@@ -4,8 +4,9 @@
 // Level k applies K_k x = A_k^T (A_k x) + lam2 M_k^T (M_k x) in three
 // launches: y = A_k x and t = A_k^T y with the CSR SpMV kernels, then
 // k_pm_lap_add adds lam2 M_k^T M_k x, where M_k^T M_k = G_L^k is the
-// Galerkin coarsening of L^T D^2 L (the 5-point fine operator on level 0,
-// the 25-point stencils on coarser levels).  Relaxation is Jacobi-
+// Galerkin coarsening of L^T D^2 L (the 5-point fine operator on level 0;
+// on coarser levels the 25-point stencils of the geometric hierarchy or the
+// CSR matrices of classical AMG).  Relaxation is Jacobi-
 // preconditioned CG; its scalar recurrences are taken by every block from
 // the previous kernel's block partials (summed in a fixed order, so every
 // block computes the same alpha and beta and no scalar kernel or host
@@ -38,6 +39,24 @@ struct GLOp {
     return acc;
   }
   __device__ __forceinline__ double diagL(int64_t p, int, int) const { return gl[(int64_t)12 * n + p]; }
+};
+
+// G_L^k of a classical AMG level: an unstructured CSR matrix (columns
+// sorted) with its diagonal.  nv = n, so a point's (i, j) is (p, 0).
+struct CsrGLOp {
+  int nv;
+  int64_t n;
+  const int64_t* __restrict__ rp;
+  const int32_t* __restrict__ ci;
+  const double* __restrict__ v;
+  const double* __restrict__ dg;
+  template <class F>
+  __device__ __forceinline__ double lap(int64_t p, int, int, F x) const {
+    double acc = 0.0;
+    for (int64_t k = rp[p]; k < rp[p + 1]; ++k) acc += v[k] * x((int64_t)ci[k]);
+    return acc;
+  }
+  __device__ __forceinline__ double diagL(int64_t p, int, int) const { return dg[p]; }
 };
 
 // sum of the first nb block partials, in index order (every block gets the
@@ -192,6 +211,32 @@ __global__ void __launch_bounds__(kBlock)
     if (di >= -2 && di <= 2 && dj >= -2 && dj <= 2)
       v += l2 * op.gl[(int64_t)((di + 2) + 5 * (dj + 2)) * n + p];
     M[e] = v;
+  }
+}
+
+// dense K_c = A_c^T A_c + lam2 G_L^c from the dense G_L^c of a classical
+// AMG coarsest level (nn = n_c^2 entries)
+__global__ void __launch_bounds__(kBlock)
+    k_pm_dense_add(int64_t nn, const double* __restrict__ lam2, const double* __restrict__ AtA,
+                   const double* __restrict__ G, double* __restrict__ M) {
+  pdl_entry();
+  const double l2 = lam2[0];
+  for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < nn; e += (int64_t)gridDim.x * kBlock)
+    M[e] = AtA[e] + l2 * G[e];
+}
+
+// y = M x (ADD: y += M x) for a CSR matrix M of `rows` rows: the
+// restriction P^T r and the prolongation x += P e of classical AMG levels;
+// one thread per row (P has a few entries per row)
+template <bool ADD>
+__global__ void __launch_bounds__(kBlock)
+    k_pm_csr_mv(int64_t rows, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                const double* __restrict__ v, const double* __restrict__ x, double* __restrict__ y) {
+  pdl_entry();
+  for (int64_t r = (int64_t)blockIdx.x * kBlock + threadIdx.x; r < rows; r += (int64_t)gridDim.x * kBlock) {
+    double acc = 0.0;
+    for (int64_t k = rp[r]; k < rp[r + 1]; ++k) acc += v[k] * x[ci[k]];
+    y[r] = ADD ? y[r] + acc : acc;
   }
 }
 

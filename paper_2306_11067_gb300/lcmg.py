@@ -46,7 +46,8 @@ class lcmg_params(C.Structure):
                 ("autotune", C.c_int32),
                 ("spmv_variant", C.c_int32),
                 ("stop_rule", C.c_int32),
-                ("precond", C.c_int32), ("gmres_restart", C.c_int32)]
+                ("precond", C.c_int32), ("gmres_restart", C.c_int32),
+                ("coarsening", C.c_int32), ("amg_coarse_max", C.c_int32), ("compact_cols", C.c_int32)]
 
 
 class lcmg_stats(C.Structure):
@@ -110,6 +111,9 @@ _SIGS = {
     "lcmg_update_weights": (C.c_int, [_P, _P, _D, _D, _P]),
     "lcmg_update_weights_dev": (C.c_int, [_P, _P, _D, _D]),
     "lcmg_cull_lambdas": (C.c_int, [_I32, _I32, _PI32, _PI32]),
+    "lcmg_rs_split": (C.c_int, [_I64, _P, _P, _P, _D, _P]),
+    "lcmg_rs_interp": (C.c_int, [_I64, _P, _P, _P, _D, _P, _I64, _P, _P, _P, _PI64]),
+    "lcmg_amg_levels": (C.c_int, [_P, _I32, _P, _PI32]),
     "lcmg_lcurve_run": (C.c_int, [_P, _I32, _P, _P, _I32, _P, _P, _PI32, _PI64, _PI64]),
     "lcmg_lcurve_run_dev": (C.c_int, [_P, _I32, _P, _P, _I32, _P, _P, _PI32, _PI64, _PI64]),
     "lcmg_get_stats": (C.c_int, [_P, C.POINTER(lcmg_stats)]),
@@ -290,6 +294,45 @@ def lcmg_cull_lambdas(m: int, i_prev: int):
     lo, hi = C.c_int32(), C.c_int32()
     _check(lib().lcmg_cull_lambdas(m, i_prev, C.byref(lo), C.byref(hi)))
     return lo.value, hi.value
+
+
+def _csr_in(K):
+    """(n, row_ptr int64, col int32 sorted per row, val f64) of a square
+    scipy-like CSR matrix."""
+    n = K.shape[0]
+    K = K.tocsr()
+    K.sort_indices()
+    return (n, np.ascontiguousarray(K.indptr, dtype=np.int64), np.ascontiguousarray(K.indices, dtype=np.int32),
+            np.ascontiguousarray(K.data, dtype=np.float64))
+
+
+def lcmg_rs_split(K, theta=0.25):
+    """C/F split of classical AMG (host): int8 array, 1 = C, 0 = F."""
+    n, rp, ci, v = _csr_in(K)
+    cf = np.empty(n, np.int8)
+    _check(lib().lcmg_rs_split(n, _ptr(rp), _ptr(ci), _ptr(v), theta, _ptr(cf)))
+    return cf
+
+
+def lcmg_rs_interp(K, cf, theta=0.25):
+    """Interpolation of the split cf (host): (row_ptr, col, val, n_coarse)."""
+    n, rp, ci, v = _csr_in(K)
+    cf = np.ascontiguousarray(cf, dtype=np.int8)
+    nnz = C.c_int64()
+    prp = np.empty(n + 1, np.int64)
+    cap = int(v.size) + n
+    pci = np.empty(cap, np.int32)
+    pv = np.empty(cap)
+    _check(lib().lcmg_rs_interp(n, _ptr(rp), _ptr(ci), _ptr(v), theta, _ptr(cf), cap, _ptr(prp), _ptr(pci),
+                                _ptr(pv), C.byref(nnz)))
+    return prp, pci[:nnz.value].copy(), pv[:nnz.value].copy(), int(cf.sum())
+
+
+def lcmg_amg_levels(ctx):
+    sizes = np.zeros(64, np.int64)
+    nl = C.c_int32()
+    _check(lib().lcmg_amg_levels(ctx, 64, _ptr(sizes), C.byref(nl)))
+    return sizes[:nl.value].copy()
 
 
 def lcmg_lcurve_run(ctx, lambdas, b, max_outer: int, n: int):

@@ -70,3 +70,44 @@ def test_server_rejects_bad_arguments_without_a_device():
     assert L.lib().lcmg_server_create(None, 0, 1 << 30, 2, C.byref(p)) == L.LCMG_ERR_INVALID_ARG
     assert b"bad arguments" in L.lib().lcmg_server_last_error()
     assert L.lib().lcmg_server_destroy(None) == L.LCMG_OK
+
+
+def _amg_levels(n_v, n_h, d, max_coarse=16):
+    from oracle import amg, operators as ops, multigrid as mg
+    return amg.hierarchy(mg.weighted_laplacian(ops.gradient(n_v, n_h), d), max_coarse=max_coarse)
+
+
+@pytest.mark.parametrize("n_v,n_h,seed", [(16, 16, 1), (32, 28, 2), (48, 52, 3), (9, 31, 4)])
+@pytest.mark.parametrize("weights", ["random", "ones"])
+def test_rs_split_and_interpolation_match_oracle(n_v, n_h, seed, weights):
+    """Classical AMG on the host (lcmg_rs_split / lcmg_rs_interp) on every
+    level of the oracle's hierarchy of L^T D^2 L: the C/F split is the same
+    bit for bit (integer work), P within 1e-14."""
+    import scipy.sparse as sp
+    from oracle import operators as ops
+    ne = ops.n_edges(n_v, n_h)
+    d = pg.random_weights(ne, seed, d_min=0.02) if weights == "random" else np.ones(ne)
+    Ks, Ps, cfs = _amg_levels(n_v, n_h, d)
+    assert len(Ps) >= 2
+    for k, P in enumerate(Ps):
+        cf = L.lcmg_rs_split(Ks[k])
+        assert (cf == cfs[k]).all(), (k, int((cf != cfs[k]).sum()))
+        rp, ci, v, nc = L.lcmg_rs_interp(Ks[k], cf)
+        Pl = sp.csr_matrix((v, ci, rp), shape=(Ks[k].shape[0], nc))
+        assert nc == P.shape[1]
+        assert abs(Pl - P).max() <= 1e-14
+
+
+def test_rs_host_argument_errors():
+    import scipy.sparse as sp
+    K = sp.csr_matrix(np.array([[2.0, -1.0], [-1.0, 2.0]]))
+    with pytest.raises(L.LcmgError) as e:
+        L.lcmg_rs_split(K, theta=1.5)
+    assert e.value.status == L.LCMG_ERR_INVALID_ARG
+    n, rp, ci, v = L._csr_in(K)
+    bad = ci.copy()
+    bad[0], bad[1] = bad[1], bad[0]                       # unsorted row
+    cf = np.empty(2, np.int8)
+    assert L.lib().lcmg_rs_split(n, L._ptr(rp), L._ptr(bad), L._ptr(v), 0.25, L._ptr(cf)) == L.LCMG_ERR_INVALID_ARG
+    with pytest.raises(L.LcmgError):                     # an F point without a strong C connection
+        L.lcmg_rs_interp(K, np.array([0, 0], np.int8))
