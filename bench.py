@@ -36,7 +36,7 @@ WORKLOAD = "ct256"
 WORKLOAD_DESC = ("ct256: 256x256 parallel-beam CT, 180 angles x 363 bins exact ray-length CSR "
                  "(FP32 values, int32 indices), 10 seeded ellipses, 1% noise, 20 lambdas "
                  "logspace(-4, 0), Algorithm 2 (max 15 outer iterations, three-equal stop, "
-                 "largest-lambda-first warm-start chain), rel-res 1e-6, 5-level V(2,2) l1-Jacobi")
+                 "largest-lambda-first warm-start chain), rel-res 1e-6, 5-level V(1,1) l1-Jacobi")
 METRIC = "lambda-solves/s at rel-res 1e-6"
 KERNEL_SRC = os.path.join(ROOT, "paper_2306_11067_gb300", "csrc", "kernels.cuh")
 LAUNCH_SRC = os.path.join(ROOT, "paper_2306_11067_gb300", "csrc", "launch_spmm.cu")

@@ -83,8 +83,10 @@ typedef struct {
   int32_t levels;       /* multigrid levels incl. the finest; 0 = coarsen by 2 while
                            both sides are even and one exceeds coarse_max            */
   int32_t coarse_max;   /* side limit of the coarsest grid for levels = 0 (default 16) */
-  int32_t nu;           /* pre- = post-smoothing sweeps (default 2; equal counts keep
-                           the V-cycle symmetric so CG applies)                      */
+  int32_t nu;           /* pre- = post-smoothing sweeps (default 1; equal counts keep
+                           the V-cycle symmetric so CG applies; on the 256^2 CT
+                           chain V(1,1) needs fewer PCG iterations than V(2,2)
+                           and each is cheaper)                                     */
   int32_t smoother;     /* lcmg_smoother (default l1-Jacobi)                         */
   double omega;         /* damping of LCMG_SMOOTH_JACOBI (default 2/3)               */
   double q;             /* exponent of eq. (g) (default 2)                           */
@@ -174,6 +176,12 @@ typedef struct {
                            fewer than 65,536 columns, else int32 indices are
                            read; default); 0 = always int32.  Results are
                            bitwise identical                                 */
+  int32_t alpha_fuse;   /* one column (batch of 1): 1 = every block of the x/r
+                           update sums the p.q partials itself (fixed order)
+                           and applies alpha = r.z / p.q, so no scalar kernel
+                           runs between the operator and the update (default);
+                           0 = a scalar kernel computes alpha first.  The two
+                           sum in different orders (last-bit differences)  */
 } lcmg_params;
 
 typedef struct lcmg_ctx lcmg_ctx;

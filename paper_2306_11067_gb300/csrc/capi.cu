@@ -292,6 +292,7 @@ static void check_params(const lcmg_params& p) {
   if (p.gmres_restart < 1 || p.gmres_restart > 2000) throw ArgError("gmres_restart must be 1..2000");
   if (p.coarsening != 0 && p.coarsening != 1) throw ArgError("coarsening must be 0 or 1");
   if (p.compact_cols != 0 && p.compact_cols != 1) throw ArgError("compact_cols must be 0 or 1");
+  if (p.alpha_fuse != 0 && p.alpha_fuse != 1) throw ArgError("alpha_fuse must be 0 or 1");
   if (p.amg_coarse_max < 2 || p.amg_coarse_max > 2048) throw ArgError("amg_coarse_max must be 2..2048");
 }
 
@@ -713,15 +714,17 @@ struct Batch {
     fa.ticket = c.tickets.p;
     bool alpha_folded = false;
     const int nb_pq = apply_K(P, Q, c.part_pq.p, c.prm.fold ? &fa : nullptr, &alpha_folded);
-    if (!alpha_folded) {
-      klaunch(k_scalar_col_alpha, dim3(B), dim3(kColThreads), 0, s, B, nb_pq, c.part_pq.p, st);
-      LCMG_LAUNCHED();
-    }
+    T* X = std::is_same<T, double>::value ? reinterpret_cast<T*>(c.x64.p) : reinterpret_cast<T*>(c.xlo.p);
     int nb_rr;
-    if (std::is_same<T, double>::value)
-      nb_rr = launch_update_xr<T, T>(c.n, B, st, P, Q, reinterpret_cast<T*>(c.x64.p), R, c.part_rr.p, c.maxblk, s);
-    else
-      nb_rr = launch_update_xr<T, T>(c.n, B, st, P, Q, reinterpret_cast<T*>(c.xlo.p), R, c.part_rr.p, c.maxblk, s);
+    if (!alpha_folded && B == 1 && c.prm.alpha_fuse) {  // alpha inside the update
+      nb_rr = launch_update_xr_alpha<T, T>(c.n, st, nb_pq, c.part_pq.p, P, Q, X, R, c.part_rr.p, c.maxblk, s);
+    } else {
+      if (!alpha_folded) {
+        klaunch(k_scalar_col_alpha, dim3(B), dim3(kColThreads), 0, s, B, nb_pq, c.part_pq.p, st);
+        LCMG_LAUNCHED();
+      }
+      nb_rr = launch_update_xr<T, T>(c.n, B, st, P, Q, X, R, c.part_rr.p, c.maxblk, s);
+    }
     // beta in the last block of the final level-0 sweep when possible
     ScalarFold fb{};
     fb.st = st;
@@ -1918,7 +1921,7 @@ void lcmg_default_params(lcmg_params* p) {
   std::memset(p, 0, sizeof(*p));
   p->levels = 0;
   p->coarse_max = 16;
-  p->nu = 2;
+  p->nu = 1;
   p->smoother = LCMG_SMOOTH_L1_JACOBI;
   p->omega = 2.0 / 3.0;
   p->q = 2.0;
@@ -1945,6 +1948,7 @@ void lcmg_default_params(lcmg_params* p) {
   p->coarsening = 0;
   p->amg_coarse_max = 256;
   p->compact_cols = 1;
+  p->alpha_fuse = 1;
 }
 
 const char* lcmg_last_error(void) { return lcmg::g_err.c_str(); }

@@ -997,6 +997,70 @@ __global__ void __launch_bounds__(kBlock)
   block_col_sum(acc, cm, sm, part + (int64_t)blockIdx.x * B);
 }
 
+// One column (B = 1) with alpha taken in the update: every block sums the
+// p.q partials in the same fixed order, so all blocks compute the same
+// alpha = rz / p.q and the same breakdown decision; block 0 alone records
+// the column state (iteration count, status) and clears the counters that
+// k_scalar_col_beta accumulates.  No block reads what block 0 writes, and
+// block 0 writes active = 0 only when every block has found the step void.
+template <class T, class TX>
+__global__ void __launch_bounds__(kBlock)
+    k_update_xr_alpha(int64_t n, ColState st, int nb_pq, const double* __restrict__ pq_part,
+                      const T* __restrict__ p, const T* __restrict__ q, TX* __restrict__ x, T* __restrict__ r,
+                      double* __restrict__ part) {
+  pdl_entry();
+  __shared__ double sm[kBlock / 32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb_pq; b += kBlock) s += pq_part[b];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double pq = 0.0;
+#pragma unroll
+  for (int w = 0; w < kBlock / 32; ++w) pq += sm[w];
+  __syncthreads();
+  const int act = st.active[0];
+  const bool fin = isfinite(pq);
+  const bool ok = act && fin && pq > 0.0;
+  const double al = ok ? st.rz[0] / pq : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st.counters[0] = 0;
+    st.counters[1] = 0;
+    st.counters[2] = 0;
+    st.alpha[0] = al;
+    if (act) {
+      st.iters[0] += 1;
+      if (!fin) {
+        st.status[0] = ST_NONFINITE;
+        st.active[0] = 0;
+      } else if (!(pq > 0.0)) {
+        st.status[0] = ST_BREAKDOWN;
+        st.active[0] = 0;
+      }
+    }
+  }
+  double acc = 0.0;
+  if (ok) {
+    const T alT = (T)al;
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
+      x[i] = (TX)(x[i] + (TX)al * (TX)p[i]);
+      const T rn = r[i] - alT * q[i];
+      r[i] = rn;
+      acc += to_d(rn) * to_d(rn);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) t += sm[w];
+    part[blockIdx.x] = t;
+  }
+}
+
 // p = z + beta p
 template <class T>
 __global__ void __launch_bounds__(kBlock)

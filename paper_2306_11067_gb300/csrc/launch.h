@@ -67,6 +67,10 @@ void launch_galerkin(const RapIn& in, int nvc, int nhc, double* out, int max_blo
 template <class T, class TX>
 int launch_update_xr(int64_t n, int B, const ColState& st, const T* p, const T* q, TX* x, T* r,
                      double* part, int max_blocks, cudaStream_t s);
+// one column: alpha from the p.q partials inside the update (no scalar kernel)
+template <class T, class TX>
+int launch_update_xr_alpha(int64_t n, const ColState& st, int nb_pq, const double* pq_part, const T* p,
+                           const T* q, TX* x, T* r, double* part, int max_blocks, cudaStream_t s);
 template <class T>
 void launch_update_p(int64_t n, int B, const ColState& st, const T* z, T* p, int max_blocks,
                      cudaStream_t s);

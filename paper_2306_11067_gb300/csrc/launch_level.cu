@@ -137,6 +137,15 @@ int launch_update_xr(int64_t n, int B, const ColState& st, const T* p, const T* 
   return g;
 }
 
+template <class T, class TX>
+int launch_update_xr_alpha(int64_t n, const ColState& st, int nb_pq, const double* pq_part, const T* p,
+                           const T* q, TX* x, T* r, double* part, int max_blocks, cudaStream_t s) {
+  const int g = grid_for(n, 1, max_blocks);
+  klaunch(k_update_xr_alpha<T, TX>, dim3(g), dim3(kBlock), 0, s, n, st, nb_pq, pq_part, p, q, x, r, part);
+  LCMG_LAUNCHED();
+  return g;
+}
+
 template <class T>
 void launch_update_p(int64_t n, int B, const ColState& st, const T* z, T* p, int max_blocks,
                      cudaStream_t s) {
@@ -182,5 +191,11 @@ template int launch_update_xr<double, double>(int64_t, int, const ColState&, con
 template int launch_update_xr<float, float>(int64_t, int, const ColState&, const float*,
                                             const float*, float*, float*, double*, int,
                                             cudaStream_t);
+template int launch_update_xr_alpha<double, double>(int64_t, const ColState&, int, const double*,
+                                                    const double*, const double*, double*, double*,
+                                                    double*, int, cudaStream_t);
+template int launch_update_xr_alpha<float, float>(int64_t, const ColState&, int, const double*, const float*,
+                                                  const float*, float*, float*, double*, int,
+                                                  cudaStream_t);
 
 }  // namespace lcmg

@@ -47,7 +47,8 @@ class lcmg_params(C.Structure):
                 ("spmv_variant", C.c_int32),
                 ("stop_rule", C.c_int32),
                 ("precond", C.c_int32), ("gmres_restart", C.c_int32),
-                ("coarsening", C.c_int32), ("amg_coarse_max", C.c_int32), ("compact_cols", C.c_int32)]
+                ("coarsening", C.c_int32), ("amg_coarse_max", C.c_int32), ("compact_cols", C.c_int32),
+                ("alpha_fuse", C.c_int32)]
 
 
 class lcmg_stats(C.Structure):

@@ -27,7 +27,7 @@ def test_library_exports_every_header_function():
 
 def test_default_params():
     p = L.lcmg_default_params()
-    assert (p.nu, p.coarse_max, p.maxit, p.check_every, p.graphs) == (2, 16, 10000, 16, 1)
+    assert (p.nu, p.coarse_max, p.maxit, p.check_every, p.graphs) == (1, 16, 10000, 16, 1)
     assert (p.tol, p.q, p.d_min) == (1e-6, 2.0, 1e-3)
     # execution-path options: the measured-fastest combination on GB300
     assert (p.fused, p.tail_points, p.pdl, p.fold, p.staged, p.vfuse) == (0, 0, 0, 0, 0, 1)

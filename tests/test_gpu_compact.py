@@ -57,3 +57,30 @@ def test_wide_rows_fall_back_to_int32_columns():
     x, *_ = krylov.pcg(lambda v: ops.normal_apply(F, Lg, d, 0.5, v), c, None, mg.VCycle(H, 0.5), tol=1e-12,
                        maxit=5000)
     assert np.linalg.norm(outs[0]["x"][0, 0] - x) <= 1e-7 * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("precision,bound", [(L.PREC_FP64, 1e-8), (L.PREC_MIXED, 1e-6)])
+def test_alpha_inside_the_update_matches_the_scalar_kernel(precision, bound):
+    """One column: alpha taken by every block of the x/r update (alpha_fuse =
+    1, the default) and by the scalar kernel (0) sum p.q in different orders;
+    both solve to the oracle's solution and report the same status."""
+    P = pg.make_problem("ct256", size=48)
+    lams = np.array([0.05, 0.5])
+    outs = []
+    for af in (1, 0):
+        s = Solver(48, 48, mode=L.MODE_SEQUENTIAL, tol=1e-12, maxit=20000, precision=precision, alpha_fuse=af)
+        s.set_forward_csr(P.A)
+        outs.append(s.solve(lams, P.b[:, 0]))
+        s.close()
+    F = ops.ForwardCSR(P.A.to_scipy())
+    Lg = ops.gradient(48, 48)
+    d = np.ones(ops.n_edges(48, 48))
+    H = mg.build_hierarchy(mg.weighted_laplacian(Lg, d), sp.diags(F.diag_AtA()), 48, 48, 3)
+    c = ops.rhs(F, P.b[:, 0])
+    for j, lam in enumerate(lams):
+        x, *_ = krylov.pcg(lambda v: ops.normal_apply(F, Lg, d, lam, v), c, None, mg.VCycle(H, lam), tol=1e-12,
+                           maxit=20000)
+        for out in outs:
+            assert out["status"][0, j] == 0
+            assert np.linalg.norm(out["x"][0, j] - x) <= bound * np.linalg.norm(x)
+        assert abs(int(outs[0]["iters"][0, j]) - int(outs[1]["iters"][0, j])) <= max(3, 0.05 * outs[1]["iters"][0, j])

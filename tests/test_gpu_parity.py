@@ -148,11 +148,12 @@ def test_galerkin_levels_parity(n_v, n_h, levels):
 @pytest.mark.parametrize("smoother", [L.SMOOTH_L1_JACOBI, L.SMOOTH_JACOBI])
 @pytest.mark.parametrize("n_v,n_h,levels", [(32, 32, 3), (40, 24, 3), (8, 8, 1)])
 @pytest.mark.parametrize("tail_points", [0, 4096, 100000])
-def test_vcycle_parity(smoother, n_v, n_h, levels, tail_points):
+@pytest.mark.parametrize("nu", [1, 2])
+def test_vcycle_parity(smoother, n_v, n_h, levels, tail_points, nu):
     """tail_points 0: one kernel per level step; 4096: the small levels in one
     CTA; 100000: every coarse level in one CTA."""
     A = pg.blur_csr(n_v, n_h, pg.gaussian_psf(2, 1.0))
-    s = Solver(n_v, n_h, levels=levels, smoother=smoother, tail_points=tail_points, vfuse=0)
+    s = Solver(n_v, n_h, levels=levels, smoother=smoother, tail_points=tail_points, vfuse=0, nu=nu)
     s.set_forward_csr(A)
     d = pg.random_weights(ops.n_edges(n_v, n_h), 9)
     s.set_weights(d)
@@ -166,7 +167,7 @@ def test_vcycle_parity(smoother, n_v, n_h, levels, tail_points):
     H = mg.build_hierarchy(mg.weighted_laplacian(Lg, d), sp.diags(F.diag_AtA()), n_v, n_h, levels)
     sm = "l1" if smoother == L.SMOOTH_L1_JACOBI else "jacobi"
     for j, lam in enumerate(lams):
-        ref = mg.VCycle(H, lam, nu=2, smoother=sm)(R[j])
+        ref = mg.VCycle(H, lam, nu=nu, smoother=sm)(R[j])
         assert _rel(zd[j].cpu().numpy(), ref) <= 1e-12, (lam, _rel(zd[j].cpu().numpy(), ref))
     s.close()
 
