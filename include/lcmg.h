@@ -108,8 +108,8 @@ typedef struct {
                            0 = one kernel per step (default)                        */
   int32_t tail_points;  /* levels whose points x columns are at most this run their
                            whole V-cycle part (down to the coarsest solve and back)
-                           in one CTA; 0 = off (default; on GB300 the one-CTA form
-                           is slower than one multi-block kernel per step)          */
+                           in one launch: one CTA or one cluster (tail_ctas);
+                           0 = off (default)                                        */
   int32_t pdl;          /* 1 = launch the kernels of the PCG iteration with
                            programmatic dependent launch, so each kernel is
                            scheduled while its predecessor drains; 0 = plain
@@ -182,6 +182,19 @@ typedef struct {
                            runs between the operator and the update (default);
                            0 = a scalar kernel computes alpha first.  The two
                            sum in different orders (last-bit differences)  */
+  int32_t beta_fuse;    /* one column with alpha_fuse and keep_direction = 0:
+                           1 = every block of the p update sums the r.r and
+                           r.z partials itself, takes the convergence /
+                           limit / breakdown decision and applies
+                           beta = r.z_new / r.z (default); 0 = a scalar kernel
+                           computes beta first                             */
+  int32_t tail_ctas;    /* with tail_points > 0: run the tail levels in one
+                           CTA (1, default) or in one thread-block cluster of
+                           up to this many CTAs (2..16; the largest power of
+                           two that fits on the device), the points of each
+                           level strided over the whole cluster and the steps
+                           separated by cluster barriers; combines with the
+                           two-kernels-per-level V-cycle (vfuse)            */
 } lcmg_params;
 
 typedef struct lcmg_ctx lcmg_ctx;

@@ -178,7 +178,7 @@ struct lcmg_ctx {
   DevBuf<char> lam2T;
   DevBuf<double> kinv, Mw, Ww;
   DevBuf<double> part_pq, part_rr, part_rz, part_x, mega_part;
-  DevBuf<double> s_rz, s_alpha, s_beta, s_rr, s_rmax, s_tol2cc, s_cc, s_rrtrue, s_out;
+  DevBuf<double> s_rz, s_rz2, s_alpha, s_beta, s_rr, s_rmax, s_tol2cc, s_cc, s_rrtrue, s_out;
   DevBuf<int> s_active, s_iters, s_status, s_pending, s_counters, s_info, s_flag;
   DevBuf<double*> colptr;
   DevBuf<int> tickets;  // last-block tickets of the folded scalar updates (kept at zero)
@@ -293,6 +293,8 @@ static void check_params(const lcmg_params& p) {
   if (p.coarsening != 0 && p.coarsening != 1) throw ArgError("coarsening must be 0 or 1");
   if (p.compact_cols != 0 && p.compact_cols != 1) throw ArgError("compact_cols must be 0 or 1");
   if (p.alpha_fuse != 0 && p.alpha_fuse != 1) throw ArgError("alpha_fuse must be 0 or 1");
+  if (p.beta_fuse != 0 && p.beta_fuse != 1) throw ArgError("beta_fuse must be 0 or 1");
+  if (p.tail_ctas < 1 || p.tail_ctas > 16) throw ArgError("tail_ctas must be 1..16");
   if (p.amg_coarse_max < 2 || p.amg_coarse_max > 2048) throw ArgError("amg_coarse_max must be 2..2048");
 }
 
@@ -411,7 +413,7 @@ static void ensure_work(lcmg_ctx& c, int B) {
   const size_t pb = (size_t)kMaxBlocks * B;
   c.part_pq.need(pb); c.part_rr.need(pb); c.part_rz.need(pb); c.part_x.need(pb);
   c.mega_part.need((size_t)kMegaMaxCtas * 2 * kMaxB);
-  for (auto* b : {&c.s_rz, &c.s_alpha, &c.s_beta, &c.s_rr, &c.s_rmax, &c.s_tol2cc, &c.s_cc, &c.s_rrtrue, &c.s_out})
+  for (auto* b : {&c.s_rz, &c.s_rz2, &c.s_alpha, &c.s_beta, &c.s_rr, &c.s_rmax, &c.s_tol2cc, &c.s_cc, &c.s_rrtrue, &c.s_out})
     b->need(B);
   for (auto* b : {&c.s_active, &c.s_iters, &c.s_status, &c.s_pending, &c.s_info, &c.s_flag}) b->need(B);
   c.s_counters.need(4);
@@ -425,7 +427,7 @@ static void ensure_work(lcmg_ctx& c, int B) {
 
 static ColState colstate(lcmg_ctx& c) {
   ColState s;
-  s.rz = c.s_rz.p; s.alpha = c.s_alpha.p; s.beta = c.s_beta.p; s.rr = c.s_rr.p; s.rmax = c.s_rmax.p;
+  s.rz = c.s_rz.p; s.rz2 = c.s_rz2.p; s.alpha = c.s_alpha.p; s.beta = c.s_beta.p; s.rr = c.s_rr.p; s.rmax = c.s_rmax.p;
   s.tol2cc = c.s_tol2cc.p; s.active = c.s_active.p; s.iters = c.s_iters.p; s.status = c.s_status.p;
   s.pending = c.s_pending.p; s.counters = c.s_counters.p;
   // the one-cluster iteration kernel restarts failed columns itself
@@ -553,6 +555,30 @@ struct Batch {
     return nlev;
   }
 
+  // the tail on levels k0 .. nlev-1 (input lw[k0].rhs, output lw[k0].z)
+  void tail(int k0) {
+    TailArgs<T> ta{};
+    ta.B = B;
+    ta.nl = nlev - k0;
+    ta.nu = c.prm.nu;
+    ta.nc = (int)c.lev[nlev - 1].n;
+    ta.kinv = c.kinv.p;
+    ta.lam2T = lam2T();
+    for (int k = k0; k < nlev; ++k) {
+      TailLevel<T>& t = ta.lev[k - k0];
+      t.nv = c.lev[k].nv;
+      t.nh = c.lev[k].nh;
+      t.n = c.lev[k].n;
+      t.cf = view<T>(c, k).cf;
+      t.dinv = tp(c.lw[k].dinv);
+      t.rhs = tp(c.lw[k].rhs);
+      t.z = tp(c.lw[k].z);
+      t.t = tp(c.lw[k].t);
+      t.res = tp(c.lw[k].res);
+    }
+    launch_vcycle_tail<T>(ta, tail_cluster_ctas<T>(c.prm.tail_ctas), s);
+  }
+
   int vcycle(const T* r0, T* z0, double* part, const ScalarFold* fold = nullptr, bool* folded = nullptr) {
     if (folded) *folded = false;
     const int nu = c.prm.nu;
@@ -571,13 +597,19 @@ struct Batch {
     // (the finest level's tiles hold the r.z partials: at most kMaxBlocks)
     const int64_t tiles0 = (int64_t)((c.lev[0].nv / 2 + kVTile - 1) / kVTile) * ((c.lev[0].nh / 2 + kVTile - 1) / kVTile);
     const bool vf = vf_force >= 0 ? vf_force == 1 : (c.prm.vfuse == 2 || (c.prm.vfuse == 1 && B <= kVfuseAutoB));
-    if (vf && (nu == 1 || nu == 2) && c.prm.tail_points <= 0 && tiles0 <= kMaxBlocks) {
-      // two kernels per level: pre-smoothed z of level k goes to t[k]
-      for (int k = 0; k + 1 < nlev; ++k)
+    if (vf && (nu == 1 || nu == 2) && tiles0 <= kMaxBlocks) {
+      // two kernels per level: pre-smoothed z of level k goes to t[k]; the
+      // levels from tail_level() down run in one tail launch
+      const int k0 = tail_level();
+      const int kdown = std::min(k0, nlev - 1);
+      for (int k = 0; k < kdown; ++k)
         launch_vdown<T>(view<T>(c, k), B, lam2T(), tp(c.lw[k].dinv), rhs[k], tp(c.lw[k].t), tp(c.lw[k + 1].rhs),
                         nu, s);
-      launch_coarse_solve<T>((int)c.lev[nlev - 1].n, B, c.kinv.p, rhs[nlev - 1], zz[nlev - 1], s);
-      for (int k = nlev - 2; k >= 0; --k) {
+      if (k0 < nlev)
+        tail(k0);
+      else
+        launch_coarse_solve<T>((int)c.lev[nlev - 1].n, B, c.kinv.p, rhs[nlev - 1], zz[nlev - 1], s);
+      for (int k = kdown - 1; k >= 0; --k) {
         const int g = launch_vup<T>(view<T>(c, k), B, lam2T(), tp(c.lw[k].dinv), rhs[k], zz[k + 1],
                                     tp(c.lw[k].t), zz[k], k == 0 ? part : nullptr, nu, s);
         if (k == 0) nb = g;
@@ -596,26 +628,7 @@ struct Batch {
       launch_restrict<T>(c.lev[k + 1].nv, c.lev[k + 1].nh, B, tp(c.lw[k].res), tp(c.lw[k + 1].rhs), c.maxblk, s);
     }
     if (k0 < nlev) {
-      TailArgs<T> ta{};
-      ta.B = B;
-      ta.nl = nlev - k0;
-      ta.nu = nu;
-      ta.nc = (int)c.lev[nlev - 1].n;
-      ta.kinv = c.kinv.p;
-      ta.lam2T = lam2T();
-      for (int k = k0; k < nlev; ++k) {
-        TailLevel<T>& t = ta.lev[k - k0];
-        t.nv = c.lev[k].nv;
-        t.nh = c.lev[k].nh;
-        t.n = c.lev[k].n;
-        t.cf = view<T>(c, k).cf;
-        t.dinv = tp(c.lw[k].dinv);
-        t.rhs = tp(c.lw[k].rhs);
-        t.z = tp(c.lw[k].z);
-        t.t = tp(c.lw[k].t);
-        t.res = tp(c.lw[k].res);
-      }
-      launch_vcycle_tail<T>(ta, s);
+      tail(k0);
     } else {
       launch_coarse_solve<T>((int)c.lev[nlev - 1].n, B, c.kinv.p, rhs[nlev - 1], zz[nlev - 1], s);
     }
@@ -716,7 +729,8 @@ struct Batch {
     const int nb_pq = apply_K(P, Q, c.part_pq.p, c.prm.fold ? &fa : nullptr, &alpha_folded);
     T* X = std::is_same<T, double>::value ? reinterpret_cast<T*>(c.x64.p) : reinterpret_cast<T*>(c.xlo.p);
     int nb_rr;
-    if (!alpha_folded && B == 1 && c.prm.alpha_fuse) {  // alpha inside the update
+    const bool alpha_fused = !alpha_folded && B == 1 && c.prm.alpha_fuse;
+    if (alpha_fused) {  // alpha inside the update
       nb_rr = launch_update_xr_alpha<T, T>(c.n, st, nb_pq, c.part_pq.p, P, Q, X, R, c.part_rr.p, c.maxblk, s);
     } else {
       if (!alpha_folded) {
@@ -735,6 +749,10 @@ struct Batch {
     fb.rel_trigger = trig;
     bool beta_folded = false;
     const int nb_rz = vcycle(R, Z, c.part_rz.p, c.prm.fold ? &fb : nullptr, &beta_folded);
+    if (!beta_folded && alpha_fused && c.prm.beta_fuse && !c.prm.keep_direction) {  // beta inside the p update
+      launch_update_p_beta<T>(c.n, st, nb_rr, c.part_rr.p, nb_rz, c.part_rz.p, c.prm.maxit, trig, Z, P, c.maxblk, s);
+      return;
+    }
     if (!beta_folded) {
       klaunch(k_scalar_col_beta, dim3(B), dim3(kColThreads), 0, s, B, nb_rr, c.part_rr.p, nb_rz, c.part_rz.p, st,
               c.prm.maxit, trig);
@@ -866,6 +884,7 @@ struct Batch {
     const int nbz = vcycle(tp(c.r), tp(c.z), c.part_rz.p);
     klaunch(k_sum_parts, dim3(1), dim3(kScalarThreads), 0, s, B, nbz, c.part_rz.p, c.s_rz.p);
     LCMG_LAUNCHED();
+    LCMG_CUDA(cudaMemcpyAsync(c.s_rz2.p, c.s_rz.p, sizeof(double) * B, cudaMemcpyDeviceToDevice, s));
     launch_copy_cols<T>(c.n, B, nullptr, tp(c.z), tp(c.p), c.maxblk, s);
     int64_t batch_its = 0;
     cudaEvent_t e0, e1;
@@ -1949,6 +1968,8 @@ void lcmg_default_params(lcmg_params* p) {
   p->amg_coarse_max = 256;
   p->compact_cols = 1;
   p->alpha_fuse = 1;
+  p->beta_fuse = 1;
+  p->tail_ctas = 1;
 }
 
 const char* lcmg_last_error(void) { return lcmg::g_err.c_str(); }

@@ -243,6 +243,10 @@ __global__ void k_coef_pack(int64_t n, const double* __restrict__ gl, const doub
 // ---------------------------------------------------------------------------
 struct ColState {
   double* rz;      // r^T z of the current iterate
+  double* rz2;     // the same value, written by every writer of rz; the
+                   // one-column fused beta writes rz2 only and the fused
+                   // alpha that follows reads rz2 and copies it to rz, so
+                   // neither kernel reads a slot it writes
   double* alpha;
   double* beta;
   double* rr;      // ||r||^2 (recursive)
@@ -268,6 +272,7 @@ __device__ __forceinline__ void mark_pending(const ColState& st, int col, double
   if (st.keep && rzn > 0.0) {
     st.beta[col] = rzn / st.rz[col];
     st.rz[col] = rzn;
+    st.rz2[col] = rzn;
   } else {
     st.beta[col] = 0.0;
   }
@@ -368,6 +373,7 @@ __device__ __forceinline__ void fold_beta(const ScalarFold& f, int B, const doub
     } else {
       st.beta[col] = rzn / st.rz[col];
       st.rz[col] = rzn;
+      st.rz2[col] = rzn;
       if (f.rel_trigger > 0.0 && rr < f.rel_trigger * st.rmax[col]) atomicAdd(&nvote, 1);
     }
   }
@@ -999,10 +1005,11 @@ __global__ void __launch_bounds__(kBlock)
 
 // One column (B = 1) with alpha taken in the update: every block sums the
 // p.q partials in the same fixed order, so all blocks compute the same
-// alpha = rz / p.q and the same breakdown decision; block 0 alone records
-// the column state (iteration count, status) and clears the counters that
-// k_scalar_col_beta accumulates.  No block reads what block 0 writes, and
-// block 0 writes active = 0 only when every block has found the step void.
+// alpha = rz / p.q (rz read from the rz2 slot) and the same breakdown
+// decision; block 0 alone records the column state (iteration count,
+// status, rz = rz2) and clears the counters the beta step accumulates.  No
+// block reads what block 0 writes, and block 0 writes active = 0 only when
+// every block has found the step void.
 template <class T, class TX>
 __global__ void __launch_bounds__(kBlock)
     k_update_xr_alpha(int64_t n, ColState st, int nb_pq, const double* __restrict__ pq_part,
@@ -1021,10 +1028,12 @@ __global__ void __launch_bounds__(kBlock)
   for (int w = 0; w < kBlock / 32; ++w) pq += sm[w];
   __syncthreads();
   const int act = st.active[0];
+  const double rzc = st.rz2[0];
   const bool fin = isfinite(pq);
   const bool ok = act && fin && pq > 0.0;
-  const double al = ok ? st.rz[0] / pq : 0.0;
+  const double al = ok ? rzc / pq : 0.0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st.rz[0] = rzc;
     st.counters[0] = 0;
     st.counters[1] = 0;
     st.counters[2] = 0;
@@ -1058,6 +1067,76 @@ __global__ void __launch_bounds__(kBlock)
     double t = 0.0;
     for (int w = 0; w < kBlock / 32; ++w) t += sm[w];
     part[blockIdx.x] = t;
+  }
+}
+
+// sum of part[0 .. nb) in a fixed order, the same in every block
+__device__ __forceinline__ double fixed_block_sum(const double* __restrict__ part, int nb, double* sm) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kBlock) s += part[b];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < kBlock / 32; ++w) t += sm[w];
+  __syncthreads();
+  return t;
+}
+
+// One column (B = 1, st.keep = 0) with beta taken in the p update: every
+// block sums the r.r and r.z partials in the same fixed order and takes the
+// same decision as k_scalar_col_beta (non-finite, converged -> true-residual
+// check, iteration limit, breakdown, or a regular step with
+// beta = rz_new / rz); only a regular step updates p = z + beta p.  Block 0
+// alone writes the column state; the new rz goes to the rz2 slot (the fused
+// alpha of the next iteration reads it there and copies it to rz), so no
+// block reads a value written in this kernel, and block 0 clears active
+// only when every block has found no regular step.
+template <class T>
+__global__ void __launch_bounds__(kBlock)
+    k_update_p_beta(int64_t n, ColState st, int nb_rr, const double* __restrict__ rr_part, int nb_rz,
+                    const double* __restrict__ rz_part, int maxit, double rel_trigger, const T* __restrict__ z,
+                    T* __restrict__ p) {
+  pdl_entry();
+  __shared__ double sm[kBlock / 32];
+  const double rr = fixed_block_sum(rr_part, nb_rr, sm);
+  const double rzn = fixed_block_sum(rz_part, nb_rz, sm);
+  const int act = st.active[0];
+  const double rzo = st.rz[0];
+  int kind = -1;  // -1 inactive, 0 regular, 1 converged, 2 limit, 3 breakdown, 4 non-finite
+  if (act) {
+    if (!isfinite(rr) || !isfinite(rzn)) kind = 4;
+    else if (rr <= st.tol2cc[0]) kind = 1;
+    else if (st.iters[0] >= maxit) kind = 2;
+    else if (!(rzn > 0.0)) kind = 3;
+    else kind = 0;
+  }
+  const double be = kind == 0 ? rzn / rzo : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (act) {
+      st.rr[0] = rr;
+      if (kind == 0) {
+        st.beta[0] = be;
+        st.rz2[0] = rzn;
+        if (rel_trigger > 0.0 && rr < rel_trigger * st.rmax[0]) atomicAdd(&st.counters[2], 1);
+      } else {
+        st.beta[0] = 0.0;
+        st.active[0] = 0;
+        if (kind == 1) st.pending[0] = 1;
+        if (kind == 2) st.status[0] = ST_MAXIT;
+        if (kind == 3) st.status[0] = ST_BREAKDOWN;
+        if (kind == 4) st.status[0] = ST_NONFINITE;
+      }
+    }
+    if (st.active[0]) atomicAdd(&st.counters[0], 1);
+    if (st.pending[0]) atomicAdd(&st.counters[1], 1);
+  }
+  if (kind == 0) {
+    const T bT = (T)be;
+    for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock)
+      p[i] = z[i] + bT * p[i];
   }
 }
 
@@ -1184,6 +1263,7 @@ static __global__ void __launch_bounds__(kColThreads)
       } else {
         st.beta[col] = rzn / st.rz[col];
         st.rz[col] = rzn;
+        st.rz2[col] = rzn;
         if (rel_trigger > 0.0 && rr < rel_trigger * st.rmax[col]) atomicAdd(&st.counters[2], 1);
       }
     }
@@ -1509,7 +1589,7 @@ __global__ void k_restart_finish(int64_t n, int B, int nblk, const double* __res
   pdl_entry();
   const ColMap cm(B);
   if (!cm.ok || flag[cm.col] != 1) return;
-  if (blockIdx.x == 0 && cm.k == 0) st.rz[cm.col] = sum_parts(part, nblk, B, cm.col);
+  if (blockIdx.x == 0 && cm.k == 0) st.rz[cm.col] = st.rz2[cm.col] = sum_parts(part, nblk, B, cm.col);
   for (int64_t i = cm.first(); i < n; i += cm.stride()) p[i * B + cm.col] = z[i * B + cm.col];
 }
 

@@ -74,6 +74,11 @@ int launch_update_xr_alpha(int64_t n, const ColState& st, int nb_pq, const doubl
 template <class T>
 void launch_update_p(int64_t n, int B, const ColState& st, const T* z, T* p, int max_blocks,
                      cudaStream_t s);
+// one column, keep = 0: beta from the r.r and r.z partials inside the p update
+template <class T>
+void launch_update_p_beta(int64_t n, const ColState& st, int nb_rr, const double* rr_part, int nb_rz,
+                          const double* rz_part, int maxit, double rel_trigger, const T* z, T* p, int max_blocks,
+                          cudaStream_t s);
 template <class T>
 void launch_copy_cols(int64_t n, int B, const int* flag, const T* src, T* dst, int max_blocks,
                       cudaStream_t s);

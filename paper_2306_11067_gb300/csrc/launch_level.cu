@@ -147,6 +147,16 @@ int launch_update_xr_alpha(int64_t n, const ColState& st, int nb_pq, const doubl
 }
 
 template <class T>
+void launch_update_p_beta(int64_t n, const ColState& st, int nb_rr, const double* rr_part, int nb_rz,
+                          const double* rz_part, int maxit, double rel_trigger, const T* z, T* p, int max_blocks,
+                          cudaStream_t s) {
+  const int g = grid_for(n, 1, max_blocks);
+  klaunch(k_update_p_beta<T>, dim3(g), dim3(kBlock), 0, s, n, st, nb_rr, rr_part, nb_rz, rz_part, maxit, rel_trigger,
+          z, p);
+  LCMG_LAUNCHED();
+}
+
+template <class T>
 void launch_update_p(int64_t n, int B, const ColState& st, const T* z, T* p, int max_blocks,
                      cudaStream_t s) {
   const int g = grid_for(n, B, max_blocks);
@@ -181,7 +191,9 @@ void launch_copy_cols(int64_t n, int B, const int* flag, const T* src, T* dst, i
   template void launch_coarse_solve<T>(int, int, const double*, const T*, T*, cudaStream_t);    \
   template void launch_update_p<T>(int64_t, int, const ColState&, const T*, T*, int,            \
                                    cudaStream_t);                                               \
-  template void launch_copy_cols<T>(int64_t, int, const int*, const T*, T*, int, cudaStream_t);
+  template void launch_copy_cols<T>(int64_t, int, const int*, const T*, T*, int, cudaStream_t);       \
+  template void launch_update_p_beta<T>(int64_t, const ColState&, int, const double*, int, const double*, int, \
+                                        double, const T*, T*, int, cudaStream_t);
 LCMG_INST_T(float)
 LCMG_INST_T(double)
 #undef LCMG_INST_T

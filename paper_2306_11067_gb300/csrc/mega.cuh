@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(kMegaThreads, 1) k_pcg_mega(const MegaArgs<T> 
       } else {
         st.rr[c] = rr;
         st.beta[c] = be;
-        if (go) st.rz[c] = rzn;
+        if (go) st.rz[c] = st.rz2[c] = rzn;
         if (!go) st.active[c] = 0;
         if (stt >= 0) st.status[c] = stt;
         if (pend) st.pending[c] = 1;

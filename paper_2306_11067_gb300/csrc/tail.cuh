@@ -1,22 +1,29 @@
-// The coarse end of the V-cycle in one CTA.
+// The coarse end of the V-cycle in one launch.
 //
 // On the small levels of the hierarchy every V-cycle step is a tiny kernel
 // whose cost is launch latency.  k_vcycle_tail runs the V-cycle of
 // Algorithm 1 on levels k0 .. L-1 (pre-smoothing from zero, residual,
 // restriction, the coarsest direct solve, prolongation, post-smoothing) in
-// a single block of tail_threads<T>() threads; steps are separated by
-// __syncthreads, which orders the block's global-memory writes and reads.
+// one block of tail_threads<T>() threads (CL = false; steps separated by
+// __syncthreads) or in one thread-block cluster of such blocks (CL = true;
+// points strided over the whole cluster, steps separated by cluster
+// barriers, and data written earlier in the launch read with ld.global.cg
+// from L2, so no CTA reads a stale L1 line).  Every thread reaches every
+// barrier: no early return, uniform loop bounds.
 // Input: the restricted residual of level k0; output: z of level k0.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "kernels.cuh"
 
 namespace lcmg {
 
 constexpr int kTailMaxLevels = 16;
-// threads of the tail block: 1024 in FP32; 512 in FP64, whose 25-point
-// stencil rows need more than the 64 registers a 1024-thread block allows
-template <class T>
-__host__ __device__ constexpr int tail_threads() { return sizeof(T) == 8 ? 512 : 1024; }
+// threads of a tail block: one CTA, 1024 in FP32 and 512 in FP64, whose
+// 25-point stencil rows need more than the 64 registers a 1024-thread block
+// allows; in a cluster 512 for both (room for 128 registers, no spills)
+template <class T, bool CL = false>
+__host__ __device__ constexpr int tail_threads() { return (CL || sizeof(T) == 8) ? 512 : 1024; }
 
 template <class T>
 struct TailLevel {
@@ -38,18 +45,35 @@ struct TailArgs {
   const T* lam2T;
 };
 
-template <class T>
-__global__ void __launch_bounds__(tail_threads<T>(), 1) k_vcycle_tail(const TailArgs<T> a) {
+template <class T, bool CL>
+__global__ void __launch_bounds__(tail_threads<T, CL>(), 1) k_vcycle_tail(const TailArgs<T> a) {
   pdl_entry();
-  constexpr int kTailThreads = tail_threads<T>();
+  namespace cg = cooperative_groups;
+  constexpr int kTailThreads = tail_threads<T, CL>();
   const int B = a.B;
-  const int tid = threadIdx.x;
-  const int ppb = kTailThreads / B;
+  const int rank = CL ? (int)cg::this_cluster().block_rank() : 0;
+  const int nctas = CL ? (int)cg::this_cluster().num_blocks() : 1;
+  const int tid = rank * kTailThreads + (int)threadIdx.x;  // thread within the launch
+  const int nthreads = nctas * kTailThreads;
+  const int ppb = nthreads / B;
   const int kk = tid / B;
   const int col = tid - kk * B;
   const bool ok = kk < ppb;
   const T l2 = ok ? a.lam2T[col] : (T)0;
   const int nl = a.nl, nu = a.nu;
+  auto sync = [&]() {
+    if constexpr (CL) {
+      __threadfence();
+      cg::this_cluster().sync();
+    } else {
+      __syncthreads();
+    }
+  };
+  // data written earlier in this launch (rhs below level 0, z, t, res)
+  auto ld = [&](const T* q) -> T {
+    if constexpr (CL) return __ldcg(q);
+    else return *q;
+  };
 
   auto level_loop = [&](const TailLevel<T>& L, auto&& body) {
     if (!ok) return;
@@ -64,35 +88,35 @@ __global__ void __launch_bounds__(tail_threads<T>(), 1) k_vcycle_tail(const Tail
   };
   auto sweep = [&](const TailLevel<T>& L, const T* zin, T* zout) {
     level_loop(L, [&](int64_t pt, int i, int j) {
-      auto v = [&](int64_t q) { return zin[q * B + col]; };
+      auto v = [&](int64_t q) { return ld(zin + q * B + col); };
       const T kz = K_apply(L, pt, i, j, v);
-      zout[pt * B + col] = zin[pt * B + col] + L.dinv[pt * B + col] * (L.rhs[pt * B + col] - kz);
+      zout[pt * B + col] = ld(zin + pt * B + col) + L.dinv[pt * B + col] * (ld(L.rhs + pt * B + col) - kz);
     });
   };
 
   for (int k = 0; k + 1 < nl; ++k) {
     const TailLevel<T> L = a.lev[k];
     level_loop(L, [&](int64_t pt, int i, int j) {
-      const T z1 = L.dinv[pt * B + col] * L.rhs[pt * B + col];
+      const T z1 = L.dinv[pt * B + col] * ld(L.rhs + pt * B + col);
       if (nu < 2) {
         L.z[pt * B + col] = z1;
         return;
       }
-      auto v = [&](int64_t q) { return L.dinv[q * B + col] * L.rhs[q * B + col]; };
-      L.z[pt * B + col] = z1 + L.dinv[pt * B + col] * (L.rhs[pt * B + col] - K_apply(L, pt, i, j, v));
+      auto v = [&](int64_t q) { return L.dinv[q * B + col] * ld(L.rhs + q * B + col); };
+      L.z[pt * B + col] = z1 + L.dinv[pt * B + col] * (ld(L.rhs + pt * B + col) - K_apply(L, pt, i, j, v));
     });
-    __syncthreads();
+    sync();
     for (int s = 2; s < nu; ++s) {
       sweep(L, L.z, L.t);
-      __syncthreads();
-      level_loop(L, [&](int64_t pt, int, int) { L.z[pt * B + col] = L.t[pt * B + col]; });
-      __syncthreads();
+      sync();
+      level_loop(L, [&](int64_t pt, int, int) { L.z[pt * B + col] = ld(L.t + pt * B + col); });
+      sync();
     }
     level_loop(L, [&](int64_t pt, int i, int j) {
-      auto v = [&](int64_t q) { return L.z[q * B + col]; };
-      L.res[pt * B + col] = L.rhs[pt * B + col] - K_apply(L, pt, i, j, v);
+      auto v = [&](int64_t q) { return ld(L.z + q * B + col); };
+      L.res[pt * B + col] = ld(L.rhs + pt * B + col) - K_apply(L, pt, i, j, v);
     });
-    __syncthreads();
+    sync();
     const TailLevel<T> C = a.lev[k + 1];
     level_loop(C, [&](int64_t pc, int I, int J) {
       T acc = 0;
@@ -101,26 +125,26 @@ __global__ void __launch_bounds__(tail_threads<T>(), 1) k_vcycle_tail(const Tail
         const T wb = (T)pw1(bb, J, C.nh);
         for (int aa = 2 * I - 1; aa <= 2 * I + 2; ++aa) {
           if (aa < 0 || aa >= L.nv) continue;
-          acc += wb * (T)pw1(aa, I, C.nv) * L.res[((int64_t)aa + (int64_t)bb * L.nv) * B + col];
+          acc += wb * (T)pw1(aa, I, C.nv) * ld(L.res + ((int64_t)aa + (int64_t)bb * L.nv) * B + col);
         }
       }
       C.rhs[pc * B + col] = acc;
     });
-    __syncthreads();
+    sync();
   }
   {  // coarsest level
     const TailLevel<T> Lc = a.lev[nl - 1];
     const int nc = a.nc;
-    for (int64_t t = tid; t < (int64_t)nc * B; t += kTailThreads) {
+    for (int64_t t = tid; t < (int64_t)nc * B; t += nthreads) {
       const int c = (int)(t % B);
       const int i = (int)(t / B);
       const double* M = a.kinv + ((int64_t)c * nc + i) * nc;
       double s = 0.0;
-      for (int q = 0; q < nc; ++q) s += M[q] * (double)Lc.rhs[(int64_t)q * B + c];
+      for (int q = 0; q < nc; ++q) s += M[q] * (double)ld(Lc.rhs + (int64_t)q * B + c);
       Lc.z[(int64_t)i * B + c] = (T)s;
     }
   }
-  __syncthreads();
+  sync();
   for (int k = nl - 2; k >= 0; --k) {
     const TailLevel<T> L = a.lev[k];
     const TailLevel<T> C = a.lev[k + 1];
@@ -139,20 +163,20 @@ __global__ void __launch_bounds__(tail_threads<T>(), 1) k_vcycle_tail(const Tail
         for (int w2 = 0; w2 < 2; ++w2) {
           const int I = Is[w2];
           if (I < 0 || I >= C.nv) continue;
-          acc += wb * (T)pw1(i, I, C.nv) * C.z[((int64_t)I + (int64_t)J * C.nv) * B + col];
+          acc += wb * (T)pw1(i, I, C.nv) * ld(C.z + ((int64_t)I + (int64_t)J * C.nv) * B + col);
         }
       }
-      L.z[pt * B + col] += acc;
+      L.z[pt * B + col] = ld(L.z + pt * B + col) + acc;
     });
-    __syncthreads();
+    sync();
     if (nu % 2 == 1) {
-      level_loop(L, [&](int64_t pt, int, int) { L.t[pt * B + col] = L.z[pt * B + col]; });
-      __syncthreads();
+      level_loop(L, [&](int64_t pt, int, int) { L.t[pt * B + col] = ld(L.z + pt * B + col); });
+      sync();
     }
     for (int s = 0; s < nu; ++s) {
       if ((nu - s) % 2 == 0) sweep(L, L.z, L.t);
       else sweep(L, L.t, L.z);
-      __syncthreads();
+      sync();
     }
   }
 }

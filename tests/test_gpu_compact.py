@@ -60,15 +60,18 @@ def test_wide_rows_fall_back_to_int32_columns():
 
 
 @pytest.mark.parametrize("precision,bound", [(L.PREC_FP64, 1e-8), (L.PREC_MIXED, 1e-6)])
-def test_alpha_inside_the_update_matches_the_scalar_kernel(precision, bound):
-    """One column: alpha taken by every block of the x/r update (alpha_fuse =
-    1, the default) and by the scalar kernel (0) sum p.q in different orders;
-    both solve to the oracle's solution and report the same status."""
+def test_scalars_inside_the_updates_match_the_scalar_kernels(precision, bound):
+    """One column: alpha and beta taken by every block of the x/r and p
+    updates (alpha_fuse = beta_fuse = 1, the default), alpha only, or both
+    by the scalar kernels, sum in different orders; every form solves to
+    the oracle's solution (reliable updates and restarts included at
+    tol 1e-12) in about the same number of iterations."""
     P = pg.make_problem("ct256", size=48)
     lams = np.array([0.05, 0.5])
     outs = []
-    for af in (1, 0):
-        s = Solver(48, 48, mode=L.MODE_SEQUENTIAL, tol=1e-12, maxit=20000, precision=precision, alpha_fuse=af)
+    for af, bf in ((1, 1), (1, 0), (0, 0)):
+        s = Solver(48, 48, mode=L.MODE_SEQUENTIAL, tol=1e-12, maxit=20000, precision=precision, alpha_fuse=af,
+                   beta_fuse=bf)
         s.set_forward_csr(P.A)
         outs.append(s.solve(lams, P.b[:, 0]))
         s.close()
@@ -80,7 +83,22 @@ def test_alpha_inside_the_update_matches_the_scalar_kernel(precision, bound):
     for j, lam in enumerate(lams):
         x, *_ = krylov.pcg(lambda v: ops.normal_apply(F, Lg, d, lam, v), c, None, mg.VCycle(H, lam), tol=1e-12,
                            maxit=20000)
+        ref_its = int(outs[-1]["iters"][0, j])
         for out in outs:
             assert out["status"][0, j] == 0
             assert np.linalg.norm(out["x"][0, j] - x) <= bound * np.linalg.norm(x)
-        assert abs(int(outs[0]["iters"][0, j]) - int(outs[1]["iters"][0, j])) <= max(3, 0.05 * outs[1]["iters"][0, j])
+            assert abs(int(out["iters"][0, j]) - ref_its) <= max(3, 0.05 * ref_its)
+
+
+@pytest.mark.parametrize("fuse", [0, 1])
+def test_iteration_limit_with_scalars_inside_the_updates(fuse):
+    """The fused beta step takes the iteration-limit decision as the scalar
+    kernel does: status MAXIT after exactly maxit iterations."""
+    P = pg.make_problem("ct256", size=48)
+    s = Solver(48, 48, mode=L.MODE_SEQUENTIAL, tol=1e-14, maxit=7, precision=L.PREC_MIXED, alpha_fuse=fuse,
+               beta_fuse=fuse)
+    s.set_forward_csr(P.A)
+    out = s.solve([1e-3], P.b[:, 0])
+    s.close()
+    assert out["status"][0, 0] == L.MAXIT
+    assert int(out["iters"][0, 0]) == 7

@@ -147,13 +147,14 @@ def test_galerkin_levels_parity(n_v, n_h, levels):
 
 @pytest.mark.parametrize("smoother", [L.SMOOTH_L1_JACOBI, L.SMOOTH_JACOBI])
 @pytest.mark.parametrize("n_v,n_h,levels", [(32, 32, 3), (40, 24, 3), (8, 8, 1)])
-@pytest.mark.parametrize("tail_points", [0, 4096, 100000])
+@pytest.mark.parametrize("tail_points,tail_ctas", [(0, 1), (4096, 1), (100000, 1), (100000, 16)])
 @pytest.mark.parametrize("nu", [1, 2])
-def test_vcycle_parity(smoother, n_v, n_h, levels, tail_points, nu):
+def test_vcycle_parity(smoother, n_v, n_h, levels, tail_points, tail_ctas, nu):
     """tail_points 0: one kernel per level step; 4096: the small levels in one
-    CTA; 100000: every coarse level in one CTA."""
+    CTA; 100000: every coarse level in one CTA, or in a 16-CTA cluster."""
     A = pg.blur_csr(n_v, n_h, pg.gaussian_psf(2, 1.0))
-    s = Solver(n_v, n_h, levels=levels, smoother=smoother, tail_points=tail_points, vfuse=0, nu=nu)
+    s = Solver(n_v, n_h, levels=levels, smoother=smoother, tail_points=tail_points, tail_ctas=tail_ctas, vfuse=0,
+               nu=nu)
     s.set_forward_csr(A)
     d = pg.random_weights(ops.n_edges(n_v, n_h), 9)
     s.set_weights(d)
