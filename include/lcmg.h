@@ -143,7 +143,10 @@ typedef struct {
   int32_t spmv_variant; /* one-column SpMV configuration of both operator passes
                            (unless autotuned): 0 = per-pass default (32 lanes x
                            4 nonzeros for A p, 8 x 8 for the transposed pass);
-                           1 = 32 x 4, 2 = 16 x 8, 3 = 8 x 8                    */
+                           1 = 32 x 4, 2 = 16 x 8, 3 = 8 x 8; with FP32 vectors
+                           also 4 = 8 x 8 compiled for 5 resident blocks per SM
+                           (48 registers), 5 = 8 x 8 for 6 blocks, 6 = 8 lanes
+                           x 4 for 8 blocks (as 3 with FP64 vectors)           */
   int32_t stop_rule;    /* outer loop of Algorithm 2: 0 = stop after three equal
                            selections (Sec. 3.5, default); 1 = stop once
                            ||L x*||_2 decreases from one outer iteration to the
@@ -195,6 +198,8 @@ typedef struct {
                            level strided over the whole cluster and the steps
                            separated by cluster barriers; combines with the
                            two-kernels-per-level V-cycle (vfuse)            */
+  int32_t spmv_variant_at; /* configuration of the transposed pass alone (0 =
+                           as spmv_variant; 1..6 as there)                  */
 } lcmg_params;
 
 typedef struct lcmg_ctx lcmg_ctx;

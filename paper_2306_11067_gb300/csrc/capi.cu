@@ -157,6 +157,7 @@ struct lcmg_ctx {
   bool am_ok = false;                // am and pm hold the AMG hierarchy of the current D
   DevBuf<double> pm_GLc;             // dense G_L^c of the coarsest AMG level
   DevBuf<double> pm_V, pm_Z, pm_w, pm_r, pm_h, pm_part, pm_y;
+  DevBuf<double> pm_cin, pm_cout;    // input and output of the captured cycle
   int rv = 0, rh = 0;
   DevBuf<double> psf64;
   DevBuf<float> psf32;
@@ -286,7 +287,8 @@ static void check_params(const lcmg_params& p) {
   if (p.vfuse < 0 || p.vfuse > 2) throw ArgError("vfuse must be 0, 1 or 2");
   if (p.keep_direction != 0 && p.keep_direction != 1) throw ArgError("keep_direction must be 0 or 1");
   if (p.autotune != 0 && p.autotune != 1) throw ArgError("autotune must be 0 or 1");
-  if (p.spmv_variant < 0 || p.spmv_variant > 3) throw ArgError("spmv_variant must be 0..3");
+  if (p.spmv_variant < 0 || p.spmv_variant > 6) throw ArgError("spmv_variant must be 0..6");
+  if (p.spmv_variant_at < 0 || p.spmv_variant_at > 6) throw ArgError("spmv_variant_at must be 0..6");
   if (p.stop_rule != 0 && p.stop_rule != 1) throw ArgError("stop_rule must be 0 or 1");
   if (p.precond != 0 && p.precond != 1) throw ArgError("precond must be 0 or 1");
   if (p.gmres_restart < 1 || p.gmres_restart > 2000) throw ArgError("gmres_restart must be 1..2000");
@@ -454,6 +456,7 @@ struct Batch {
 
   Batch(lcmg_ctx& c_, int B_) : c(c_), B(B_), s(c_.stream), nlev((int)c_.lev.size()) {
     var_a = var_at = c.prm.spmv_variant;
+    if (c.prm.spmv_variant_at) var_at = c.prm.spmv_variant_at;
     auto it = c.tuned.find(tune_key());
     if (c.prm.autotune && it != c.tuned.end()) {
       var_a = it->second.var_a;
@@ -820,7 +823,7 @@ struct Batch {
       }
       var_a = t.var_a;
       best = 1e30f;
-      for (int v = 1; v <= 3; ++v) {
+      for (int v = 1; v <= 6; ++v) {
         var_at = v;
         const float ms = time(apply);
         if (ms < best) { best = ms; t.var_at = v; }
@@ -1494,6 +1497,47 @@ struct PaperMG {
     c.pm_part.need((size_t)(m + 1) * 128);
     c.pm_y.need(m);
     setup(lam);
+    // the cycle as one CUDA graph (params.graphs): it reads lambda^2, the
+    // level diagonals and the coarsest inverse from device buffers that
+    // setup() has filled, and runs from pm_cin into pm_cout
+    cudaGraphExec_t gexec = nullptr;
+    int64_t per_cycle = 0;
+    if (c.prm.graphs) {
+      c.pm_cin.need(n);
+      c.pm_cout.need(n);
+      cudaGraph_t graph = nullptr;
+      const int64_t l0 = launch_counter();
+      LCMG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      try {
+        cycle(0, c.pm_cin.p, c.pm_cout.p);
+      } catch (...) {
+        cudaStreamEndCapture(s, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+      }
+      per_cycle = launch_counter() - l0;
+      launch_counter() = l0;  // captured, not executed
+      LCMG_CUDA(cudaStreamEndCapture(s, &graph));
+      const cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      LCMG_CUDA(ie);
+    }
+    struct ExecGuard {
+      cudaGraphExec_t e;
+      ~ExecGuard() {
+        if (e) cudaGraphExecDestroy(e);
+      }
+    } guard{gexec};
+    auto apply_cycle = [&](const double* in, double* out) {
+      if (!gexec) {
+        cycle(0, in, out);
+        return;
+      }
+      LCMG_CUDA(cudaMemcpyAsync(c.pm_cin.p, in, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      LCMG_CUDA(cudaGraphLaunch(gexec, s));
+      launch_counter() += per_cycle;
+      LCMG_CUDA(cudaMemcpyAsync(out, c.pm_cout.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    };
     cudaEvent_t e0, e1;
     LCMG_CUDA(cudaEventCreate(&e0));
     LCMG_CUDA(cudaEventCreate(&e1));
@@ -1529,7 +1573,7 @@ struct PaperMG {
       for (int j = 0; j < mm; ++j) {
         double* vj = c.pm_V.p + (int64_t)j * n;
         double* zj = c.pm_Z.p + (int64_t)j * n;
-        cycle(0, vj, zj);
+        apply_cycle(vj, zj);
         apply<0>(0, zj, nullptr, c.pm_w.p, c.pmw[0].ppq.p);
         ++it;
         cgs_pass(j + 1, c.pm_w.p, c.pm_h.p);
@@ -1970,6 +2014,7 @@ void lcmg_default_params(lcmg_params* p) {
   p->alpha_fuse = 1;
   p->beta_fuse = 1;
   p->tail_ctas = 1;
+  p->spmv_variant_at = 0;
 }
 
 const char* lcmg_last_error(void) { return lcmg::g_err.c_str(); }

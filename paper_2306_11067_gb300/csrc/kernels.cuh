@@ -418,7 +418,10 @@ struct SpmmArgs {
   int64_t nck;
   int* err;               // set to 1 when a staging wait gives up
   int variant;            // one-column kernel (k_spmv1): 0 = the pass's default,
-                          // 1 = 32 lanes x 4, 2 = 16 lanes x 8, 3 = 8 lanes x 8
+                          // 1 = 32 lanes x 4, 2 = 16 lanes x 8, 3 = 8 lanes x 8;
+                          // FP32 vectors only (else as 3): 4 = 8 x 8 with at
+                          // least 5 blocks per SM, 5 = 8 x 8 with 6, 6 = 8 x 4
+                          // with 8
   // one-column kernel: column of nonzero k of row r = rbase[r] + c16[k]
   // (null: ci), 6 instead of 8 bytes per FP32 nonzero
   const uint16_t* c16;
@@ -541,8 +544,13 @@ __global__ void __launch_bounds__(kBlock)
 // C16: column indices as 16-bit offsets from a per-row base (a.c16,
 // a.rbase), when every row's column span is below 65,536.
 // ---------------------------------------------------------------------------
-template <class V, class T, class TO, int MODE, int U, int LPR, bool PF, bool C16>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? (LPR == 32 ? 8 : 4) : (LPR == 32 ? 5 : 3))
+// MINB: resident blocks per SM the register allocation must allow (the
+// launch bound; more blocks = fewer registers per thread).
+template <class T, int LPR>
+constexpr int spmv1_minb() { return sizeof(T) == 4 ? (LPR == 32 ? 8 : 4) : (LPR == 32 ? 5 : 3); }
+
+template <class V, class T, class TO, int MODE, int U, int LPR, bool PF, bool C16, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB)
     k_spmv1(SpmmArgs a, const V* __restrict__ va, const T* __restrict__ X, TO* __restrict__ Y,
             FineOp<T> fop, const T* __restrict__ P, const T* __restrict__ C,
             const double* __restrict__ lam2, const double* __restrict__ bvec,

@@ -56,11 +56,11 @@ static int resident_grid(K kern, int threads, size_t smem) {
 
 // One column: k_spmv1 with U nonzeros per lane and LPR lanes per row;
 // 16-bit column offsets (C16) for the transposed operator pass when present.
-template <class V, class T, class TO, int MODE, int U, int LPR, bool C16>
+template <class V, class T, class TO, int MODE, int U, int LPR, bool C16, int MINB>
 static int run1c(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop, const T* P,
                  const T* C, const double* lam2, const double* bvec, double* part, int max_blocks,
                  cudaStream_t s, const ScalarFold* fold) {
-  auto k = k_spmv1<V, T, TO, MODE, U, LPR, true, C16>;
+  auto k = k_spmv1<V, T, TO, MODE, U, LPR, true, C16, MINB>;
   int64_t blocks = resident_grid(k, kBlock, 0);
   const int64_t need = (a.rows * LPR + kBlock - 1) / kBlock;
   if (blocks > need) blocks = need;
@@ -72,7 +72,7 @@ static int run1c(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp
   return (int)blocks;
 }
 
-template <class V, class T, class TO, int MODE, int U, int LPR>
+template <class V, class T, class TO, int MODE, int U, int LPR, int MINB = spmv1_minb<T, LPR>()>
 static int run1v(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop, const T* P,
                  const T* C, const double* lam2, const double* bvec, double* part, int max_blocks,
                  cudaStream_t s, const ScalarFold* fold) {
@@ -81,9 +81,10 @@ static int run1v(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp
   // cap) loses (31.1 -> 38.3 us), so it keeps int32 columns
   if constexpr (MODE == 1) {
     if (a.c16 != nullptr)
-      return run1c<V, T, TO, MODE, U, LPR, true>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
+      return run1c<V, T, TO, MODE, U, LPR, true, MINB>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s,
+                                                       fold);
   }
-  return run1c<V, T, TO, MODE, U, LPR, false>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
+  return run1c<V, T, TO, MODE, U, LPR, false, MINB>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
 }
 
 // The pass's configuration: a.variant, or by default (measured on GB300,
@@ -96,7 +97,12 @@ static int run1(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<
   constexpr bool kT = (MODE == 1 || MODE == 3);
   const int v = a.variant != 0 ? a.variant : (kT ? 3 : 1);
   if (v == 2) return run1v<V, T, TO, MODE, 8, 16>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
-  if (v == 3) return run1v<V, T, TO, MODE, 8, 8>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
+  if constexpr (std::is_same<T, float>::value) {  // register-bounded forms of the 8-lane layout
+    if (v == 4) return run1v<V, T, TO, MODE, 8, 8, 5>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
+    if (v == 5) return run1v<V, T, TO, MODE, 8, 8, 6>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
+    if (v == 6) return run1v<V, T, TO, MODE, 4, 8, 8>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
+  }
+  if (v >= 3) return run1v<V, T, TO, MODE, 8, 8>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
   return run1v<V, T, TO, MODE, 4, 32>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
 }
 

@@ -48,7 +48,8 @@ class lcmg_params(C.Structure):
                 ("stop_rule", C.c_int32),
                 ("precond", C.c_int32), ("gmres_restart", C.c_int32),
                 ("coarsening", C.c_int32), ("amg_coarse_max", C.c_int32), ("compact_cols", C.c_int32),
-                ("alpha_fuse", C.c_int32), ("beta_fuse", C.c_int32), ("tail_ctas", C.c_int32)]
+                ("alpha_fuse", C.c_int32), ("beta_fuse", C.c_int32), ("tail_ctas", C.c_int32),
+                ("spmv_variant_at", C.c_int32)]
 
 
 class lcmg_stats(C.Structure):

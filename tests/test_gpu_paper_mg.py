@@ -150,3 +150,20 @@ def test_paper_method_argument_errors():
     with pytest.raises(LcmgError):
         s.solve([0.1], Q.b[:, 0])
     s.close()
+
+
+@pytest.mark.parametrize("coarsening", [0, 1])
+def test_paper_cycle_graph_is_bitwise_the_launched_cycle(coarsening):
+    """With params.graphs the FGMRES loop replays the cycle as one captured
+    CUDA graph: the same kernels in the same order, so the same bits."""
+    P, A = _problem("ct")
+    d = pg.random_weights(ops.n_edges(32, 32), 3, d_min=0.05)
+    outs = []
+    for graphs in (1, 0):
+        s = Solver(32, 32, levels=3, precond=1, coarsening=coarsening, graphs=graphs, tol=1e-10, maxit=500)
+        s.set_forward_csr(A)
+        s.set_weights(d)
+        outs.append(s.solve([0.05, 0.5], P.b[:, 0]))
+        s.close()
+    for key in ("x", "rho", "eta", "iters", "status"):
+        assert np.array_equal(outs[0][key], outs[1][key]), key
