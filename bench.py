@@ -38,6 +38,7 @@ WORKLOAD_DESC = ("ct256: 256x256 parallel-beam CT, 180 angles x 363 bins exact r
                  "logspace(-4, 0), Algorithm 2 (max 15 outer iterations, three-equal stop, "
                  "largest-lambda-first warm-start chain), rel-res 1e-6, 5-level V(1,1) l1-Jacobi")
 METRIC = "lambda-solves/s at rel-res 1e-6"
+NU = 1  # V(nu, nu) sweeps: the library's default, and what the oracle arms run
 KERNEL_SRC = os.path.join(ROOT, "paper_2306_11067_gb300", "csrc", "kernels.cuh")
 LAUNCH_SRC = os.path.join(ROOT, "paper_2306_11067_gb300", "csrc", "launch_spmm.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_spmv1_ct256_traffic.txt")
@@ -77,7 +78,7 @@ def oracle_sample(budget_s: float, n_solves_max: int = 2) -> dict:
     from oracle import outer
     from oracle import operators as ops
     P = pg.make_problem(WORKLOAD)
-    prm = outer.Params(tol=1e-6, maxit=10000)
+    prm = outer.Params(tol=1e-6, maxit=10000, nu=NU)
     t0 = time.perf_counter()
     S = outer.setup(P)
     c = ops.rhs(S.F, P.b[:, 0])
@@ -364,7 +365,7 @@ def main():
     max_outer = P.meta.get("max_outer", 15)
 
     def make_solver(precision, timing):
-        s = L.Solver(P.n_v, P.n_h, device=local, stream=stream, precision=precision, mode=mode,
+        s = L.Solver(P.n_v, P.n_h, device=local, stream=stream, precision=precision, mode=mode, nu=NU,
                      tol=1e-6, maxit=10000, timing=timing)
         s.set_forward_csr(P.A)
         return s

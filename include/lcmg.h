@@ -142,7 +142,8 @@ typedef struct {
                            defaults (default)                                   */
   int32_t spmv_variant; /* one-column SpMV configuration of both operator passes
                            (unless autotuned): 0 = per-pass default (32 lanes x
-                           4 nonzeros for A p, 8 x 8 for the transposed pass);
+                           4 nonzeros for A p, 8 x 8 for the transposed pass,
+                           as variant 4 with FP32 vectors);
                            1 = 32 x 4, 2 = 16 x 8, 3 = 8 x 8; with FP32 vectors
                            also 4 = 8 x 8 compiled for 5 resident blocks per SM
                            (48 registers), 5 = 8 x 8 for 6 blocks, 6 = 8 lanes

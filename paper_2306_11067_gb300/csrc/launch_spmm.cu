@@ -89,13 +89,16 @@ static int run1v(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp
 
 // The pass's configuration: a.variant, or by default (measured on GB300,
 // 256^2 CT) 32 lanes x 4 for y = A p and 8 lanes x 8 for the transposed
-// pass, whose fine-level epilogue runs on one lane per row.
+// pass, whose fine-level epilogue runs on one lane per row (with FP32
+// vectors compiled for 5 resident blocks per SM).
 template <class V, class T, class TO, int MODE>
 static int run1(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop, const T* P,
                 const T* C, const double* lam2, const double* bvec, double* part, int max_blocks,
                 cudaStream_t s, const ScalarFold* fold) {
   constexpr bool kT = (MODE == 1 || MODE == 3);
-  const int v = a.variant != 0 ? a.variant : (kT ? 3 : 1);
+  // transposed pass with FP32 vectors: 8 x 8 bounded to 5 blocks per SM
+  // (48 registers; 32.8 vs 35.7-36.2 us per pass on GB300, same sums)
+  const int v = a.variant != 0 ? a.variant : (kT ? (std::is_same<T, float>::value ? 4 : 3) : 1);
   if (v == 2) return run1v<V, T, TO, MODE, 8, 16>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
   if constexpr (std::is_same<T, float>::value) {  // register-bounded forms of the 8-lane layout
     if (v == 4) return run1v<V, T, TO, MODE, 8, 8, 5>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);

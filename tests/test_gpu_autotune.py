@@ -61,7 +61,7 @@ def test_autotuned_solves_reach_oracle_and_keep_their_choice(nlam):
     levels = L.lcmg_num_levels(s.ctx)
     s.close()
     if nlam == 1:
-        assert st1["tuned_spmv_a"] in (1, 2, 3) and st1["tuned_spmv_at"] in (1, 2, 3)
+        assert st1["tuned_spmv_a"] in (1, 2, 3) and st1["tuned_spmv_at"] in (1, 2, 3, 4, 5, 6)
     else:
         assert (st1["tuned_spmv_a"], st1["tuned_spmv_at"]) == (0, 0)
     assert st1["tuned_vfuse"] in (0, 1)
