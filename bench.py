@@ -61,6 +61,10 @@ def parse():
                     help="time the lambda sweep of one outer iteration with the default preconditioner (FP64 and "
                          "mixed) and the paper's own (geometric and classical AMG interpolation, FP64) at 64^2, "
                          "128^2, 256^2; one JSON line per arm, no bench line")
+    ap.add_argument("--compare-algorithm2", action="store_true",
+                    help="one full Algorithm 2 run of the workload per solver arm (default preconditioner mixed "
+                         "and FP64, the paper's method with geometric and classical AMG interpolation): "
+                         "lambda-solves/s and the selected lambda indices; one JSON line per arm")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiler workload: one lambda of the workload, this many PCG iterations, no JSON line")
     return ap.parse_args()
@@ -323,6 +327,33 @@ def compare_precond():
             s.close()
 
 
+def compare_algorithm2():
+    """Algorithm 2 end to end on the workload (tol 1e-6, the paper's chain)
+    with each solver arm: one untimed run, then one timed run (wall clock,
+    the weights, hierarchies and every solve included)."""
+    import problemgen as pg
+    from paper_2306_11067_gb300 import lcmg as L
+    P = pg.make_problem(WORKLOAD)
+    b = P.b[:, 0]
+    max_outer = P.meta.get("max_outer", 15)
+    arms = [("pcg-default-mixed", dict(precond=0, precision=L.PREC_MIXED)),
+            ("pcg-default-fp64", dict(precond=0, precision=L.PREC_FP64)),
+            ("paper-geometric", dict(precond=1, precision=L.PREC_FP64)),
+            ("paper-amg", dict(precond=1, coarsening=1, precision=L.PREC_FP64))]
+    for name, kw in arms:
+        s = L.Solver(P.n_v, P.n_h, mode=L.MODE_SEQUENTIAL, tol=1e-6, maxit=10000, nu=NU, **kw)
+        s.set_forward_csr(P.A)
+        s.lcurve_run(P.lambdas, b, max_outer=max_outer)
+        t0 = time.perf_counter()
+        r = s.lcurve_run(P.lambdas, b, max_outer=max_outer)
+        dt = time.perf_counter() - t0
+        s.close()
+        print(json.dumps({"arm": name, "workload": WORKLOAD, "seconds": round(dt, 3),
+                          "lambda_solves": int(r["n_converged"]), "lambda_solves_per_s": round(r["n_converged"] / dt, 3),
+                          "outer_iterations": len(r["history"]), "selected_lambda_indices": [int(h) for h in r["history"]]}),
+              flush=True)
+
+
 # ---------------------------------------------------------------------------
 def main():
     args = parse()
@@ -339,6 +370,8 @@ def main():
         return profile_workload(args)
     if args.compare_precond:
         return compare_precond()
+    if args.compare_algorithm2:
+        return compare_algorithm2()
     if args.serve_only:
         print(json.dumps(serving_leg(int(os.environ.get("LOCAL_RANK", "0")))))
         return

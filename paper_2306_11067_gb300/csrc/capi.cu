@@ -1117,23 +1117,19 @@ static double interp_w(int a, int I, int nc) {
   return 0.0;
 }
 
-// A P for P = P_h (x) P_v from the nv/2 x nh/2 grid to the nv x nh grid;
-// each row is accumulated in the order of its nonzeros, then sorted
+// A P for P = P_h (x) P_v from the nv/2 x nh/2 grid to the nv x nh grid,
+// by the threaded host product with the explicit P (a fine pixel's row
+// holds w_j * w_i for its 2 x 2 coarse parents): every nonzero of A adds to
+// a coarse column at most once, in the order of A's nonzeros, whatever the
+// thread count
 static HostCsr times_p(const HostCsr& A, int nv, int nh) {
   const int nvc = nv / 2, nhc = nh / 2;
-  HostCsr Bm;
-  Bm.rows = A.rows;
-  Bm.cols = (int64_t)nvc * nhc;
-  Bm.rp.assign(A.rows + 1, 0);
-  std::vector<double> acc(Bm.cols, 0.0);
-  std::vector<int64_t> mark(Bm.cols, -1);
-  std::vector<int32_t> touched;
-  for (int64_t r = 0; r < A.rows; ++r) {
-    touched.clear();
-    for (int64_t k = A.rp[r]; k < A.rp[r + 1]; ++k) {
-      const int c = A.ci[k];
-      const double v = A.v[k];
-      const int j = c / nv, i = c - j * nv;
+  HostCsr P;
+  P.rows = (int64_t)nv * nh;
+  P.cols = (int64_t)nvc * nhc;
+  P.rp.assign(P.rows + 1, 0);
+  for (int j = 0; j < nh; ++j)
+    for (int i = 0; i < nv; ++i) {
       const int Is[2] = {i >> 1, (i & 1) ? (i >> 1) + 1 : (i >> 1) - 1};
       const int Js[2] = {j >> 1, (j & 1) ? (j >> 1) + 1 : (j >> 1) - 1};
       for (int u = 0; u < 2; ++u) {
@@ -1143,26 +1139,14 @@ static HostCsr times_p(const HostCsr& A, int nv, int nh) {
         for (int t = 0; t < 2; ++t) {
           const int I = Is[t];
           if (I < 0 || I >= nvc) continue;
-          const int32_t col = I + J * nvc;
-          if (mark[col] != r) {
-            mark[col] = r;
-            acc[col] = 0.0;
-            touched.push_back(col);
-          }
-          acc[col] += v * (wj * interp_w(i, I, nvc));
+          P.ci.push_back(I + J * nvc);
+          P.v.push_back(wj * interp_w(i, I, nvc));
         }
       }
+      P.rp[(int64_t)i + (int64_t)j * nv + 1] = (int64_t)P.ci.size();
     }
-    std::sort(touched.begin(), touched.end());
-    for (int32_t col : touched) {
-      Bm.ci.push_back(col);
-      Bm.v.push_back(acc[col]);
-    }
-    Bm.rp[r + 1] = (int64_t)Bm.ci.size();
-  }
-  return Bm;
+  return amg::spgemm(A, P);
 }
-
 
 // host copy of the CSR forward operator A (values in FP64)
 static HostCsr host_forward(lcmg_ctx& c) {

@@ -157,6 +157,25 @@ HostCsr interpolation(const HostCsr& K, const Strength& S, const std::vector<int
   return P;
 }
 
+// threads for a host pass over `work` nonzeros (1 below a million)
+static int host_threads(int64_t work) {
+  if (work < (int64_t)1 << 20) return 1;
+  return (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+}
+
+// row blocks balanced by nonzeros: cut[0] = 0 <= ... <= cut[nt] = rows
+static std::vector<int64_t> row_cuts(const HostCsr& A, int nt) {
+  std::vector<int64_t> cut(nt + 1);
+  const int64_t work = (int64_t)A.ci.size();
+  for (int t = 0; t <= nt; ++t) {
+    const int64_t target = work * t / nt;
+    cut[t] = std::min<int64_t>(std::lower_bound(A.rp.begin(), A.rp.end(), target) - A.rp.begin(), A.rows);
+  }
+  cut[0] = 0;
+  cut[nt] = A.rows;
+  return cut;
+}
+
 // rows [r0, r1) of A B into ci / v, with the entry count of each row
 static void spgemm_rows(const HostCsr& A, const HostCsr& B, int64_t r0, int64_t r1, std::vector<int32_t>& ci,
                         std::vector<double>& v, int64_t* count) {
@@ -197,17 +216,8 @@ HostCsr spgemm(const HostCsr& A, const HostCsr& B) {
   C.rp.assign(A.rows + 1, 0);
   // contiguous row blocks on up to 16 threads (each row is computed the
   // same way whatever the split, so the result does not depend on it)
-  const int64_t work = (int64_t)A.ci.size();
-  int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
-  if (work < (int64_t)1 << 20) nt = 1;
-  std::vector<int64_t> cut(nt + 1);
-  for (int t = 0; t <= nt; ++t) {  // balance by nonzeros of A
-    const int64_t target = work * t / nt;
-    cut[t] = std::lower_bound(A.rp.begin(), A.rp.end(), target) - A.rp.begin();
-    cut[t] = std::min<int64_t>(cut[t], A.rows);
-  }
-  cut[0] = 0;
-  cut[nt] = A.rows;
+  const int nt = host_threads((int64_t)A.ci.size());
+  const std::vector<int64_t> cut = row_cuts(A, nt);
   std::vector<std::vector<int32_t>> ci(nt);
   std::vector<std::vector<double>> v(nt);
   std::vector<int64_t> count(A.rows, 0);
@@ -227,22 +237,52 @@ HostCsr spgemm(const HostCsr& A, const HostCsr& B) {
   return C;
 }
 
+// Stable transpose (entries of a column in increasing row order): each
+// thread counts the columns of its row block, the per-thread counts give
+// every (thread, column) its first slot, and each thread scatters its rows
+// in order, so the result does not depend on the thread count.
 HostCsr transpose(const HostCsr& A) {
   HostCsr T;
   T.rows = A.cols;
   T.cols = A.rows;
   T.rp.assign(A.cols + 1, 0);
-  for (int32_t c : A.ci) T.rp[c + 1]++;
-  for (int64_t i = 0; i < A.cols; ++i) T.rp[i + 1] += T.rp[i];
   T.ci.resize(A.ci.size());
   T.v.resize(A.v.size());
-  std::vector<int64_t> pos(T.rp.begin(), T.rp.end() - 1);
-  for (int64_t r = 0; r < A.rows; ++r)
-    for (int64_t k = A.rp[r]; k < A.rp[r + 1]; ++k) {
-      const int64_t d = pos[A.ci[k]]++;
-      T.ci[d] = (int32_t)r;
-      T.v[d] = A.v[k];
+  // per-thread column counts: at most 2^26 entries in all
+  const int nt = (int)std::max<int64_t>(1, std::min<int64_t>(host_threads((int64_t)A.ci.size()),
+                                                             ((int64_t)1 << 26) / std::max<int64_t>(A.cols, 1)));
+  const std::vector<int64_t> cut = row_cuts(A, nt);
+  std::vector<std::vector<int64_t>> cnt(nt, std::vector<int64_t>(A.cols, 0));
+  auto count = [&](int t) {
+    for (int64_t k = A.rp[cut[t]]; k < A.rp[cut[t + 1]]; ++k) cnt[t][A.ci[k]]++;
+  };
+  auto scatter = [&](int t) {
+    std::vector<int64_t>& pos = cnt[t];  // first slot of (t, column)
+    for (int64_t r = cut[t]; r < cut[t + 1]; ++r)
+      for (int64_t k = A.rp[r]; k < A.rp[r + 1]; ++k) {
+        const int64_t d = pos[A.ci[k]]++;
+        T.ci[d] = (int32_t)r;
+        T.v[d] = A.v[k];
+      }
+  };
+  auto run = [&](auto&& fn) {
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(fn, t);
+    fn(0);
+    for (auto& th : pool) th.join();
+  };
+  run(count);
+  int64_t off = 0;
+  for (int64_t c = 0; c < A.cols; ++c) {
+    T.rp[c] = off;
+    for (int t = 0; t < nt; ++t) {
+      const int64_t n = cnt[t][c];
+      cnt[t][c] = off;
+      off += n;
     }
+  }
+  T.rp[A.cols] = off;
+  run(scatter);
   return T;
 }
 
