@@ -67,6 +67,9 @@ def parse():
                          "lambda-solves/s and the selected lambda indices; one JSON line per arm")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiler workload: one lambda of the workload, this many PCG iterations, no JSON line")
+    ap.add_argument("--profile-precond", type=int, default=0, choices=[0, 1, 2],
+                    help="profiler workload's solver: 0 the default PCG (mixed), 1 the paper's method with "
+                         "geometric P, 2 with classical AMG (FP64; --profile-iters FGMRES steps)")
     return ap.parse_args()
 
 
@@ -283,8 +286,10 @@ def profile_workload(args):
     import problemgen as pg
     from paper_2306_11067_gb300 import lcmg as L
     P = pg.make_problem(WORKLOAD)
-    s = L.Solver(P.n_v, P.n_h, precision=L.PREC_MIXED, mode=L.MODE_SEQUENTIAL, tol=1e-30,
-                 maxit=args.profile_iters)
+    kw = {0: dict(precision=L.PREC_MIXED),
+          1: dict(precision=L.PREC_FP64, precond=1),
+          2: dict(precision=L.PREC_FP64, precond=1, coarsening=1)}[args.profile_precond]
+    s = L.Solver(P.n_v, P.n_h, mode=L.MODE_SEQUENTIAL, tol=1e-30, maxit=args.profile_iters, **kw)
     s.set_forward_csr(P.A)
     lam = P.lambdas[len(P.lambdas) // 2: len(P.lambdas) // 2 + 1]
     s.solve(lam, P.b[:, 0])

@@ -173,7 +173,7 @@ typedef struct {
   int32_t amg_coarse_max; /* classical AMG: coarsen while a level has more
                            points than this (2..2048; 256); the last level is
                            solved densely                                   */
-  int32_t compact_cols; /* one-column transposed pass (q = A^T y + ...): 1 = read
+  int32_t compact_cols; /* one-column transposed pass (8-lane layout): 1 = read
                            column indices as 16-bit offsets from a per-row base
                            (6 instead of 8 bytes per FP32 nonzero; built by
                            set_forward_csr when every row of A and A^T spans

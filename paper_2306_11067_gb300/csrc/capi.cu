@@ -1336,6 +1336,7 @@ struct PaperMG {
     const FineOp<double> f = fop();
     if (k == 0) {
       SpmmArgs a = csr_args(c, false, 1), at = csr_args(c, true, 1);
+      at.variant = 3;  // the transposed pass in the 8-lane layout, as on the default path
       if (c.vdtype == 1) {
         launch_spmm<double, double, double, 0>(a, c.v64.p, x, y, f, nullptr, nullptr, nullptr, nullptr, nullptr, c.maxblk, s);
         launch_spmm<double, double, double, 0>(at, c.vT64.p, y, t, f, nullptr, nullptr, nullptr, nullptr, nullptr, c.maxblk, s);

@@ -169,6 +169,11 @@ struct CoarseOp {
   __device__ __forceinline__ T apply_off(int64_t p, int i, int j, T lam2, F v) const {
     T k[28];
     coefs(p, lam2, k);
+    return apply_k(k, i, j, v);
+  }
+  // the same with the coefficients k of the point already loaded (coefs)
+  template <class F>
+  __device__ __forceinline__ T apply_k(const T (&k)[28], int i, int j, F v) const {
     T acc = 0;
     if (i >= 2 && i + 2 < nv && j >= 2 && j + 2 < nh) {
 #pragma unroll

@@ -58,11 +58,11 @@ int launch_vdown(const LevelView<T>& L, int B, const T* lam2, const T* dinv, con
   const int ntx = (L.nv / 2 + kVTile - 1) / kVTile, nty = (L.nh / 2 + kVTile - 1) / kVTile;
   const dim3 grid((unsigned)(ntx * nty), (unsigned)B);
   if (L.fine) {
-    if (nu == 1) klaunch(k_vdown<FineOp<T>, T, 1>, grid, dim3(vtile_threads<FineOp<T>, T>()), 0, s, L.fine_op(), B, lam2, dinv, r, zpre, rc, ntx);
-    else klaunch(k_vdown<FineOp<T>, T, 2>, grid, dim3(vtile_threads<FineOp<T>, T>()), 0, s, L.fine_op(), B, lam2, dinv, r, zpre, rc, ntx);
+    if (nu == 1) klaunch(k_vdown<FineOp<T>, T, 1>, grid, dim3(vtile_threads<FineOp<T>, T, 1>()), 0, s, L.fine_op(), B, lam2, dinv, r, zpre, rc, ntx);
+    else klaunch(k_vdown<FineOp<T>, T, 2>, grid, dim3(vtile_threads<FineOp<T>, T, 2>()), 0, s, L.fine_op(), B, lam2, dinv, r, zpre, rc, ntx);
   } else {
-    if (nu == 1) klaunch(k_vdown<CoarseOp<T>, T, 1>, grid, dim3(vtile_threads<CoarseOp<T>, T>()), 0, s, L.coarse_op(), B, lam2, dinv, r, zpre, rc, ntx);
-    else klaunch(k_vdown<CoarseOp<T>, T, 2>, grid, dim3(vtile_threads<CoarseOp<T>, T>()), 0, s, L.coarse_op(), B, lam2, dinv, r, zpre, rc, ntx);
+    if (nu == 1) klaunch(k_vdown<CoarseOp<T>, T, 1>, grid, dim3(vtile_threads<CoarseOp<T>, T, 1>()), 0, s, L.coarse_op(), B, lam2, dinv, r, zpre, rc, ntx);
+    else klaunch(k_vdown<CoarseOp<T>, T, 2>, grid, dim3(vtile_threads<CoarseOp<T>, T, 2>()), 0, s, L.coarse_op(), B, lam2, dinv, r, zpre, rc, ntx);
   }
   LCMG_LAUNCHED();
   return ntx * nty;
@@ -74,11 +74,11 @@ int launch_vup(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const
   const int ntx = (L.nv / 2 + kVTile - 1) / kVTile, nty = (L.nh / 2 + kVTile - 1) / kVTile;
   const dim3 grid((unsigned)(ntx * nty), (unsigned)B);
   if (L.fine) {
-    if (nu == 1) klaunch(k_vup<FineOp<T>, T, 1>, grid, dim3(vtile_threads<FineOp<T>, T>()), 0, s, L.fine_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
-    else klaunch(k_vup<FineOp<T>, T, 2>, grid, dim3(vtile_threads<FineOp<T>, T>()), 0, s, L.fine_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
+    if (nu == 1) klaunch(k_vup<FineOp<T>, T, 1>, grid, dim3(vtile_threads<FineOp<T>, T, 1>()), 0, s, L.fine_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
+    else klaunch(k_vup<FineOp<T>, T, 2>, grid, dim3(vtile_threads<FineOp<T>, T, 2>()), 0, s, L.fine_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
   } else {
-    if (nu == 1) klaunch(k_vup<CoarseOp<T>, T, 1>, grid, dim3(vtile_threads<CoarseOp<T>, T>()), 0, s, L.coarse_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
-    else klaunch(k_vup<CoarseOp<T>, T, 2>, grid, dim3(vtile_threads<CoarseOp<T>, T>()), 0, s, L.coarse_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
+    if (nu == 1) klaunch(k_vup<CoarseOp<T>, T, 1>, grid, dim3(vtile_threads<CoarseOp<T>, T, 1>()), 0, s, L.coarse_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
+    else klaunch(k_vup<CoarseOp<T>, T, 2>, grid, dim3(vtile_threads<CoarseOp<T>, T, 2>()), 0, s, L.coarse_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
   }
   LCMG_LAUNCHED();
   return ntx * nty;

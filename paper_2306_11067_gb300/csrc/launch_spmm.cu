@@ -55,7 +55,7 @@ static int resident_grid(K kern, int threads, size_t smem) {
 }
 
 // One column: k_spmv1 with U nonzeros per lane and LPR lanes per row;
-// 16-bit column offsets (C16) for the transposed operator pass when present.
+// 16-bit column offsets (C16) in the 8-lane layout when present.
 template <class V, class T, class TO, int MODE, int U, int LPR, bool C16, int MINB>
 static int run1c(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop, const T* P,
                  const T* C, const double* lam2, const double* bvec, double* part, int max_blocks,
@@ -76,10 +76,11 @@ template <class V, class T, class TO, int MODE, int U, int LPR, int MINB = spmv1
 static int run1v(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop, const T* P,
                  const T* C, const double* lam2, const double* bvec, double* part, int max_blocks,
                  cudaStream_t s, const ScalarFold* fold) {
-  // measured on GB300 (ct256): the transposed pass (8 lanes x 8) gains
-  // (38.2 -> 35.3 us per pass); y = A p (32 lanes x 4 under a 32-register
-  // cap) loses (31.1 -> 38.3 us), so it keeps int32 columns
-  if constexpr (MODE == 1) {
+  // 16-bit columns in the 8-lane layout (the transposed pass): measured on
+  // GB300 (ct256) it gains (38.2 -> 35.3 us per pass), while y = A p in the
+  // 32-lane layout under a 32-register cap loses (31.1 -> 38.3 us) and keeps
+  // int32 columns
+  if constexpr ((MODE == 0 || MODE == 1) && LPR == 8) {
     if (a.c16 != nullptr)
       return run1c<V, T, TO, MODE, U, LPR, true, MINB>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s,
                                                        fold);

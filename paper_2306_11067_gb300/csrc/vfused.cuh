@@ -25,11 +25,14 @@ namespace lcmg {
 constexpr int kVTile = 8;  // coarse points per tile side
 // threads of a tile block: enough for one point per thread in every phase
 // (the widest window is 22 x 22 on the 5-point finest level and 26 x 26 on
-// the 25-point levels); FP64 25-point blocks stay at 512 (their stencil
-// rows need more than the 64 registers a 1024-thread block allows)
-template <class Op, class T>
+// the 25-point levels with nu = 2; with nu = 1 the 25-point windows are at
+// most 22 x 22); FP64 25-point blocks stay at 512 (their stencil rows need
+// more than the 64 registers a 1024-thread block allows), and so do nu = 1
+// 25-point blocks, whose second phase's loads are issued before the first
+// phase's barrier (registers for the prefetched coefficients)
+template <class Op, class T, int NU = 2>
 __host__ __device__ constexpr int vtile_threads() {
-  return (Op::kRadius == 1 || sizeof(T) == 8) ? 512 : 1024;
+  return (Op::kRadius == 1 || sizeof(T) == 8 || NU == 1) ? 512 : 1024;
 }
 
 // block sum of v into part[blockIdx.x * B + col] (NT threads)
@@ -47,11 +50,11 @@ __device__ __forceinline__ void vblock_sum(double v, double* sred, double* part,
 }
 
 template <class Op, class T, int NU>
-__global__ void __launch_bounds__(vtile_threads<Op, T>())
+__global__ void __launch_bounds__(vtile_threads<Op, T, NU>())
     k_vdown(Op op, int B, const T* __restrict__ lam2, const T* __restrict__ dinv, const T* __restrict__ r,
             T* __restrict__ zpre, T* __restrict__ rc, int ntx) {
   pdl_entry();
-  constexpr int NTD = vtile_threads<Op, T>();
+  constexpr int NTD = vtile_threads<Op, T, NU>();
   constexpr int H = Op::kRadius;
   constexpr int WR = 2 * kVTile + 2;                  // restriction window
   constexpr int WZ = WR + 2 * H;                      // z window
@@ -70,6 +73,27 @@ __global__ void __launch_bounds__(vtile_threads<Op, T>())
   auto inside = [&](int i, int j) { return i >= 0 && i < nv && j >= 0 && j < nh; };
   auto gidx = [&](int i, int j) { return ((int64_t)i + (int64_t)j * nv) * B + col; };
 
+  // nu = 1 on the 25-point levels: the residual phase's loads (the point's
+  // coefficients and r) do not depend on z1, so they are issued before the
+  // first barrier, one residual point per thread
+  constexpr bool kPre = (NU == 1 && H == 2);
+  static_assert(!kPre || WR * WR <= NTD, "one residual point per thread");
+  T kpre[kPre ? 28 : 1];
+  T rpre = 0;
+  int pi = 0, pj = 0;
+  bool phave = false;
+  if constexpr (kPre) {
+    if ((int)threadIdx.x < WR * WR) {
+      pi = ri + (int)threadIdx.x % WR;
+      pj = rj + (int)threadIdx.x / WR;
+      phave = inside(pi, pj);
+      if (phave) {
+        const int64_t p = (int64_t)pi + (int64_t)pj * nv;
+        op.coefs(p, l2, kpre);
+        rpre = r[p * B + col];
+      }
+    }
+  }
   // z1 = D r
   for (int t = threadIdx.x; t < W1 * W1; t += NTD) {
     const int i = oi + t % W1, j = oj + t / W1;
@@ -96,16 +120,28 @@ __global__ void __launch_bounds__(vtile_threads<Op, T>())
   constexpr int WS = (NU == 2) ? WZ : W1;
   const int si = (NU == 2) ? zi : oi, sj = (NU == 2) ? zj : oj;
   // res = r - K z on the restriction window
-  for (int t = threadIdx.x; t < WR * WR; t += NTD) {
-    const int i = ri + t % WR, j = rj + t / WR;
-    T v = 0;
-    if (inside(i, j)) {
-      const int64_t p = (int64_t)i + (int64_t)j * nv;
-      const int q = (i - si) + (j - sj) * WS;
-      auto vz = [&](int di, int dj) { return zs[q + di + dj * WS]; };
-      v = r[p * B + col] - op.apply_off(p, i, j, l2, vz);
+  if constexpr (kPre) {
+    if ((int)threadIdx.x < WR * WR) {
+      T v = 0;
+      if (phave) {
+        const int q = (pi - si) + (pj - sj) * WS;
+        auto vz = [&](int di, int dj) { return zs[q + di + dj * WS]; };
+        v = rpre - op.apply_k(kpre, pi, pj, vz);
+      }
+      sres[threadIdx.x] = v;
     }
-    sres[t] = v;
+  } else {
+    for (int t = threadIdx.x; t < WR * WR; t += NTD) {
+      const int i = ri + t % WR, j = rj + t / WR;
+      T v = 0;
+      if (inside(i, j)) {
+        const int64_t p = (int64_t)i + (int64_t)j * nv;
+        const int q = (i - si) + (j - sj) * WS;
+        auto vz = [&](int di, int dj) { return zs[q + di + dj * WS]; };
+        v = r[p * B + col] - op.apply_off(p, i, j, l2, vz);
+      }
+      sres[t] = v;
+    }
   }
   // the pre-smoothed z of the tile's own fine points
   for (int t = threadIdx.x; t < 4 * kVTile * kVTile; t += NTD) {
@@ -133,19 +169,19 @@ __global__ void __launch_bounds__(vtile_threads<Op, T>())
 }
 
 template <class Op, class T, int NU>
-__global__ void __launch_bounds__(vtile_threads<Op, T>())
+__global__ void __launch_bounds__(vtile_threads<Op, T, NU>())
     k_vup(Op op, int B, const T* __restrict__ lam2, const T* __restrict__ dinv, const T* __restrict__ r,
           const T* __restrict__ ec, const T* __restrict__ zpre, T* __restrict__ zout, int ntx,
           double* __restrict__ part) {
   pdl_entry();
-  constexpr int NTD = vtile_threads<Op, T>();
+  constexpr int NTD = vtile_threads<Op, T, NU>();
   constexpr int H = Op::kRadius;
   constexpr int WF = 2 * kVTile;           // the tile's fine points
   constexpr int W0 = WF + 2 * NU * H;      // z0 window
   constexpr int W1 = WF + 2 * H;           // window after the first of two sweeps
   __shared__ T s0[W0 * W0];
   __shared__ T s1[(NU == 2) ? W1 * W1 : 1];
-  constexpr int NT = vtile_threads<Op, T>();
+  constexpr int NT = vtile_threads<Op, T, NU>();
   __shared__ double sred[NT / 32];
   const int col = blockIdx.y;
   const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
@@ -156,6 +192,28 @@ __global__ void __launch_bounds__(vtile_threads<Op, T>())
   const T l2 = lam2[col];
   auto inside = [&](int i, int j) { return i >= 0 && i < nv && j >= 0 && j < nh; };
 
+  // nu = 1 on the 25-point levels: the sweep's loads (coefficients, r and
+  // the inverse diagonal of the tile's fine points) do not depend on z0, so
+  // they are issued before the barrier, one fine point per thread
+  constexpr bool kPre = (NU == 1 && H == 2);
+  static_assert(!kPre || WF * WF <= NTD, "one fine point per thread");
+  T kpre[kPre ? 28 : 1];
+  T rpre = 0, dpre = 0;
+  int pi = 0, pj = 0;
+  bool phave = false;
+  if constexpr (kPre) {
+    if ((int)threadIdx.x < WF * WF) {
+      pi = fi + (int)threadIdx.x % WF;
+      pj = fj + (int)threadIdx.x / WF;
+      phave = inside(pi, pj);
+      if (phave) {
+        const int64_t p = (int64_t)pi + (int64_t)pj * nv;
+        op.coefs(p, l2, kpre);
+        rpre = r[p * B + col];
+        dpre = dinv[p * B + col];
+      }
+    }
+  }
   // z0 = z + P e_c
   for (int t = threadIdx.x; t < W0 * W0; t += NTD) {
     const int a2 = oi + t % W0, b = oj + t / W0;
@@ -204,7 +262,18 @@ __global__ void __launch_bounds__(vtile_threads<Op, T>())
   const int si = (NU == 2) ? ai : oi, sj = (NU == 2) ? aj : oj;
   // last sweep on the tile's fine points
   double dacc = 0.0;
-  for (int t = threadIdx.x; t < WF * WF; t += NTD) {
+  if constexpr (kPre) {
+    if (phave) {
+      const int64_t p = (int64_t)pi + (int64_t)pj * nv;
+      const int q = (pi - si) + (pj - sj) * WS;
+      auto vz = [&](int di, int dj) { return zs[q + di + dj * WS]; };
+      const T kz = op.apply_k(kpre, pi, pj, vz);
+      const T zn = zs[q] + dpre * (rpre - kz);
+      zout[p * B + col] = zn;
+      dacc += to_d(rpre) * to_d(zn);
+    }
+  }
+  for (int t = kPre ? WF * WF : (int)threadIdx.x; t < WF * WF; t += NTD) {
     const int i = fi + t % WF, j = fj + t / WF;
     if (!inside(i, j)) continue;
     const int64_t p = (int64_t)i + (int64_t)j * nv;
