@@ -359,6 +359,31 @@ def compare_algorithm2():
               flush=True)
 
 
+def job_aggregate(conv: float, elapsed: float, world: int, device=None):
+    """Whole-job totals of a replicas run: the converged lambda-solves of all
+    ranks (sum) and the slowest rank's time (max), over the default process
+    group (NCCL on GPUs, gloo on CPUs); a single rank returns its own."""
+    if world <= 1:
+        return float(conv), float(elapsed)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(conv), float(elapsed)], dtype=torch.float64, device=device)
+    tot = t[:1].clone()
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    mx = t[1:].clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    return float(tot[0]), float(mx[0])
+
+
+def replica_rhs(P, rank: int):
+    """Right-hand side of a rank's replica: the workload's own b on rank 0;
+    the same operator and phantom with the rank's own noise draw elsewhere."""
+    import problemgen as pg
+    if rank == 0:
+        return P.b[:, 0]
+    return pg.add_noise(P.A.to_scipy() @ P.x_true[:, 0], P.meta["noise"], P.meta["noise_seed"] + 7919 * rank)
+
+
 # ---------------------------------------------------------------------------
 def main():
     args = parse()
@@ -394,9 +419,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
 
     P = pg.make_problem(WORKLOAD)
-    b = P.b[:, 0]
-    if rank > 0:  # replica: same operator, its own noise draw
-        b = pg.add_noise(P.A.to_scipy() @ P.x_true[:, 0], P.meta["noise"], P.meta["noise_seed"] + 7919 * rank)
+    b = replica_rhs(P, rank)
     n, m = P.n, P.m
     prec = L.PREC_MIXED if args.precision == "mixed" else L.PREC_FP64
     mode = L.MODE_SEQUENTIAL if args.mode == "sequential" else L.MODE_BATCHED
@@ -454,15 +477,7 @@ def main():
     history = results[-1][0]["history"]
 
     # whole-job aggregate over ranks
-    if world > 1:
-        t = torch.tensor([float(conv), elapsed], device=dev, dtype=torch.float64)
-        tot = t.clone()
-        dist.all_reduce(tot[:1], op=dist.ReduceOp.SUM)
-        mx = t[1:].clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        conv_all, elapsed_all = float(tot[0]), float(mx[0])
-    else:
-        conv_all, elapsed_all = float(conv), elapsed
+    conv_all, elapsed_all = job_aggregate(conv, elapsed, world, dev)
     value = conv_all / elapsed_all
 
     # ---------------- end to end through the host API ---------------------
