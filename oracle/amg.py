@@ -46,6 +46,18 @@ Readings of this build (the paper names the steps, not these details):
   * coarsening stops at `max_levels` levels, when a level has at most
     `max_coarse` points, or when a pass keeps every point.
 
+Parallel replacement of the two passes (method="pmis"; De Sterck, Yang and
+Heys' PMIS, 2006): every point's measure is |S_i^T| plus a uniform random
+number in [0, 1); a point with no strong connection in either direction is
+F (a reading: PMIS makes every point nothing depends on F, which can leave
+an F point with no C point to interpolate from); then, in rounds, every unsorted point whose (measure, index) exceeds that of each
+unsorted point it is strongly connected to in either direction becomes C,
+and every unsorted point with a strong connection to a C point becomes F.
+The random numbers are SplitMix64 (Steele, Lea and Flood 2014) outputs of
+the stream seeded with PMIS_SEED + level, each mapped to (z >> 11) 2^-53.
+Interpolation is the paper's formula as above; its lumping rule covers the
+strong F-F pairs without a common C point that PMIS leaves.
+
 Every step is a plain loop over rows in the order stated; scipy is used for
 the sparse products only.
 """
@@ -59,6 +71,8 @@ import scipy.sparse as sp
 THETA = 0.25
 TIE_REL = 1e-10
 C_PT, F_PT = 1, 0
+PMIS_SEED = 2306
+_M64 = (1 << 64) - 1
 
 
 def _rows(K):
@@ -147,6 +161,41 @@ def split(K, theta=THETA):
     return second_pass(S, cf), S
 
 
+def splitmix64_uniform(seed, n):
+    """n uniforms in [0, 1) from the SplitMix64 stream seeded with `seed`."""
+    out = np.empty(n)
+    state = seed & _M64
+    for i in range(n):
+        state = (state + 0x9E3779B97F4A7C15) & _M64
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+        z ^= z >> 31
+        out[i] = (z >> 11) * 2.0 ** -53
+    return out
+
+
+def pmis_split(S, n, rand):
+    """PMIS C/F split of the strength sets S with the random numbers rand."""
+    ST = transpose_sets(S, n)
+    w = [len(ST[i]) + float(rand[i]) for i in range(n)]
+    nbr = [sorted(set(S[i]) | set(ST[i])) for i in range(n)]
+    U = -1
+    cf = [U] * n
+    for i in range(n):
+        if not ST[i] and not S[i]:
+            cf[i] = F_PT
+    while U in cf:
+        new_c = [i for i in range(n) if cf[i] == U and
+                 all((w[i], i) > (w[j], j) for j in nbr[i] if cf[j] == U)]
+        for i in new_c:
+            cf[i] = C_PT
+        for i in range(n):
+            if cf[i] == U and any(cf[j] == C_PT for j in S[i]):
+                cf[i] = F_PT
+    return np.array(cf, dtype=np.int8)
+
+
 def interpolation(K, S, cf) -> sp.csr_matrix:
     """P (n x n_c) of the paper's interpolation formula."""
     K = _rows(K)
@@ -182,11 +231,17 @@ def interpolation(K, S, cf) -> sp.csr_matrix:
     return sp.csr_matrix((vals, (rows, cols)), shape=(n, cpts.size))
 
 
-def hierarchy(K0, max_levels=20, max_coarse=256, theta=THETA):
-    """Operators K_k, interpolations P_k (level k+1 -> k) and splits."""
+def hierarchy(K0, max_levels=20, max_coarse=256, theta=THETA, method="rs"):
+    """Operators K_k, interpolations P_k (level k+1 -> k) and splits;
+    method "rs" (the paper's two passes) or "pmis"."""
     Ks, Ps, cfs = [_rows(K0)], [], []
     while len(Ks) < max_levels and Ks[-1].shape[0] > max_coarse:
-        cf, S = split(Ks[-1], theta)
+        if method == "pmis":
+            S = strength(Ks[-1], theta)
+            n = len(S)
+            cf = pmis_split(S, n, splitmix64_uniform(PMIS_SEED + len(Ks) - 1, n))
+        else:
+            cf, S = split(Ks[-1], theta)
         if cf.sum() in (0, cf.size):
             break
         P = interpolation(Ks[-1], S, cf)

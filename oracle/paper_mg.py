@@ -85,10 +85,12 @@ def build_one_sided(A, L, d, n_v, n_h, levels) -> OneSided:
     return OneSided(shapes, As, Ms, Ps, dA, dM)
 
 
-def build_one_sided_amg(A, L, d, max_levels=20, max_coarse=256) -> OneSided:
+def build_one_sided_amg(A, L, d, max_levels=20, max_coarse=256, method="rs") -> OneSided:
     """As build_one_sided with the classical AMG interpolation of
-    G_L = L^T D^2 L (Sec. 3.2); level shapes are (n_k, 1)."""
-    Ks, Ps, _ = amg.hierarchy(mg.weighted_laplacian(L, np.asarray(d, dtype=np.float64)), max_levels, max_coarse)
+    G_L = L^T D^2 L (Sec. 3.2; split by the paper's two passes or by PMIS);
+    level shapes are (n_k, 1)."""
+    Ks, Ps, _ = amg.hierarchy(mg.weighted_laplacian(L, np.asarray(d, dtype=np.float64)), max_levels, max_coarse,
+                              method=method)
     As = [sp.csr_matrix(A, dtype=np.float64)]
     Ms = [(sp.diags(np.asarray(d, dtype=np.float64)) @ L).tocsr()]
     for P in Ps:
@@ -226,10 +228,11 @@ def fgmres(apply_K, c, x0=None, apply_M=None, tol=1e-6, maxit=10000, restart=200
 def solve(F, L, d, n_v, n_h, levels, c, lam, x0=None, tol=1e-6, maxit=10000, nu1=2, nu2=1,
           restart=200, coarsening="geometric", max_coarse=256, orth="mgs"):
     """FGMRES with the paper's V-cycle on eq. (normal) for one lambda;
-    with coarsening="amg", `levels` is the largest number of levels."""
+    with coarsening="amg" (the paper's split) or "pmis", `levels` is the
+    largest number of levels."""
     A = explicit_forward(F)
-    if coarsening == "amg":
-        h = build_one_sided_amg(A, L, d, levels, max_coarse)
+    if coarsening in ("amg", "pmis"):
+        h = build_one_sided_amg(A, L, d, levels, max_coarse, "pmis" if coarsening == "pmis" else "rs")
     else:
         h = build_one_sided(A, L, d, n_v, n_h, levels)
     V = PaperVCycle(h, lam, nu1, nu2)

@@ -194,3 +194,59 @@ def test_amg_paper_solver_reaches_the_dense_solution(lam):
     x, it, st, _ = pm.solve(F, Lg, d, n, n, 20, c, lam, tol=1e-12, maxit=500, coarsening="amg", max_coarse=32)
     assert st == krylov.CONVERGED
     assert np.linalg.norm(x - x_ref) <= 10 * np.linalg.cond(Kd) * 1e-12 * np.linalg.norm(x_ref)
+
+
+def test_splitmix64_reproduces_its_published_outputs():
+    """The reference SplitMix64 stream seeded with 0 starts 0xe220a8397b1dcdaf,
+    0x6e789e6aa1b965f4, 0x06c45d188009454f; the uniforms are the top 53 bits."""
+    u = amg.splitmix64_uniform(0, 3)
+    for x, z in zip(u, (0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F)):
+        assert x == (z >> 11) * 2.0 ** -53
+
+
+def _path(n, edges):
+    K = np.zeros((n, n))
+    for a, b in edges:
+        K[a, b] = K[b, a] = -1.0
+    K[np.arange(n), np.arange(n)] = -K.sum(axis=1)
+    return sp.csr_matrix(K)
+
+
+def test_pmis_one_round_by_hand():
+    """Path 0-1-2-3-4, rand (.1 .9 .2 .8 .3): measures 1.1 2.9 2.2 2.8 1.3;
+    1 and 3 exceed their unsorted neighbours and become C; 0, 2, 4 depend on
+    them and become F."""
+    K = _path(5, [(0, 1), (1, 2), (2, 3), (3, 4)])
+    S = amg.strength(K)
+    cf = amg.pmis_split(S, 5, np.array([0.1, 0.9, 0.2, 0.8, 0.3]))
+    assert cf.tolist() == [0, 1, 0, 1, 0]
+
+
+def test_pmis_two_rounds_by_hand():
+    """Path 0-..-5, measures 1.5 2.1 2.9 2.3 2.2 1.05: round 1 makes 2 C and
+    1, 3 F; round 2: 0 has no unsorted neighbour left (C), 4 exceeds 5 (C),
+    then 5 depends on 4 (F)."""
+    K = _path(6, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5)])
+    S = amg.strength(K)
+    cf = amg.pmis_split(S, 6, np.array([0.5, 0.1, 0.9, 0.3, 0.2, 0.05]))
+    assert cf.tolist() == [1, 0, 1, 0, 1, 0]
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_pmis_invariants_on_random_weights(seed):
+    """Every point is sorted; an F point either has no strong connections at
+    all or a strong connection to a C point; the hierarchy interpolates
+    constants exactly."""
+    n_v, n_h = 24, 20
+    d = pg.random_weights(ops.n_edges(n_v, n_h), seed, d_min=0.02)
+    K = mg.weighted_laplacian(ops.gradient(n_v, n_h), d)
+    S = amg.strength(K)
+    ST = amg.transpose_sets(S, K.shape[0])
+    cf = amg.pmis_split(S, K.shape[0], amg.splitmix64_uniform(amg.PMIS_SEED, K.shape[0]))
+    assert set(cf.tolist()) <= {0, 1}
+    for i in np.flatnonzero(cf == amg.F_PT):
+        assert (not ST[i] and not S[i]) or any(cf[j] == amg.C_PT for j in S[i])
+    Ks, Ps, _ = amg.hierarchy(K, max_coarse=16, method="pmis")
+    assert len(Ps) >= 2
+    for P in Ps:
+        assert np.abs(P @ np.ones(P.shape[1]) - 1.0).max() <= 1e-13
