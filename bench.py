@@ -308,6 +308,7 @@ def compare_precond():
     F64, MIX = L.PREC_FP64, L.PREC_MIXED
     arms = [("pcg-default", dict(precond=0, precision=F64)), ("paper-geometric", dict(precond=1, precision=F64)),
             ("paper-amg", dict(precond=1, coarsening=1, precision=F64)),
+            ("paper-amg-pmis", dict(precond=1, coarsening=2, precision=F64)),
             ("pcg-default-mixed", dict(precond=0, precision=MIX))]
     for N in (64, 128, 256):
         P = pg.make_problem(WORKLOAD, size=None if N == 256 else N)

@@ -168,8 +168,11 @@ typedef struct {
                            (default); 1 = classical AMG of Sec. 3.1 on
                            L^T D^2 L (strength theta = 0.25, the two-pass C/F
                            split, the paper's interpolation formula), rebuilt
-                           on the host for every weight vector; `levels` is
-                           then the largest level count (0 = no limit)      */
+                           on the host for every weight vector; 2 = the same
+                           with the split by PMIS on the device
+                           (lcmg_pmis_split) instead of the two passes;
+                           `levels` is then the largest level count (0 = no
+                           limit)                                           */
   int32_t amg_coarse_max; /* classical AMG: coarsen while a level has more
                            points than this (2..2048; 256); the last level is
                            solved densely                                   */
@@ -331,6 +334,20 @@ int lcmg_rs_split(int64_t n, const int64_t* row_ptr, const int32_t* col, const d
 int lcmg_rs_interp(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
                    double theta, const int8_t* cf, int64_t cap, int64_t* p_row_ptr,
                    int32_t* p_col, double* p_val, int64_t* nnz);
+
+/* PMIS C/F split (De Sterck, Yang and Heys 2006), the parallel replacement
+ * of lcmg_rs_split's two passes, run on the current CUDA device for a matrix
+ * in host memory (same arguments and strength rule as lcmg_rs_split).
+ * Measure of point i: |S_i^T| + u_i, u_i = (z >> 11) 2^-53 for the i-th
+ * output z of the SplitMix64 stream seeded with `seed` (level k of a
+ * context's hierarchy uses seed 2306 + k).  A point with no strong
+ * connection in either direction is F; then, in rounds, every unsorted
+ * point whose (measure, index) exceeds that of each unsorted point it is
+ * strongly connected to (either direction) becomes C, and every unsorted
+ * point with a strong connection to a C point becomes F.  cf[i] = 1 for C,
+ * 0 for F.  Errors: as lcmg_rs_split; NOMEM or CUDA from the device. */
+int lcmg_pmis_split(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val,
+                    double theta, uint64_t seed, int8_t* cf);
 
 /* Level sizes of the classical AMG hierarchy the context last built
  * (coarsening = 1, after a solve): sizes[k] for k < min(cap, levels),

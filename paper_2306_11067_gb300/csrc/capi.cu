@@ -292,7 +292,7 @@ static void check_params(const lcmg_params& p) {
   if (p.stop_rule != 0 && p.stop_rule != 1) throw ArgError("stop_rule must be 0 or 1");
   if (p.precond != 0 && p.precond != 1) throw ArgError("precond must be 0 or 1");
   if (p.gmres_restart < 1 || p.gmres_restart > 2000) throw ArgError("gmres_restart must be 1..2000");
-  if (p.coarsening != 0 && p.coarsening != 1) throw ArgError("coarsening must be 0 or 1");
+  if (p.coarsening < 0 || p.coarsening > 2) throw ArgError("coarsening must be 0, 1 or 2");
   if (p.compact_cols != 0 && p.compact_cols != 1) throw ArgError("compact_cols must be 0 or 1");
   if (p.alpha_fuse != 0 && p.alpha_fuse != 1) throw ArgError("alpha_fuse must be 0 or 1");
   if (p.beta_fuse != 0 && p.beta_fuse != 1) throw ArgError("beta_fuse must be 0 or 1");
@@ -1232,7 +1232,7 @@ static void pm_build_amg(lcmg_ctx& c) {
   copy_sync(s, d.data(), c.d.p, sizeof(double) * c.ne, cudaMemcpyDeviceToHost);
   const HostCsr K0 = amg::weighted_laplacian(c.nv, c.nh, d.data());
   const int maxlev = c.prm.levels > 0 ? c.prm.levels : 64;
-  amg::Hierarchy H = amg::hierarchy(K0, maxlev, c.prm.amg_coarse_max, amg::kTheta);
+  amg::Hierarchy H = amg::hierarchy(K0, maxlev, c.prm.amg_coarse_max, amg::kTheta, c.prm.coarsening == 2, s);
   const int L = (int)H.K.size();
   if (L < 2) throw ArgError("classical AMG made no coarse level (grid at most amg_coarse_max points, or levels = 1)");
   const int64_t nc = H.K[L - 1].rows;
@@ -1288,7 +1288,7 @@ static void pm_build_amg(lcmg_ctx& c) {
 }
 
 static void pm_build(lcmg_ctx& c) {
-  if (c.prm.coarsening == 1) {
+  if (c.prm.coarsening == 1 || c.prm.coarsening == 2) {
     pm_build_amg(c);
     return;
   }
@@ -1319,8 +1319,8 @@ struct PaperMG {
   bool amg;
   int L;
   explicit PaperMG(lcmg_ctx& c_)
-      : c(c_), s(c_.stream), amg(c_.prm.coarsening == 1),
-        L(c_.prm.coarsening == 1 ? (int)c_.am.size() : (int)c_.lev.size()) {}
+      : c(c_), s(c_.stream), amg(c_.prm.coarsening != 0),
+        L(c_.prm.coarsening != 0 ? (int)c_.am.size() : (int)c_.lev.size()) {}
 
   int64_t nk(int k) const { return amg ? c.am[k].n : c.lev[k].n; }
   int grid(int k) const { return grid_for(nk(k), 1, c.maxblk); }
@@ -2406,6 +2406,16 @@ int lcmg_rs_interp(int64_t n, const int64_t* row_ptr, const int32_t* col, const 
   std::copy(P.rp.begin(), P.rp.end(), p_row_ptr);
   std::copy(P.ci.begin(), P.ci.end(), p_col);
   std::copy(P.v.begin(), P.v.end(), p_val);
+  API_END
+}
+
+int lcmg_pmis_split(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* val, double theta,
+                    uint64_t seed, int8_t* cf) {
+  API_BEGIN
+  if (!cf || !(theta > 0.0 && theta < 1.0)) throw lcmg::ArgError("null cf or theta outside (0, 1)");
+  const lcmg::HostCsr K = lcmg::host_square_csr(n, row_ptr, col, val);
+  const std::vector<int8_t> s = lcmg::amg::pmis_split(lcmg::amg::strength(K, theta), n, seed, nullptr);
+  std::copy(s.begin(), s.end(), cf);
   API_END
 }
 

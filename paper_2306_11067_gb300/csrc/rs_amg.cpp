@@ -312,13 +312,15 @@ HostCsr weighted_laplacian(int nv, int nh, const double* d) {
   return K;
 }
 
-Hierarchy hierarchy(const HostCsr& K0, int max_levels, int64_t max_coarse, double theta) {
+Hierarchy hierarchy(const HostCsr& K0, int max_levels, int64_t max_coarse, double theta, bool pmis,
+                    cudaStream_t s) {
   Hierarchy H;
   H.K.push_back(K0);
   while ((int)H.K.size() < max_levels && H.K.back().rows > max_coarse) {
     const HostCsr& K = H.K.back();
     const Strength S = strength(K, theta);
-    const std::vector<int8_t> cf = split(S, K.rows);
+    const std::vector<int8_t> cf =
+        pmis ? pmis_split(S, K.rows, kPmisSeed + (uint64_t)(H.K.size() - 1), s) : split(S, K.rows);
     int64_t nc = 0;
     for (int8_t f : cf) nc += f == kC;
     if (nc == 0 || nc == K.rows) break;

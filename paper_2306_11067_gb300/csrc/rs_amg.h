@@ -6,6 +6,8 @@
 // choice depends on every earlier one), and its result is the coarse grid,
 // so it runs here on the host, once per weight vector, in O(nnz log n).
 #pragma once
+#include <cuda_runtime_api.h>
+
 #include <cstdint>
 #include <vector>
 
@@ -49,6 +51,17 @@ std::vector<int8_t> split(const Strength& S, int64_t n);
 // A strong F connection whose sum over C_i is zero is lumped with F_i^w.
 HostCsr interpolation(const HostCsr& K, const Strength& S, const std::vector<int8_t>& cf);
 
+// PMIS (De Sterck, Yang and Heys 2006), the parallel replacement of the two
+// passes, on the device: measure = |S_i^T| + u_i, u_i the i-th uniform
+// (z >> 11) 2^-53 of the SplitMix64 stream seeded with `seed`; a point with
+// no strong connection in either direction is F; then rounds in which every
+// unsorted point whose (measure, index) exceeds that of each unsorted point
+// it is strongly connected to (either direction) becomes C, and every
+// unsorted point with a strong connection to a C point becomes F.
+// Level k of a hierarchy uses seed kPmisSeed + k.
+constexpr uint64_t kPmisSeed = 2306;
+std::vector<int8_t> pmis_split(const Strength& S, int64_t n, uint64_t seed, cudaStream_t s);
+
 // C = A B, rows accumulated in the order of A's and B's nonzeros, then sorted.
 HostCsr spgemm(const HostCsr& A, const HostCsr& B);
 HostCsr transpose(const HostCsr& A);
@@ -65,8 +78,10 @@ struct Hierarchy {
 };
 
 // Coarsen while fewer than max_levels levels and more than max_coarse
-// points remain; stop when a split keeps every point or none.
-Hierarchy hierarchy(const HostCsr& K0, int max_levels, int64_t max_coarse, double theta);
+// points remain; stop when a split keeps every point or none.  pmis: split
+// by PMIS on the device (stream s) instead of the two passes.
+Hierarchy hierarchy(const HostCsr& K0, int max_levels, int64_t max_coarse, double theta, bool pmis = false,
+                    cudaStream_t s = nullptr);
 
 }  // namespace amg
 }  // namespace lcmg

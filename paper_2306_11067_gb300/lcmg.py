@@ -116,6 +116,7 @@ _SIGS = {
     "lcmg_rs_split": (C.c_int, [_I64, _P, _P, _P, _D, _P]),
     "lcmg_rs_interp": (C.c_int, [_I64, _P, _P, _P, _D, _P, _I64, _P, _P, _P, _PI64]),
     "lcmg_amg_levels": (C.c_int, [_P, _I32, _P, _PI32]),
+    "lcmg_pmis_split": (C.c_int, [_I64, _P, _P, _P, _D, C.c_uint64, _P]),
     "lcmg_lcurve_run": (C.c_int, [_P, _I32, _P, _P, _I32, _P, _P, _PI32, _PI64, _PI64]),
     "lcmg_lcurve_run_dev": (C.c_int, [_P, _I32, _P, _P, _I32, _P, _P, _PI32, _PI64, _PI64]),
     "lcmg_get_stats": (C.c_int, [_P, C.POINTER(lcmg_stats)]),
@@ -328,6 +329,14 @@ def lcmg_rs_interp(K, cf, theta=0.25):
     _check(lib().lcmg_rs_interp(n, _ptr(rp), _ptr(ci), _ptr(v), theta, _ptr(cf), cap, _ptr(prp), _ptr(pci),
                                 _ptr(pv), C.byref(nnz)))
     return prp, pci[:nnz.value].copy(), pv[:nnz.value].copy(), int(cf.sum())
+
+
+def lcmg_pmis_split(K, seed, theta=0.25):
+    """PMIS C/F split on the current device: int8 array, 1 = C, 0 = F."""
+    n, rp, ci, v = _csr_in(K)
+    cf = np.empty(n, np.int8)
+    _check(lib().lcmg_pmis_split(n, _ptr(rp), _ptr(ci), _ptr(v), theta, seed, _ptr(cf)))
+    return cf
 
 
 def lcmg_amg_levels(ctx):

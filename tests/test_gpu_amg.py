@@ -146,7 +146,7 @@ def test_amg_method_selects_the_same_corners():
 
 def test_amg_argument_errors():
     with pytest.raises(L.LcmgError):
-        Solver(32, 32, precond=1, coarsening=2)
+        Solver(32, 32, precond=1, coarsening=3)
     with pytest.raises(L.LcmgError):
         Solver(32, 32, precond=1, coarsening=1, amg_coarse_max=1)
     P = pg.make_problem("ct256", size=32)
@@ -159,3 +159,46 @@ def test_amg_argument_errors():
     with pytest.raises(L.LcmgError):
         s.solve([0.1], P.b[:, 0])
     s.close()
+
+
+@pytest.mark.parametrize("n_v,n_h,seed", [(32, 32, 1), (40, 24, 2), (64, 64, 3)])
+def test_pmis_split_on_the_device_matches_oracle(n_v, n_h, seed):
+    """lcmg_pmis_split (device rounds) on every level of the oracle's PMIS
+    hierarchy: the same split, bit for bit, with the level's seed."""
+    d = pg.random_weights(ops.n_edges(n_v, n_h), seed, d_min=0.02)
+    Ks, _, cfs = amg.hierarchy(mg.weighted_laplacian(ops.gradient(n_v, n_h), d), max_coarse=16, method="pmis")
+    assert len(cfs) >= 2
+    for k, cf in enumerate(cfs):
+        got = L.lcmg_pmis_split(Ks[k], amg.PMIS_SEED + k)
+        assert np.array_equal(got, cf), (k, int((got != cf).sum()))
+
+
+@pytest.mark.parametrize("kind", ["blur", "ct"])
+def test_pmis_cycle_and_solve_match_oracle(kind):
+    """coarsening = 2: the hierarchy split by PMIS on the device; the cycle
+    to 1e-10 and FGMRES solutions to 1e-8 against the oracle's."""
+    n_v, n_h, A, b = _problem(kind)
+    d = pg.random_weights(ops.n_edges(n_v, n_h), 6, d_min=0.05)
+    s = Solver(n_v, n_h, precond=1, coarsening=2, amg_coarse_max=24, tol=1e-12, maxit=2000)
+    s.set_forward_csr(A)
+    s.set_weights(d)
+    lams = np.array([1e-2, 0.3, 3.0])
+    R = pg.rng(5).standard_normal((3, n_v * n_h))
+    rd = torch.tensor(R, device="cuda", dtype=torch.float64)
+    zd = torch.empty_like(rd)
+    L.lcmg_apply_vcycle_dev(s.ctx, lams, rd, zd)
+    sizes = L.lcmg_amg_levels(s.ctx)
+    out = s.solve(lams[1:], b)
+    s.close()
+    h = pm.build_one_sided_amg(A.to_scipy(), ops.gradient(n_v, n_h), d, 64, 24, method="pmis")
+    assert sizes.tolist() == [a.shape[1] for a in h.A]
+    for j, lam in enumerate(lams):
+        ref = pm.PaperVCycle(h, lam)(R[j])
+        assert _rel(zd[j].cpu().numpy(), ref) <= 1e-10, (lam, _rel(zd[j].cpu().numpy(), ref))
+    F = ops.ForwardCSR(A.to_scipy())
+    c = ops.rhs(F, b)
+    for j, lam in enumerate(lams[1:]):
+        x, _, st, _ = pm.solve(F, ops.gradient(n_v, n_h), d, n_v, n_h, 64, c, lam, tol=1e-12, maxit=2000,
+                               coarsening="pmis", max_coarse=24)
+        assert st == krylov.CONVERGED and out["status"][0, j] == 0
+        assert _rel(out["x"][0, j], x) <= 1e-8
