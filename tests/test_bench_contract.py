@@ -1,0 +1,38 @@
+"""bench.py's host-side pieces (no GPU): the committed ncu traffic record
+belongs to the current one-column SpMV source, the roofline peak falls
+back when the measured one is absent, and the command-line modes parse."""
+import json
+import os
+import sys
+
+import bench
+
+
+def test_traffic_record_matches_the_current_kernel_source():
+    """The ncu traffic figure in profiles/ is used only while k_spmv1 and its
+    launchers hash to the recorded fingerprint: a kernel edit must come with
+    a fresh capture (else the bench reports traffic null)."""
+    assert bench.recorded_traffic() is not None, bench.kernel_fingerprint()
+    assert 1.0e8 < bench.recorded_traffic() < 1.2e8
+
+
+def test_peak_is_measured_or_the_stated_fallback(tmp_path, monkeypatch):
+    peak, kind = bench.measured_hbm_peak()
+    path = os.path.join(bench.ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        assert kind == "measured" and peak == float(json.load(open(path))["hbm_gbs"])
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_hbm_peak() == (6800.0, "fallback")
+
+
+def test_command_line_modes_parse(monkeypatch):
+    for argv in (["bench.py"], ["bench.py", "--gpus", "2", "--steps", "4", "--warmup", "3"],
+                 ["bench.py", "--impl", "reference"], ["bench.py", "--compare-precond"],
+                 ["bench.py", "--compare-algorithm2"], ["bench.py", "--profile-iters", "48", "--profile-precond", "2"],
+                 ["bench.py", "--no-serve", "--no-cpu", "--no-plain", "--precision", "fp64", "--mode", "batched"]):
+        monkeypatch.setattr(sys, "argv", argv)
+        args = bench.parse()
+        assert args.warmup >= 3 or "--warmup" not in argv
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = bench.parse()
+    assert (a.gpus, a.steps, a.warmup, a.impl) == (1, 3, 3, "ours")
