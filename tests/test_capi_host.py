@@ -111,3 +111,42 @@ def test_rs_host_argument_errors():
     assert L.lib().lcmg_rs_split(n, L._ptr(rp), L._ptr(bad), L._ptr(v), 0.25, L._ptr(cf)) == L.LCMG_ERR_INVALID_ARG
     with pytest.raises(L.LcmgError):                     # an F point without a strong C connection
         L.lcmg_rs_interp(K, np.array([0, 0], np.int8))
+
+
+def _edge_case_matrices():
+    import scipy.sparse as sp
+    yield "diagonal", sp.csr_matrix(np.diag([2.0, 3.0, 1.0, 4.0]))
+    yield "positive off-diagonals", sp.csr_matrix(np.array([[2.0, 0.5, 0.0], [0.5, 2.0, 0.5], [0.0, 0.5, 2.0]]))
+    A = np.zeros((6, 6))
+    for a, b in ((0, 1), (1, 2), (3, 4), (4, 5)):      # two components
+        A[a, b] = A[b, a] = -1.0
+    A[np.arange(6), np.arange(6)] = -A.sum(axis=1)
+    yield "two components", sp.csr_matrix(A)
+    yield "one point", sp.csr_matrix(np.array([[1.0]]))
+    g = pg.rng(7)
+    n = 12
+    perm = g.permutation(n)
+    K = np.zeros((n, n))
+    for i in range(n - 1):                               # 1-D chain, shuffled numbering
+        a, b = perm[i], perm[i + 1]
+        K[a, b] = K[b, a] = -1.0
+    K[np.arange(n), np.arange(n)] = -K.sum(axis=1)
+    yield "shuffled chain", sp.csr_matrix(K)
+
+
+@pytest.mark.parametrize("name,K", list(_edge_case_matrices()), ids=lambda v: v if isinstance(v, str) else "")
+def test_rs_amg_edge_cases_match_oracle(name, K):
+    """Degenerate inputs of the host AMG calls: the same split and
+    interpolation as the oracle (no strong connection at all: every point
+    C and P the identity)."""
+    import scipy.sparse as sp
+    from oracle import amg
+    cf_ref, S = amg.split(K)
+    cf = L.lcmg_rs_split(K)
+    assert np.array_equal(cf, cf_ref), (name, cf, cf_ref)
+    rp, ci, v, nc = L.lcmg_rs_interp(K, cf)
+    P_ref = amg.interpolation(K, S, cf_ref)
+    P = sp.csr_matrix((v, ci, rp), shape=(K.shape[0], nc))
+    assert P.shape == P_ref.shape and abs(P - P_ref).max() <= 1e-15 if P.nnz else P_ref.nnz == 0
+    if name in ("diagonal", "positive off-diagonals", "one point"):
+        assert cf.all() and np.allclose(P.toarray(), np.eye(K.shape[0]))
