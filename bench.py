@@ -63,7 +63,8 @@ def parse():
                          "128^2, 256^2; one JSON line per arm, no bench line")
     ap.add_argument("--compare-algorithm2", action="store_true",
                     help="one full Algorithm 2 run of the workload per solver arm (default preconditioner mixed "
-                         "and FP64, the paper's method with geometric and classical AMG interpolation): "
+                         "and FP64, the paper's method with geometric P and with classical AMG split by the "
+                         "paper's two passes or by PMIS): "
                          "lambda-solves/s and the selected lambda indices; one JSON line per arm")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiler workload: one lambda of the workload, this many PCG iterations, no JSON line")
@@ -345,7 +346,8 @@ def compare_algorithm2():
     arms = [("pcg-default-mixed", dict(precond=0, precision=L.PREC_MIXED)),
             ("pcg-default-fp64", dict(precond=0, precision=L.PREC_FP64)),
             ("paper-geometric", dict(precond=1, precision=L.PREC_FP64)),
-            ("paper-amg", dict(precond=1, coarsening=1, precision=L.PREC_FP64))]
+            ("paper-amg", dict(precond=1, coarsening=1, precision=L.PREC_FP64)),
+            ("paper-amg-pmis", dict(precond=1, coarsening=2, precision=L.PREC_FP64))]
     for name, kw in arms:
         s = L.Solver(P.n_v, P.n_h, mode=L.MODE_SEQUENTIAL, tol=1e-6, maxit=10000, nu=NU, **kw)
         s.set_forward_csr(P.A)
