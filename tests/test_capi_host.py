@@ -150,3 +150,52 @@ def test_rs_amg_edge_cases_match_oracle(name, K):
     assert P.shape == P_ref.shape and abs(P - P_ref).max() <= 1e-15 if P.nnz else P_ref.nnz == 0
     if name in ("diagonal", "positive off-diagonals", "one point"):
         assert cf.all() and np.allclose(P.toarray(), np.eye(K.shape[0]))
+
+
+def _header_struct_fields(name):
+    """(type, name) of every field of a typedef'd struct of include/lcmg.h,
+    in order; pointer types as 'ptr'."""
+    import re
+    txt = open(L.HEADER).read()
+    end = txt.index("} " + name + ";")
+    start = txt.rindex("typedef struct", 0, end)
+    body = re.sub(r"/\*.*?\*/", "", txt[txt.index("{", start) + 1:end], flags=re.S)
+    out = []
+    for decl in body.split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        m = re.match(r"(?:const\s+)?(\w+)\s*(\*?)\s*(.*)", decl)
+        base, star, names = m.group(1), m.group(2), m.group(3)
+        for nm in names.split(","):
+            nm = nm.strip()
+            ptr = bool(star) or nm.startswith("*")
+            out.append(("ptr" if ptr else base, nm.lstrip("*").strip()))
+    return out
+
+
+@pytest.mark.parametrize("name", ["lcmg_params", "lcmg_stats", "lcmg_problem", "lcmg_request", "lcmg_result",
+                                  "lcmg_server_stats"])
+def test_abi_structs_match_the_header_field_by_field(name):
+    import ctypes as C
+    want = _header_struct_fields(name)
+    got = getattr(L, name)._fields_
+    # a C field named after a Python keyword carries a trailing underscore
+    assert [n for _, n in want] == [n.rstrip("_") for n, _ in got]
+    cmap = {"int32_t": C.c_int32, "int64_t": C.c_int64, "double": C.c_double, "size_t": C.c_size_t,
+            "ptr": C.c_void_p}
+    for (t, n), (n2, ct) in zip(want, got):
+        assert cmap[t] == ct, (name, n)
+
+
+def test_default_params_write_exactly_the_struct():
+    """The library fills sizeof(lcmg_params) bytes: guard bytes after the
+    binding's struct stay untouched and the last fields hold their defaults."""
+    import ctypes as C
+    size = C.sizeof(L.lcmg_params)
+    buf = (C.c_ubyte * (size + 64))(*([0xA5] * (size + 64)))
+    L.lib().lcmg_default_params(C.cast(buf, C.POINTER(L.lcmg_params)))
+    assert bytes(buf[size:]) == bytes([0xA5]) * 64
+    p = L.lcmg_params.from_buffer(buf)
+    assert (p.amg_coarse_max, p.compact_cols, p.alpha_fuse, p.beta_fuse, p.tail_ctas, p.spmv_variant_at) == \
+        (256, 1, 1, 1, 1, 0)
