@@ -398,8 +398,9 @@ typedef struct {
   int64_t op_bytes;
   int32_t fused_ctas;   /* CTAs of the cluster running the fused iteration, 0 if unused */
   int32_t tuned_spmv_a, tuned_spmv_at;  /* SpMV configuration of the passes
-                           (SpmmArgs variant: 1 = 32 lanes x 4, 2 = 16 x 8,
-                           3 = 8 x 8; 0 = default) used by the last batch     */
+                           (params.spmv_variant numbering: 1 = 32 lanes x 4,
+                           2 = 16 x 8, 3 = 8 x 8, 4-6 the register-bounded
+                           forms; 0 = default) used by the last batch        */
   int32_t tuned_vfuse;  /* V-cycle form of the last batch: 1 fused, 0 per step,
                            -1 the params.vfuse rule                              */
 } lcmg_stats;
