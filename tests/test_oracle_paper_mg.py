@@ -128,3 +128,22 @@ def test_paper_cycle_beats_the_jacobi_preconditioner():
     _, it_mg, st_mg, _ = pm.fgmres(K, c, None, V, 1e-6, 2000)
     _, it_j, st_j, _ = pm.fgmres(K, c, None, lambda v: V.dinv[0] * v, 1e-6, 2000)
     assert st_mg == krylov.CONVERGED and it_mg < it_j
+
+
+@pytest.mark.parametrize("orth", ["mgs", "cgs2"])
+def test_fgmres_restart_one_is_the_minimal_residual_iteration(orth):
+    """Restarted after every step, unpreconditioned GMRES is the minimal
+    residual iteration x <- x + a r, a = (r.Kr) / (Kr.Kr): the restart
+    logic (true residual, new basis) against that closed form."""
+    g = pg.rng(11)
+    n = 16
+    K = g.standard_normal((n, n)) + 8 * np.eye(n)
+    c = g.standard_normal(n)
+    x_ref = np.zeros(n)
+    for _ in range(5):
+        r = c - K @ x_ref
+        Kr = K @ r
+        x_ref = x_ref + (r @ Kr) / (Kr @ Kr) * r
+    x, it, st, _ = pm.fgmres(lambda v: K @ v, c, None, None, tol=0.0, maxit=5, restart=1, orth=orth)
+    assert it == 5
+    assert np.linalg.norm(x - x_ref) <= 1e-12 * np.linalg.norm(x_ref)
