@@ -147,3 +147,43 @@ def test_fgmres_restart_one_is_the_minimal_residual_iteration(orth):
     x, it, st, _ = pm.fgmres(lambda v: K @ v, c, None, None, tol=0.0, maxit=5, restart=1, orth=orth)
     assert it == 5
     assert np.linalg.norm(x - x_ref) <= 1e-12 * np.linalg.norm(x_ref)
+
+
+@pytest.mark.parametrize("lam", [0.05, 0.7])
+def test_two_level_cycle_by_krylov_optimality(lam):
+    """A two-level cycle with a 2-column coarse space P, built from
+    characterisations independent of the module: k steps of
+    Jacobi-preconditioned CG from 0 minimise the K-norm error over
+    span{D^-1 b, (D^-1 K) D^-1 b, ...}; the coarse correction is the exact
+    Galerkin correction along P; one CG step from x minimises the K-norm
+    error over x + span{D^-1 r}.  D = diag(A^T A) + lam^2 diag(M^T M)."""
+    g = pg.rng(21)
+    n_v, n_h = 4, 3
+    n = n_v * n_h
+    A = sp.csr_matrix(g.standard_normal((15, n)))
+    Lg = ops.gradient(n_v, n_h)
+    d = g.uniform(0.3, 1.0, ops.n_edges(n_v, n_h))
+    M = (sp.diags(d) @ Lg).tocsr()
+    P = sp.csr_matrix(g.standard_normal((n, 2)))
+    As = [A, (A @ P).tocsr()]
+    Ms = [M, (M @ P).tocsr()]
+    dA = [np.asarray(X.multiply(X).sum(axis=0)).ravel() for X in As]
+    dM = [np.asarray(X.multiply(X).sum(axis=0)).ravel() for X in Ms]
+    h = pm.OneSided([(n, 1), (2, 1)], As, Ms, [P], dA, dM)
+    b = g.standard_normal(n)
+    z = pm.PaperVCycle(h, lam, nu1=2, nu2=1)(b)
+
+    K = (A.T @ A + lam * lam * (M.T @ M)).toarray()
+    Dinv = 1.0 / np.diag(K)
+    xs = np.linalg.solve(K, b)
+    # pre-relaxation: K-norm minimiser over the 2-dimensional Krylov space
+    v1 = Dinv * b
+    V = np.column_stack([v1, Dinv * (K @ v1)])
+    x = V @ np.linalg.solve(V.T @ K @ V, V.T @ K @ xs)
+    # exact coarse correction along P
+    Pd = P.toarray()
+    x = x + Pd @ np.linalg.solve(Pd.T @ K @ Pd, Pd.T @ (b - K @ x))
+    # one post-relaxation step: K-norm minimiser over x + span{D^-1 r}
+    w = Dinv * (b - K @ x)
+    x = x + (w @ (b - K @ x)) / (w @ K @ w) * w
+    assert np.linalg.norm(z - x) <= 1e-10 * np.linalg.norm(x)
