@@ -115,3 +115,26 @@ def test_warm_start_chain_equals_cold_solves():
         bound = 2.0 * np.linalg.cond(K) * prm.tol
         assert np.linalg.norm(xw - xc) / np.linalg.norm(xc) <= bound
         x_prev = xw
+
+
+def test_pcg_confirms_convergence_on_the_true_residual():
+    """A perturbation of x injected after an early step makes the recursive
+    residual drift from c - K x; convergence must still hold on the true
+    residual (the check at exit restarts from it)."""
+    import numpy as np
+    g = np.random.default_rng(3)
+    n = 30
+    Q = g.standard_normal((n, n))
+    K = Q @ Q.T + n * np.eye(n)
+    c = g.standard_normal(n)
+    hit = {"done": False}
+
+    def cb(x, r):
+        if not hit["done"]:
+            x += 1e-3 * g.standard_normal(n)     # x moves, the recursive r does not
+            hit["done"] = True
+
+    tol = 1e-10
+    x, it, st, rel = krylov.pcg(lambda v: K @ v, c, None, None, tol=tol, maxit=500, callback=cb)
+    assert hit["done"] and st == krylov.CONVERGED
+    assert np.linalg.norm(c - K @ x) <= tol * np.linalg.norm(c) * (1 + 1e-9)

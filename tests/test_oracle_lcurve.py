@@ -133,3 +133,16 @@ def test_should_stop_lx_stops_at_the_first_decrease():
     assert lcurve.should_stop_lx([5.0, 4.0])
     assert lcurve.should_stop([1, 2, 2, 2])
     assert not lcurve.should_stop([5, 5, 6, 6])
+
+
+def test_weight_update_uses_the_current_weights_by_hand():
+    """Eq. (g) on v = D^(l) L x: L x = (1, 0.8), D^(l) = diag(0.5, 1) give
+    v = (0.5, 0.8), g = (0.625, 1), d = (1 - 0.625^2, d_min) and
+    D^(l+1) = diag(d) D^(l) = (0.3046875, 0.001)."""
+    import numpy as np
+    from oracle import operators as ops
+    L = ops.gradient(3, 1)                       # two vertical edges
+    x = np.array([0.0, 1.0, 1.8])
+    assert np.allclose(L @ x, [1.0, 0.8])
+    d = lcurve.update_weights(np.array([0.5, 1.0]), L, x, q=2.0, d_min=1e-3)
+    assert np.allclose(d, [0.3046875, 1e-3], rtol=1e-15, atol=0)
