@@ -75,6 +75,9 @@ class OuterRecord:
     iters: np.ndarray
     status: np.ndarray
     selected: int          # 1-based index into the full lambda list
+    d: np.ndarray | None = None   # the weights D^(l) of this outer iteration
+    x: list | None = None         # the solutions, x[j] for lambda index lo + j
+    hier: object = None           # the hierarchy built for D^(l)
 
 
 @dataclass
@@ -113,7 +116,7 @@ def lcurve_run(problem, params: Params, rhs_index: int = 0, max_outer: int = 15,
         sel = lo + lcurve.corner(rho, eta)
         hist.append(sel)
         x_star = xs[sel - lo]
-        recs.append(OuterRecord((lo, hi), lam_all[lo - 1:hi], rho, eta, its, sts, sel))
+        recs.append(OuterRecord((lo, hi), lam_all[lo - 1:hi], rho, eta, its, sts, sel, d, xs, hier))
         lx.append(float(np.linalg.norm(S.L @ x_star)))
         if params.stop_rule == 1 and lcurve.should_stop_lx(lx):
             break
