@@ -132,6 +132,41 @@ def _edge_case_matrices():
         K[a, b] = K[b, a] = -1.0
     K[np.arange(n), np.arange(n)] = -K.sum(axis=1)
     yield "shuffled chain", sp.csr_matrix(K)
+    for name, K, _, _ in _HAND_WORKED:
+        yield name, sp.csr_matrix(K)
+
+
+# Strength counts only negative couplings, and a coupling exactly at the
+# threshold is weak.  In both matrices each end point then depends strongly
+# on the middle point alone, the middle point on both ends: the first pass
+# takes the middle point (measure 2) and its two dependants become F.  Each F
+# point interpolates from the middle point, its other neighbour (weak, F)
+# lumped into the diagonal: -(-1)/(6 + 5) and -(-4)/(6 - 1).
+_HAND_WORKED = [
+    ("large positive coupling",
+     np.array([[6.0, -1.0, 5.0], [-1.0, 2.0, -1.0], [5.0, -1.0, 6.0]]),
+     [0, 1, 0], np.array([[1.0 / 11.0], [1.0], [1.0 / 11.0]])),
+    ("coupling at the threshold",
+     np.array([[6.0, -4.0, -1.0], [-4.0, 9.0, -4.0], [-1.0, -4.0, 6.0]]),
+     [0, 1, 0], np.array([[0.8], [1.0], [0.8]])),
+]
+
+
+@pytest.mark.parametrize("name,K,cf_hand,P_hand", _HAND_WORKED, ids=[c[0] for c in _HAND_WORKED])
+def test_rs_strength_cases_worked_by_hand(name, K, cf_hand, P_hand):
+    """Sec. 3.1's strength test, the first pass and the interpolation
+    formula on two 3x3 matrices worked by hand: the oracle and the host
+    library give the split and the weights above."""
+    import scipy.sparse as sp
+    from oracle import amg
+    Ks = sp.csr_matrix(K)
+    cf_ref, S = amg.split(Ks)
+    assert list(cf_ref) == cf_hand
+    assert np.allclose(amg.interpolation(Ks, S, cf_ref).toarray(), P_hand, rtol=1e-15, atol=0)
+    cf = L.lcmg_rs_split(Ks)
+    assert list(cf) == cf_hand
+    rp, ci, v, nc = L.lcmg_rs_interp(Ks, cf)
+    assert np.allclose(sp.csr_matrix((v, ci, rp), shape=(3, nc)).toarray(), P_hand, rtol=1e-15, atol=0)
 
 
 @pytest.mark.parametrize("name,K", list(_edge_case_matrices()), ids=lambda v: v if isinstance(v, str) else "")
