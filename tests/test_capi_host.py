@@ -52,6 +52,22 @@ def test_corner_matches_oracle_random_curves():
         assert L.lcmg_lcurve_corner(rho, eta) == lcurve.corner(rho, eta), trial
 
 
+@pytest.mark.parametrize("eps", [0.0, 1e-15, -1e-15])
+def test_corner_ties_go_to_the_smaller_lambda(eps):
+    """A staircase in (log rho, log eta) with two identical corners, one of
+    them moved by a relative 1e-15 either way: curvatures within a relative
+    1e-12 are a tie, and a tie goes to the smaller lambda (index 1), in the
+    library as in the oracle."""
+    from oracle import lcurve
+    u = np.array([0.0, 0.0, 1.0, 1.0 + eps, 2.0])
+    v = np.array([2.0, 1.0, 1.0, 0.0, 0.0])
+    rho, eta = 10.0 ** u, 10.0 ** v
+    kap = lcurve.menger_curvature(rho, eta)
+    assert abs(kap[3] - kap[1]) <= 1e-12 * kap[1]
+    assert lcurve.corner(rho, eta) == 1
+    assert L.lcmg_lcurve_corner(rho, eta) == 1
+
+
 def test_corner_argument_errors():
     with pytest.raises(L.LcmgError) as e:
         L.lcmg_lcurve_corner([1.0, 2.0], [2.0, 1.0])
