@@ -428,8 +428,8 @@ def main():
     mode = L.MODE_SEQUENTIAL if args.mode == "sequential" else L.MODE_BATCHED
     max_outer = P.meta.get("max_outer", 15)
 
-    def make_solver(precision, timing):
-        s = L.Solver(P.n_v, P.n_h, device=local, stream=stream, precision=precision, mode=mode, nu=NU,
+    def make_solver(precision, timing, md=mode):
+        s = L.Solver(P.n_v, P.n_h, device=local, stream=stream, precision=precision, mode=md, nu=NU,
                      tol=1e-6, maxit=10000, timing=timing)
         s.set_forward_csr(P.A)
         return s
@@ -498,7 +498,7 @@ def main():
     # ---------------- plain FP64 one-lambda-at-a-time comparison ----------
     plain = None
     if not args.no_plain and rank == 0:
-        ps = make_solver(L.PREC_FP64, 0)
+        ps = make_solver(L.PREC_FP64, 0, L.MODE_SEQUENTIAL)
         L.lcmg_lcurve_run_dev(ps.ctx, P.lambdas, b_dev, max_outer, x_dev)  # warm-up
         t1 = time.perf_counter()
         rp = L.lcmg_lcurve_run_dev(ps.ctx, P.lambdas, b_dev, max_outer, x_dev)
@@ -512,11 +512,12 @@ def main():
     peak, peak_kind = measured_hbm_peak()
     achieved = (op_bytes / (op_ms / 1e3) / 1e9) if op_ms > 0 else None
     roofline = {
-        "kernel": ("k_spmv1 (the one-column SpMV, both operator passes: y = A p with int32 columns, then "
-                   "q = A^T y + lam^2 L^T W L p with p.q and 16-bit column offsets)"),
+        "kernel": (("k_spmv1 (the one-column SpMV, both operator passes: y = A p with int32 columns, then "
+                    "q = A^T y + lam^2 L^T W L p with p.q and 16-bit column offsets)") if mode == L.MODE_SEQUENTIAL
+                   else "k_spmm (the batched SpMM, both operator passes over the active columns)"),
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
         "frac": (achieved / peak) if achieved else None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-        "traffic": recorded_traffic(),
+        "traffic": recorded_traffic() if mode == L.MODE_SEQUENTIAL else None,
         "algorithmic_bytes_per_pass": (op_bytes / op_launches) if op_launches else None,
         "avg_pass_us": (op_ms * 1e3 / op_launches) if op_launches else None,
         "avg_us_A": (op_ms_a * 2e3 / op_launches) if op_launches else None,
