@@ -250,3 +250,23 @@ def test_pmis_invariants_on_random_weights(seed):
     assert len(Ps) >= 2
     for P in Ps:
         assert np.abs(P @ np.ones(P.shape[1]) - 1.0).max() <= 1e-13
+
+
+@pytest.mark.parametrize("n,S,expected", [
+    # |S^T| = (0, 2, 1): point 1 wins, and 0 and 2 depend on it.
+    (3, [[1, 2], [], [1]], [amg.F_PT, amg.C_PT, amg.F_PT]),
+    # |S^T| = (1, 2, 0, 2, 1).  Round 1: 3 beats 1 (equal measure, larger
+    # index) and 2; 0 loses to its dependant 4 (equal measure, larger
+    # index); 1 and 2 depend on 3 and become F.  Round 2: 4 beats 0.
+    # Round 3: 0 has no unsorted neighbour left and becomes C.
+    (5, [[], [3, 4], [3], [1], [0, 1]], [amg.C_PT, amg.F_PT, amg.F_PT, amg.C_PT, amg.C_PT]),
+    # two mutually strong points of equal measure: the larger index is C
+    (2, [[1], [0]], [amg.F_PT, amg.C_PT]),
+])
+def test_pmis_asymmetric_strength_by_hand(n, S, expected):
+    """PMIS with zero random parts, worked by hand: the measure is |S_i^T|
+    (not |S_i|), a point competes with every unsorted point it is strongly
+    connected to in either direction, (measure, index) pairs compare with
+    ties to the larger index, and a point becomes F through its own strong
+    connections S_i to a new C point."""
+    assert amg.pmis_split(S, n, np.zeros(n)).tolist() == expected
