@@ -270,3 +270,29 @@ def test_pmis_asymmetric_strength_by_hand(n, S, expected):
     ties to the larger index, and a point becomes F through its own strong
     connections S_i to a new C point."""
     assert amg.pmis_split(S, n, np.zeros(n)).tolist() == expected
+
+
+def test_hierarchy_limits_and_pmis_seeds():
+    """The hierarchy's stated stopping rules and seeds: coarsening stops at
+    max_levels levels and at a level of at most max_coarse points (a level
+    of exactly max_coarse points is not split); with PMIS, level k draws its
+    random parts from the SplitMix64 stream seeded with 2306 + k."""
+    K = mg.weighted_laplacian(ops.gradient(24, 20), pg.random_weights(ops.n_edges(24, 20), 5)) \
+        + sp.identity(480) * 1e-3
+    n = K.shape[0]
+    for L in (1, 2, 3):
+        Ks, Ps, _ = amg.hierarchy(K, max_levels=L, max_coarse=2)
+        assert len(Ks) == L and len(Ps) == L - 1
+    assert len(amg.hierarchy(K, max_coarse=n)[0]) == 1
+    Ks, _, _ = amg.hierarchy(K, max_coarse=n - 1, max_levels=2)
+    assert len(Ks) == 2
+    m1 = Ks[1].shape[0]
+    assert len(amg.hierarchy(K, max_coarse=m1, max_levels=3)[0]) == 2
+    assert len(amg.hierarchy(K, max_coarse=m1 - 1, max_levels=3)[0]) == 3
+    Ks, Ps, cfs = amg.hierarchy(K, max_levels=3, max_coarse=2, method="pmis")
+    assert amg.PMIS_SEED == 2306
+    for k in range(2):
+        S = amg.strength(Ks[k])
+        nk = Ks[k].shape[0]
+        assert np.array_equal(cfs[k], amg.pmis_split(S, nk, amg.splitmix64_uniform(2306 + k, nk)))
+        assert not np.array_equal(cfs[k], amg.pmis_split(S, nk, amg.splitmix64_uniform(2306 + k + 1, nk)))
