@@ -162,13 +162,18 @@ def test_interpolation_against_a_hand_computed_row():
     assert P[0, 1] == 0.0 and P[1, 0] == 1.0 and P[3, 1] == 1.0
 
 
-def test_one_sided_amg_hierarchy_is_the_galerkin_hierarchy():
+@pytest.mark.parametrize("method", ["rs", "pmis"])
+def test_one_sided_amg_hierarchy_is_the_galerkin_hierarchy(method):
+    """A_k^T A_k and M_k^T M_k of the one-sided products are the Galerkin
+    hierarchies of A^T A and L^T D^2 L, and the level diagonals dA, dM
+    (Sec. 3.2, column sums of squares) are their diagonals, from dense
+    products."""
     n_v, n_h = 16, 12
     A = pg.blur_csr(n_v, n_h, pg.gaussian_psf(2, 1.0)).to_scipy()
     Lg = ops.gradient(n_v, n_h)
     d = pg.random_weights(ops.n_edges(n_v, n_h), 8, d_min=0.05)
-    h = pm.build_one_sided_amg(A, Lg, d, max_coarse=24)
-    Ks, Ps, _ = amg.hierarchy(mg.weighted_laplacian(Lg, d), max_coarse=24)
+    h = pm.build_one_sided_amg(A, Lg, d, max_coarse=24, method=method)
+    Ks, Ps, _ = amg.hierarchy(mg.weighted_laplacian(Lg, d), max_coarse=24, method=method)
     assert len(h.A) == len(Ks) >= 3
     G = (A.T @ A).tocsr()
     for k in range(len(Ks)):
@@ -177,6 +182,8 @@ def test_one_sided_amg_hierarchy_is_the_galerkin_hierarchy():
         assert np.abs(AtA - G.toarray()).max() <= 1e-13 * np.abs(AtA).max()
         assert np.abs(MtM - Ks[k].toarray()).max() <= 1e-12 * np.abs(MtM).max()
         assert np.allclose(h.dM[k], Ks[k].diagonal(), rtol=1e-12, atol=0)
+        assert np.allclose(h.dA[k], np.diag(AtA), rtol=1e-12, atol=0)
+        assert np.allclose(h.dM[k], np.diag(MtM), rtol=1e-12, atol=0)
         if k < len(Ps):
             G = (Ps[k].T @ G @ Ps[k]).tocsr()
 
@@ -296,3 +303,26 @@ def test_hierarchy_limits_and_pmis_seeds():
         nk = Ks[k].shape[0]
         assert np.array_equal(cfs[k], amg.pmis_split(S, nk, amg.splitmix64_uniform(2306 + k, nk)))
         assert not np.array_equal(cfs[k], amg.pmis_split(S, nk, amg.splitmix64_uniform(2306 + k + 1, nk)))
+
+
+def test_paper_solver_coarsening_selects_the_split():
+    """solve(coarsening="pmis") is FGMRES on the hierarchy built with the
+    PMIS split, and "amg" on the one built with the two passes (replayed
+    bit for bit); on this problem the two splits differ."""
+    n = 16
+    A = pg.blur_csr(n, n, pg.gaussian_psf(2, 1.0)).to_scipy()
+    Lg = ops.gradient(n, n)
+    d = pg.random_weights(ops.n_edges(n, n), 5, d_min=0.05)
+    F = ops.ForwardCSR(A)
+    c = ops.rhs(F, pg.rng(4).standard_normal(A.shape[0]))
+    lam = 0.3
+    hs = {}
+    for coarsening, method in (("amg", "rs"), ("pmis", "pmis")):
+        h = pm.build_one_sided_amg(A, Lg, d, 20, 32, method)
+        V = pm.PaperVCycle(h, lam, 2, 1)
+        ref = pm.fgmres(lambda v: V.K(0, v), c, None, V, 1e-10, 500, 200, "mgs")
+        out = pm.solve(F, Lg, d, n, n, 20, c, lam, tol=1e-10, maxit=500, coarsening=coarsening, max_coarse=32)
+        assert np.array_equal(out[0], ref[0]) and out[1] == ref[1]
+        hs[method] = h
+    assert [a.shape for a in hs["rs"].A] != [a.shape for a in hs["pmis"].A] or \
+        any((a != b).nnz for a, b in zip(hs["rs"].A, hs["pmis"].A))
