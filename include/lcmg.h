@@ -94,35 +94,12 @@ typedef struct {
   double tol;           /* relative normal-equations residual (default 1e-6)         */
   int32_t maxit;        /* PCG iteration limit per system (default 10000)            */
   int32_t precision;    /* lcmg_precision (default FP64)                             */
-  int32_t mode;         /* lcmg_mode (default batched)                               */
+  int32_t mode;         /* lcmg_mode (default sequential: the paper's chain)          */
   int32_t check_every;  /* device iterations between host convergence polls (16)     */
   int32_t graphs;       /* 1 = replay each block of check_every iterations as one CUDA
                            graph (default), 0 = launch kernels one by one            */
   int32_t timing;       /* 1 = time the operator passes with CUDA events (see
                            lcmg_stats); default 0                                     */
-  int32_t fused;        /* 1 = run everything of a PCG iteration between the two
-                           operator passes (alpha, x/r update, the whole V-cycle,
-                           beta, p update) as one kernel on one thread-block
-                           cluster when the GPU supports it; 2 = the same with
-                           L2-only loads of data written within the kernel;
-                           0 = one kernel per step (default)                        */
-  int32_t tail_points;  /* levels whose points x columns are at most this run their
-                           whole V-cycle part (down to the coarsest solve and back)
-                           in one launch: one CTA or one cluster (tail_ctas);
-                           0 = off (default)                                        */
-  int32_t pdl;          /* 1 = launch the kernels of the PCG iteration with
-                           programmatic dependent launch, so each kernel is
-                           scheduled while its predecessor drains; 0 = plain
-                           stream order (default: no gain measured on GB300)        */
-  int32_t fold;         /* 1 = compute alpha and beta in the last block of the
-                           kernels that produce their dot products; 0 = separate
-                           one-block scalar kernels (default: the fold lengthens
-                           the A^T pass by more than the kernel it saves)       */
-  int32_t staged;       /* 1 = stream the CSR matrix of A and A^T through shared
-                           memory with bulk asynchronous copies (cp.async.bulk,
-                           mbarrier ring of 3 stages) so the HBM stream does not
-                           wait on the vector gathers; 0 = direct warp-per-row
-                           loads (default)                                       */
   int32_t vfuse;        /* run each V-cycle level (nu = 1 or 2) as two kernels on
                            8 x 8 coarse-point tiles held in shared memory: pre-
                            smoothing + residual + restriction, then prolongation +
@@ -195,13 +172,6 @@ typedef struct {
                            limit / breakdown decision and applies
                            beta = r.z_new / r.z (default); 0 = a scalar kernel
                            computes beta first                             */
-  int32_t tail_ctas;    /* with tail_points > 0: run the tail levels in one
-                           CTA (1, default) or in one thread-block cluster of
-                           up to this many CTAs (2..16; the largest power of
-                           two that fits on the device), the points of each
-                           level strided over the whole cluster and the steps
-                           separated by cluster barriers; combines with the
-                           two-kernels-per-level V-cycle (vfuse)            */
   int32_t spmv_variant_at; /* configuration of the transposed pass alone (0 =
                            as spmv_variant; 1..6 as there)                  */
 } lcmg_params;
@@ -396,7 +366,6 @@ typedef struct {
   double op_ms_at;
   int64_t op_launches;
   int64_t op_bytes;
-  int32_t fused_ctas;   /* CTAs of the cluster running the fused iteration, 0 if unused */
   int32_t tuned_spmv_a, tuned_spmv_at;  /* SpMV configuration of the passes
                            (params.spmv_variant numbering: 1 = 32 lanes x 4,
                            2 = 16 x 8, 3 = 8 x 8, 4-6 the register-bounded

@@ -17,13 +17,9 @@
 #include <vector>
 
 #include "launch.h"
-#include "spmm_staged.cuh"
 #include "vfused.cuh"
 #include "paper_mg.cuh"
 #include "rs_amg.h"
-#include "mega.cuh"
-#include "tail.cuh"
-#include "tail_launch.h"
 #include "lcmg.h"
 
 namespace lcmg {
@@ -135,11 +131,6 @@ struct lcmg_ctx {
   DevBuf<int32_t> ci, ciT;
   DevBuf<float> v32, vT32;
   DevBuf<double> v64, vT64;
-  // row chunks of A and A^T for the shared-memory-staged SpMM
-  DevBuf<int32_t> ck_row, ckT_row;
-  DevBuf<int64_t> ck_nz, ckT_nz;
-  int64_t nck = 0, nckT = 0;
-  DevBuf<int> spmm_err;  // set by a staged SpMM whose stage wait gave up
   // 16-bit column offsets from a per-row base (A and A^T), when every row's
   // column span fits: read by the one-column SpMV
   DevBuf<uint16_t> c16, c16T;
@@ -178,11 +169,10 @@ struct lcmg_ctx {
   DevBuf<double> lam2;
   DevBuf<char> lam2T;
   DevBuf<double> kinv, Mw, Ww;
-  DevBuf<double> part_pq, part_rr, part_rz, part_x, mega_part;
+  DevBuf<double> part_pq, part_rr, part_rz, part_x;
   DevBuf<double> s_rz, s_rz2, s_alpha, s_beta, s_rr, s_rmax, s_tol2cc, s_cc, s_rrtrue, s_out;
   DevBuf<int> s_active, s_iters, s_status, s_pending, s_counters, s_info, s_flag;
   DevBuf<double*> colptr;
-  DevBuf<int> tickets;  // last-block tickets of the folded scalar updates (kept at zero)
   DevBuf<int> colmap;
   int* h_counters = nullptr;  // pinned
   // weight-update scratch
@@ -220,53 +210,13 @@ static SpmmArgs csr_args(const lcmg_ctx& c, bool trans, int ld) {
   a.rp = trans ? c.rpT.p : c.rp.p;
   a.ci = trans ? c.ciT.p : c.ci.p;
   a.B = ld; a.c0 = 0; a.nb = ld; a.nl = 1; a.nrhs = 1;
-  if (c.c16_ok && c.prm.compact_cols && !c.prm.staged) {
+  if (c.c16_ok && c.prm.compact_cols) {
     a.c16 = trans ? c.c16T.p : c.c16.p;
     a.rbase = trans ? c.rbaseT.p : c.rbase.p;
-  }
-  if (c.prm.staged) {
-    a.ck_row = trans ? c.ckT_row.p : c.ck_row.p;
-    a.ck_nz = trans ? c.ckT_nz.p : c.ck_nz.p;
-    a.nck = trans ? c.nckT : c.nck;
-    a.err = c.spmm_err.p;
   }
   return a;
 }
 
-// Raise if a staged SpMM reported a stage wait that gave up (and clear it).
-static void check_spmm_err(lcmg_ctx& c) {
-  if (!c.prm.staged || c.fwd != 1) return;
-  int e = 0;
-  LCMG_CUDA(cudaMemcpyAsync(&e, c.spmm_err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-  LCMG_CUDA(cudaStreamSynchronize(c.stream));
-  if (e != 0) {
-    LCMG_CUDA(cudaMemsetAsync(c.spmm_err.p, 0, sizeof(int), c.stream));
-    throw CudaError("staged SpMM: a shared-memory stage was not filled within its wait limit");
-  }
-}
-
-// Chunks of consecutive rows with at most kChunkNnz nonzeros and at most
-// kChunkRows rows; a row with more than kChunkNnz nonzeros is its own chunk.
-static int64_t build_chunks(const int64_t* rp, int64_t rows, DevBuf<int32_t>& d_row, DevBuf<int64_t>& d_nz,
-                            cudaStream_t s) {
-  std::vector<int32_t> row;
-  std::vector<int64_t> nz;
-  int64_t r = 0;
-  while (r < rows) {
-    row.push_back((int32_t)r);
-    nz.push_back(rp[r]);
-    int64_t e = r + 1;
-    if (rp[r + 1] - rp[r] <= kChunkNnz)
-      while (e < rows && e - r < kChunkRows && rp[e + 1] - rp[r] <= kChunkNnz) ++e;
-    r = e;
-  }
-  row.push_back((int32_t)rows);
-  nz.push_back(rp[rows]);
-  const int64_t nck = (int64_t)row.size() - 1;
-  copy_sync(s, d_row.need(row.size()), row.data(), sizeof(int32_t) * row.size(), cudaMemcpyHostToDevice);
-  copy_sync(s, d_nz.need(nz.size()), nz.data(), sizeof(int64_t) * nz.size(), cudaMemcpyHostToDevice);
-  return nck;
-}
 // for entry points defined in other translation units
 void set_error_message(const std::string& s) { g_err = s; }
 
@@ -279,11 +229,6 @@ static void check_params(const lcmg_params& p) {
   if (p.precision != LCMG_PREC_FP64 && p.precision != LCMG_PREC_MIXED) throw ArgError("invalid precision");
   if (p.mode != LCMG_MODE_BATCHED && p.mode != LCMG_MODE_SEQUENTIAL) throw ArgError("invalid mode");
   if (p.check_every < 1) throw ArgError("check_every must be >= 1");
-  if (p.fused < 0 || p.fused > 2) throw ArgError("fused must be 0, 1 or 2");
-  if (p.tail_points < 0) throw ArgError("tail_points must be >= 0");
-  if (p.pdl != 0 && p.pdl != 1) throw ArgError("pdl must be 0 or 1");
-  if (p.fold != 0 && p.fold != 1) throw ArgError("fold must be 0 or 1");
-  if (p.staged != 0 && p.staged != 1) throw ArgError("staged must be 0 or 1");
   if (p.vfuse < 0 || p.vfuse > 2) throw ArgError("vfuse must be 0, 1 or 2");
   if (p.keep_direction != 0 && p.keep_direction != 1) throw ArgError("keep_direction must be 0 or 1");
   if (p.autotune != 0 && p.autotune != 1) throw ArgError("autotune must be 0 or 1");
@@ -296,7 +241,6 @@ static void check_params(const lcmg_params& p) {
   if (p.compact_cols != 0 && p.compact_cols != 1) throw ArgError("compact_cols must be 0 or 1");
   if (p.alpha_fuse != 0 && p.alpha_fuse != 1) throw ArgError("alpha_fuse must be 0 or 1");
   if (p.beta_fuse != 0 && p.beta_fuse != 1) throw ArgError("beta_fuse must be 0 or 1");
-  if (p.tail_ctas < 1 || p.tail_ctas > 16) throw ArgError("tail_ctas must be 1..16");
   if (p.amg_coarse_max < 2 || p.amg_coarse_max > 2048) throw ArgError("amg_coarse_max must be 2..2048");
 }
 
@@ -414,15 +358,10 @@ static void ensure_work(lcmg_ctx& c, int B) {
   c.lam2.need(B); c.lam2T.need(B * tb);
   const size_t pb = (size_t)kMaxBlocks * B;
   c.part_pq.need(pb); c.part_rr.need(pb); c.part_rz.need(pb); c.part_x.need(pb);
-  c.mega_part.need((size_t)kMegaMaxCtas * 2 * kMaxB);
   for (auto* b : {&c.s_rz, &c.s_rz2, &c.s_alpha, &c.s_beta, &c.s_rr, &c.s_rmax, &c.s_tol2cc, &c.s_cc, &c.s_rrtrue, &c.s_out})
     b->need(B);
   for (auto* b : {&c.s_active, &c.s_iters, &c.s_status, &c.s_pending, &c.s_info, &c.s_flag}) b->need(B);
   c.s_counters.need(4);
-  if (!c.tickets.p) {
-    c.tickets.need(4);
-    fill_sync(c.stream, c.tickets.p, 0, 4 * sizeof(int));
-  }
   if (!c.h_counters) LCMG_CUDA(cudaMallocHost(&c.h_counters, 4 * sizeof(int)));
   c.Bcap = std::max(c.Bcap, B);
 }
@@ -432,8 +371,7 @@ static ColState colstate(lcmg_ctx& c) {
   s.rz = c.s_rz.p; s.rz2 = c.s_rz2.p; s.alpha = c.s_alpha.p; s.beta = c.s_beta.p; s.rr = c.s_rr.p; s.rmax = c.s_rmax.p;
   s.tol2cc = c.s_tol2cc.p; s.active = c.s_active.p; s.iters = c.s_iters.p; s.status = c.s_status.p;
   s.pending = c.s_pending.p; s.counters = c.s_counters.p;
-  // the one-cluster iteration kernel restarts failed columns itself
-  s.keep = (c.prm.keep_direction && !c.prm.fused) ? 1 : 0;
+  s.keep = c.prm.keep_direction ? 1 : 0;
   return s;
 }
 
@@ -479,7 +417,7 @@ struct Batch {
   const T* psfT();
 
   // q = K p (T precision) with partials of p.q; returns the partial count
-  int apply_K(const T* P, T* Q, double* part, const ScalarFold* fold = nullptr, bool* folded = nullptr);
+  int apply_K(const T* P, T* Q, double* part);
 
   // ---- live timing of the operator passes (params.timing) ------------
   // Only the first iteration of each block of check_every iterations is
@@ -520,11 +458,8 @@ struct Batch {
 
   // ---- V-cycle (Algorithm 1, gamma = 1, zero initial guess) ----------
   // m Jacobi sweeps z <- z + D^{-1}(rhs - K z), ending in z; with part the
-  // r.z partials of the result, and with fold (even m only) the beta update
-  // in the last sweep's last block (*folded reports whether it happened)
-  void sweeps(int k, int m, const T* rhs, T* z, T* t, double* part, int* nb_out,
-              const ScalarFold* fold = nullptr, bool* folded = nullptr) {
-    if (folded) *folded = false;
+  // r.z partials of the result
+  void sweeps(int k, int m, const T* rhs, T* z, T* t, double* part, int* nb_out) {
     if (m <= 0) return;
     LevelView<T> L = view<T>(c, k);
     const T* dinv = tp(c.lw[k].dinv);
@@ -534,8 +469,7 @@ struct Batch {
       const bool last = (i == m - 1);
       const bool with_dot = last && (m % 2 == 0);
       int nb = launch_smooth<T>(L, B, lam2T(), dinv, rhs, a, b, nullptr, with_dot ? part : nullptr,
-                                c.maxblk, s, (with_dot && part) ? fold : nullptr);
-      if (with_dot && part && fold && folded) *folded = true;
+                                c.maxblk, s);
       if (last && (m % 2 == 0) && nb_out) *nb_out = nb;
       std::swap(a, b);
     }
@@ -550,40 +484,7 @@ struct Batch {
     }
   }
 
-  // first level (>= 1) whose points x columns fit the one-CTA tail, else nlev
-  int tail_level() const {
-    if (c.prm.tail_points <= 0 || nlev < 2) return nlev;
-    for (int k = 1; k < nlev; ++k)
-      if (c.lev[k].n * B <= c.prm.tail_points && nlev - k <= kTailMaxLevels) return k;
-    return nlev;
-  }
-
-  // the tail on levels k0 .. nlev-1 (input lw[k0].rhs, output lw[k0].z)
-  void tail(int k0) {
-    TailArgs<T> ta{};
-    ta.B = B;
-    ta.nl = nlev - k0;
-    ta.nu = c.prm.nu;
-    ta.nc = (int)c.lev[nlev - 1].n;
-    ta.kinv = c.kinv.p;
-    ta.lam2T = lam2T();
-    for (int k = k0; k < nlev; ++k) {
-      TailLevel<T>& t = ta.lev[k - k0];
-      t.nv = c.lev[k].nv;
-      t.nh = c.lev[k].nh;
-      t.n = c.lev[k].n;
-      t.cf = view<T>(c, k).cf;
-      t.dinv = tp(c.lw[k].dinv);
-      t.rhs = tp(c.lw[k].rhs);
-      t.z = tp(c.lw[k].z);
-      t.t = tp(c.lw[k].t);
-      t.res = tp(c.lw[k].res);
-    }
-    launch_vcycle_tail<T>(ta, tail_cluster_ctas<T>(c.prm.tail_ctas), s);
-  }
-
-  int vcycle(const T* r0, T* z0, double* part, const ScalarFold* fold = nullptr, bool* folded = nullptr) {
-    if (folded) *folded = false;
+  int vcycle(const T* r0, T* z0, double* part) {
     const int nu = c.prm.nu;
     int nb = 0;
     if (nlev == 1) {
@@ -601,28 +502,19 @@ struct Batch {
     const int64_t tiles0 = (int64_t)((c.lev[0].nv / 2 + kVTile - 1) / kVTile) * ((c.lev[0].nh / 2 + kVTile - 1) / kVTile);
     const bool vf = vf_force >= 0 ? vf_force == 1 : (c.prm.vfuse == 2 || (c.prm.vfuse == 1 && B <= kVfuseAutoB));
     if (vf && (nu == 1 || nu == 2) && tiles0 <= kMaxBlocks) {
-      // two kernels per level: pre-smoothed z of level k goes to t[k]; the
-      // levels from tail_level() down run in one tail launch
-      const int k0 = tail_level();
-      const int kdown = std::min(k0, nlev - 1);
-      for (int k = 0; k < kdown; ++k)
+      // two kernels per level: pre-smoothed z of level k goes to t[k]
+      for (int k = 0; k < nlev - 1; ++k)
         launch_vdown<T>(view<T>(c, k), B, lam2T(), tp(c.lw[k].dinv), rhs[k], tp(c.lw[k].t), tp(c.lw[k + 1].rhs),
                         nu, s);
-      if (k0 < nlev)
-        tail(k0);
-      else
-        launch_coarse_solve<T>((int)c.lev[nlev - 1].n, B, c.kinv.p, rhs[nlev - 1], zz[nlev - 1], s);
-      for (int k = kdown - 1; k >= 0; --k) {
+      launch_coarse_solve<T>((int)c.lev[nlev - 1].n, B, c.kinv.p, rhs[nlev - 1], zz[nlev - 1], s);
+      for (int k = nlev - 2; k >= 0; --k) {
         const int g = launch_vup<T>(view<T>(c, k), B, lam2T(), tp(c.lw[k].dinv), rhs[k], zz[k + 1],
                                     tp(c.lw[k].t), zz[k], k == 0 ? part : nullptr, nu, s);
         if (k == 0) nb = g;
       }
       return nb;
     }
-    // levels k0 .. nlev-1 run in one CTA when they are small enough
-    const int k0 = tail_level();
-    const int kstop = (k0 < nlev) ? k0 : nlev - 1;
-    for (int k = 0; k < kstop; ++k) {
+    for (int k = 0; k < nlev - 1; ++k) {
       LevelView<T> L = view<T>(c, k);
       const T* dinv = tp(c.lw[k].dinv);
       launch_smooth_zero<T>(L, B, lam2T(), dinv, rhs[k], zz[k], nu >= 2 ? 1 : 0, c.maxblk, s);
@@ -630,15 +522,10 @@ struct Batch {
       launch_residual<T>(L, B, lam2T(), rhs[k], zz[k], tp(c.lw[k].res), c.maxblk, s);
       launch_restrict<T>(c.lev[k + 1].nv, c.lev[k + 1].nh, B, tp(c.lw[k].res), tp(c.lw[k + 1].rhs), c.maxblk, s);
     }
-    if (k0 < nlev) {
-      tail(k0);
-    } else {
-      launch_coarse_solve<T>((int)c.lev[nlev - 1].n, B, c.kinv.p, rhs[nlev - 1], zz[nlev - 1], s);
-    }
-    for (int k = kstop - 1; k >= 0; --k) {
+    launch_coarse_solve<T>((int)c.lev[nlev - 1].n, B, c.kinv.p, rhs[nlev - 1], zz[nlev - 1], s);
+    for (int k = nlev - 2; k >= 0; --k) {
       launch_prolong_add<T>(c.lev[k + 1].nv, c.lev[k + 1].nh, B, zz[k + 1], zz[k], c.maxblk, s);
-      sweeps(k, nu, rhs[k], zz[k], tp(c.lw[k].t), k == 0 ? part : nullptr, k == 0 ? &nb : nullptr,
-             k == 0 ? fold : nullptr, k == 0 ? folded : nullptr);
+      sweeps(k, nu, rhs[k], zz[k], tp(c.lw[k].t), k == 0 ? part : nullptr, k == 0 ? &nb : nullptr);
     }
     return nb;
   }
@@ -666,49 +553,6 @@ struct Batch {
     LCMG_CUDA(cudaStreamSynchronize(s));
   }
 
-  // the one-cluster iteration kernel is used when enabled and supported
-  bool use_fused() const {
-    return c.prm.fused && nlev <= kMegaMaxLevels && mega_cluster_ctas<T>() > 0 &&
-           (int64_t)c.lev[nlev - 1].n <= 4096;
-  }
-
-  MegaArgs<T> mega_args(int nb_pq) {
-    MegaArgs<T> a{};
-    a.B = B;
-    a.nlev = nlev;
-    a.nu = c.prm.nu;
-    a.nc = (int)c.lev[nlev - 1].n;
-    for (int k = 0; k < nlev; ++k) {
-      LevelView<T> v = view<T>(c, k);
-      MegaLevel<T>& m = a.lev[k];
-      m.nv = v.nv;
-      m.nh = v.nh;
-      m.n = v.n;
-      m.fine = k == 0;
-      m.ws = v.ws;
-      m.we = v.we;
-      m.ga = v.ga;
-      m.cf = v.cf;
-      m.dinv = tp(c.lw[k].dinv);
-      m.rhs = k == 0 ? tp(c.r) : tp(c.lw[k].rhs);
-      m.z = k == 0 ? tp(c.z) : tp(c.lw[k].z);
-      m.t = tp(c.lw[k].t);
-      m.res = tp(c.lw[k].res);
-    }
-    a.kinv = c.kinv.p;
-    a.x = std::is_same<T, double>::value ? reinterpret_cast<T*>(c.x64.p) : reinterpret_cast<T*>(c.xlo.p);
-    a.p = tp(c.p);
-    a.q = tp(c.q);
-    a.lam2T = lam2T();
-    a.st = colstate(c);
-    a.pq_part = c.part_pq.p;
-    a.nblk_pq = nb_pq;
-    a.cta_part = c.mega_part.p;
-    a.maxit = c.prm.maxit;
-    a.rel_trigger = std::is_same<T, float>::value ? 0.01 : 0.0;
-    return a;
-  }
-
   // one PCG iteration for all active columns
   void iterate_once(bool time_it = false) {
     timing_now = time_it;
@@ -718,49 +562,25 @@ struct Batch {
     T* R = tp(c.r);
     T* Z = tp(c.z);
     const double trig = std::is_same<T, float>::value ? 0.01 : 0.0;  // ||r|| fell 10x since the last update
-    if (use_fused()) {
-      const int nb_pq = apply_K(P, Q, c.part_pq.p);
-      launch_pcg_mega<T>(mega_args(nb_pq), mega_cluster_ctas<T>(), c.prm.fused == 2, s);
-      c.stats.fused_ctas = mega_cluster_ctas<T>();
-      return;
-    }
-    // alpha in the last block of the A^T pass when the operator allows it
-    ScalarFold fa{};
-    fa.st = st;
-    fa.ticket = c.tickets.p;
-    bool alpha_folded = false;
-    const int nb_pq = apply_K(P, Q, c.part_pq.p, c.prm.fold ? &fa : nullptr, &alpha_folded);
+    const int nb_pq = apply_K(P, Q, c.part_pq.p);
     T* X = std::is_same<T, double>::value ? reinterpret_cast<T*>(c.x64.p) : reinterpret_cast<T*>(c.xlo.p);
     int nb_rr;
-    const bool alpha_fused = !alpha_folded && B == 1 && c.prm.alpha_fuse;
+    const bool alpha_fused = B == 1 && c.prm.alpha_fuse;
     if (alpha_fused) {  // alpha inside the update
       nb_rr = launch_update_xr_alpha<T, T>(c.n, st, nb_pq, c.part_pq.p, P, Q, X, R, c.part_rr.p, c.maxblk, s);
     } else {
-      if (!alpha_folded) {
-        klaunch(k_scalar_col_alpha, dim3(B), dim3(kColThreads), 0, s, B, nb_pq, c.part_pq.p, st);
-        LCMG_LAUNCHED();
-      }
+      klaunch(k_scalar_col_alpha, dim3(B), dim3(kColThreads), 0, s, B, nb_pq, c.part_pq.p, st);
+      LCMG_LAUNCHED();
       nb_rr = launch_update_xr<T, T>(c.n, B, st, P, Q, X, R, c.part_rr.p, c.maxblk, s);
     }
-    // beta in the last block of the final level-0 sweep when possible
-    ScalarFold fb{};
-    fb.st = st;
-    fb.ticket = c.tickets.p + 1;
-    fb.rr_part = c.part_rr.p;
-    fb.nblk_rr = nb_rr;
-    fb.maxit = c.prm.maxit;
-    fb.rel_trigger = trig;
-    bool beta_folded = false;
-    const int nb_rz = vcycle(R, Z, c.part_rz.p, c.prm.fold ? &fb : nullptr, &beta_folded);
-    if (!beta_folded && alpha_fused && c.prm.beta_fuse && !c.prm.keep_direction) {  // beta inside the p update
+    const int nb_rz = vcycle(R, Z, c.part_rz.p);
+    if (alpha_fused && c.prm.beta_fuse && !c.prm.keep_direction) {  // beta inside the p update
       launch_update_p_beta<T>(c.n, st, nb_rr, c.part_rr.p, nb_rz, c.part_rz.p, c.prm.maxit, trig, Z, P, c.maxblk, s);
       return;
     }
-    if (!beta_folded) {
-      klaunch(k_scalar_col_beta, dim3(B), dim3(kColThreads), 0, s, B, nb_rr, c.part_rr.p, nb_rz, c.part_rz.p, st,
-              c.prm.maxit, trig);
-      LCMG_LAUNCHED();
-    }
+    klaunch(k_scalar_col_beta, dim3(B), dim3(kColThreads), 0, s, B, nb_rr, c.part_rr.p, nb_rz, c.part_rz.p, st,
+            c.prm.maxit, trig);
+    LCMG_LAUNCHED();
     launch_update_p<T>(c.n, B, st, Z, P, c.maxblk, s);
   }
 
@@ -794,7 +614,7 @@ struct Batch {
   // forms on this context's operator and hierarchy (CUDA events, 3 runs
   // after one warm-up, on scratch vectors), keep the fastest per width.
   void autotune() {
-    if (!c.prm.autotune || c.tuned.count(tune_key()) || c.prm.fused) return;
+    if (!c.prm.autotune || c.tuned.count(tune_key())) return;
     Tuned t;
     LCMG_CUDA(cudaMemsetAsync(c.p.p, 0, sizeof(T) * c.n * B, s));
     LCMG_CUDA(cudaMemsetAsync(c.r.p, 0, sizeof(T) * c.n * B, s));
@@ -831,7 +651,7 @@ struct Batch {
       var_at = t.var_at;
     }
     const int nu = c.prm.nu;
-    if (nlev >= 2 && (nu == 1 || nu == 2) && c.prm.tail_points <= 0) {
+    if (nlev >= 2 && (nu == 1 || nu == 2)) {
       float best = 1e30f;
       for (int f = 0; f <= 1; ++f) {
         vf_force = f;
@@ -848,12 +668,6 @@ struct Batch {
   // Run PCG on the batch whose x64 (initial guesses) and c64 (right-hand
   // sides A^T b) are set.  Returns the number of batch iterations.
   int64_t run(const std::vector<double>& lam) {
-    // programmatic dependent launch for the kernels of this run
-    struct PdlScope {
-      bool prev;
-      explicit PdlScope(bool on) : prev(pdl_flag()) { pdl_flag() = on; }
-      ~PdlScope() { pdl_flag() = prev; }
-    } pdl_scope(c.prm.pdl == 1);
     setup(lam);
     autotune();
     c.stats.tuned_spmv_a = var_a;
@@ -982,7 +796,7 @@ static void op_bytes(const lcmg_ctx& c, int B, int64_t* first, int64_t* second) 
   if (c.fwd == 1) {
     const int64_t sV = (std::is_same<T, float>::value || c.vdtype == 0) ? 4 : 8;
     // the one-column transposed pass reads 16-bit column offsets and a base per row
-    const bool c16 = B == 1 && c.c16_ok && c.prm.compact_cols && !c.prm.staged;
+    const bool c16 = B == 1 && c.c16_ok && c.prm.compact_cols;
     *first = c.nnz * (sV + 4) + (c.m + 1) * 8 + c.n * sB * sT + c.m * sB * sT;
     *second = c.nnz * (sV + (c16 ? 2 : 4)) + (c.n + 1) * 8 + (c16 ? c.n * 4 : 0) + c.m * sB * sT +
               2 * c.n * sB * sT + 2 * c.n * sT + c.n * sB * sT;
@@ -993,8 +807,7 @@ static void op_bytes(const lcmg_ctx& c, int B, int64_t* first, int64_t* second) 
 }
 
 template <class T>
-int Batch<T>::apply_K(const T* P, T* Q, double* part, const ScalarFold* fold, bool* folded) {
-  if (folded) *folded = false;
+int Batch<T>::apply_K(const T* P, T* Q, double* part) {
   T* Y = tp(c.y);
   mark();
   int nb;
@@ -1011,7 +824,7 @@ int Batch<T>::apply_K(const T* P, T* Q, double* part, const ScalarFold* fold, bo
       nb = launch_spmm<float, float, float, 1>(at, c.vT32.p, reinterpret_cast<const float*>(Y),
                                                reinterpret_cast<float*>(Q), view<float>(c, 0).fine_op(),
                                                reinterpret_cast<const float*>(P), nullptr, c.lam2.p, nullptr,
-                                               part, c.maxblk, s, fold);
+                                               part, c.maxblk, s);
     } else {
       const double* Pd = reinterpret_cast<const double*>(P);
       double* Qd = reinterpret_cast<double*>(Q);
@@ -1021,16 +834,15 @@ int Batch<T>::apply_K(const T* P, T* Q, double* part, const ScalarFold* fold, bo
                                                nullptr, c.maxblk, s);
         mark();
         nb = launch_spmm<double, double, double, 1>(at, c.vT64.p, Yd, Qd, fop64(), Pd, nullptr, c.lam2.p,
-                                                    nullptr, part, c.maxblk, s, fold);
+                                                    nullptr, part, c.maxblk, s);
       } else {
         launch_spmm<float, double, double, 0>(a, c.v32.p, Pd, Yd, fop64(), nullptr, nullptr, nullptr, nullptr,
                                               nullptr, c.maxblk, s);
         mark();
         nb = launch_spmm<float, double, double, 1>(at, c.vT32.p, Yd, Qd, fop64(), Pd, nullptr, c.lam2.p,
-                                                   nullptr, part, c.maxblk, s, fold);
+                                                   nullptr, part, c.maxblk, s);
       }
     }
-    if (folded) *folded = fold != nullptr;
   } else {
     // PSF operator
     nb = grid_for(c.n, B, c.maxblk);
@@ -1708,7 +1520,6 @@ static void solve_columns(lcmg_ctx& c, const std::vector<ColSpec>& cols, int nrh
   LCMG_CUDA(cudaMemcpyAsync(hi.data(), c.s_iters.p, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
   LCMG_CUDA(cudaMemcpyAsync(hs.data(), c.s_status.p, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
   LCMG_CUDA(cudaStreamSynchronize(s));
-  check_spmm_err(c);
   for (int j = 0; j < B; ++j) {
     if (rho) rho[j] = std::sqrt(hr[j]);
     if (eta) eta[j] = std::sqrt(he[j]);
@@ -1977,15 +1788,10 @@ void lcmg_default_params(lcmg_params* p) {
   p->tol = 1e-6;
   p->maxit = 10000;
   p->precision = LCMG_PREC_FP64;
-  p->mode = LCMG_MODE_BATCHED;
+  p->mode = LCMG_MODE_SEQUENTIAL;
   p->check_every = 16;
   p->graphs = 1;
   p->timing = 0;
-  p->fused = 0;
-  p->tail_points = 0;
-  p->pdl = 0;
-  p->fold = 0;
-  p->staged = 0;
   p->vfuse = 1;
   p->keep_direction = 0;
   p->autotune = 0;
@@ -1998,7 +1804,6 @@ void lcmg_default_params(lcmg_params* p) {
   p->compact_cols = 1;
   p->alpha_fuse = 1;
   p->beta_fuse = 1;
-  p->tail_ctas = 1;
   p->spmv_variant_at = 0;
 }
 
@@ -2031,10 +1836,6 @@ int lcmg_create(lcmg_ctx** out, int device, void* stream, const lcmg_params* p) 
   LCMG_CUDA(cudaGetDeviceProperties(&prop, device));
   c->sms = prop.multiProcessorCount;
   c->maxblk = std::min(lcmg::kMaxBlocks, c->sms * 8);
-  lcmg::fill_sync(c->stream, c->spmm_err.need(1), 0, sizeof(int));
-  // opt the staged SpMM kernels into their shared memory here, outside any
-  // stream capture
-  lcmg::prepare_spmm_staged();
   *out = c;
   API_END
 }
@@ -2126,7 +1927,7 @@ int lcmg_set_forward_csr(lcmg_ctx* ctx, int64_t m, int64_t n, const int64_t* row
   ctx->nnz = nnz;
   ctx->vdtype = val_dtype;
   cudaStream_t s = ctx->stream;
-  // row pointers padded: a staged copy of rp may read one entry past rp[m]
+  // CSR arrays padded by kCsrPad elements (vector loads may run past the last row)
   lcmg::copy_sync(ctx->stream, ctx->rp.need(m + 1 + lcmg::kCsrPad), row_ptr, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice);
   lcmg::copy_sync(ctx->stream, ctx->ci.need(nnz + lcmg::kCsrPad), col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
   lcmg::copy_sync(ctx->stream, ctx->rpT.need(n + 1 + lcmg::kCsrPad), rpT.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
@@ -2183,8 +1984,6 @@ int lcmg_set_forward_csr(lcmg_ctx* ctx, int64_t m, int64_t n, const int64_t* row
     lcmg::fill_sync(ctx->stream, ctx->v64.p + nnz, 0, sizeof(double) * lcmg::kCsrPad);
     lcmg::fill_sync(ctx->stream, ctx->vT64.p + nnz, 0, sizeof(double) * lcmg::kCsrPad);
   }
-  ctx->nck = lcmg::build_chunks(row_ptr, m, ctx->ck_row, ctx->ck_nz, ctx->stream);
-  ctx->nckT = lcmg::build_chunks(rpT.data(), n, ctx->ckT_row, ctx->ckT_nz, ctx->stream);
   // diag(A^T A): sums of squares along the rows of A^T
   const int g = (int)std::min<int64_t>((n * 32 + lcmg::kBlock - 1) / lcmg::kBlock, ctx->maxblk);
   if (val_dtype == 1)
@@ -2532,7 +2331,6 @@ int lcmg_apply_normal_dev(lcmg_ctx* ctx, int32_t n_cols, const double* lambda, c
   klaunch(lcmg::k_inter_to_planar, dim3(g), dim3(lcmg::kBlock), 0, ctx->stream, ctx->n, B, ctx->r64.p, y_dev);
   LCMG_LAUNCHED();
   LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
-  lcmg::check_spmm_err(*ctx);
   API_END
 }
 

@@ -41,21 +41,6 @@ inline int64_t& launch_counter() {
     LCMG_CUDA(cudaGetLastError());       \
   } while (0)
 
-// Programmatic dependent launch.  Every kernel starts with pdl_entry():
-// it lets the next kernel of the stream be scheduled as soon as all of this
-// kernel's blocks have started, then waits until the previous kernel has
-// completed and its writes are visible.  Launched without the attribute
-// (klaunch with pdl_flag() false, or <<<>>>) both instructions are no-ops.
-__device__ __forceinline__ void pdl_entry() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
-inline bool& pdl_flag() {
-  static thread_local bool on = false;
-  return on;
-}
-
 constexpr int kBlock = 256;      // threads per block of the point x column kernels
 constexpr int kMaxB = 256;       // widest batch one launch handles
 constexpr int kStencil = 25;     // coarse-level stencils are 5 x 5
@@ -108,8 +93,7 @@ __device__ __forceinline__ float from_d<float>(double v) { return (float)v; }
 template <>
 __device__ __forceinline__ double from_d<double>(double v) { return v; }
 
-// Launch with the programmatic-serialization attribute when pdl_flag() is
-// set (the kernel must begin with pdl_entry()).
+// Launch kern on stream s (every launch of the library goes through here).
 template <typename... KArgs, typename... Args>
 inline void klaunch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                     Args... args) {
@@ -118,11 +102,6 @@ inline void klaunch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, 
   cfg.blockDim = block;
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = pdl_flag() ? 1 : 0;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
   LCMG_CUDA(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
 }
 

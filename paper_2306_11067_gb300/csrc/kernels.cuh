@@ -226,7 +226,6 @@ struct CoarseOp {
 template <class T>
 __global__ void k_coef_pack(int64_t n, const double* __restrict__ gl, const double* __restrict__ ga,
                             T* __restrict__ cf) {
-  pdl_entry();
   for (int64_t t = (int64_t)blockIdx.x * kBlock + threadIdx.x; t < n * kCoefStride;
        t += (int64_t)gridDim.x * kBlock) {
     const int64_t p = t / kCoefStride;
@@ -283,118 +282,6 @@ __device__ __forceinline__ void mark_pending(const ColState& st, int col, double
   }
 }
 
-// The scalar update folded into the producing kernel's last block.
-struct ScalarFold {
-  ColState st;
-  int* ticket;            // zero before the launch; the last block resets it
-  const double* rr_part;  // beta fold: ||r||^2 partials of the x/r update
-  int nblk_rr;
-  int maxit;
-  double rel_trigger;
-};
-
-// true in exactly one block of the grid, after every block's partials are
-// written and visible
-__device__ __forceinline__ bool last_block(int* ticket) {
-  __shared__ int is_last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int nb = (int)(gridDim.x * gridDim.y);
-    const int t = atomicAdd(ticket, 1);
-    is_last = (t == nb - 1);
-    if (is_last) *ticket = 0;
-  }
-  __syncthreads();
-  return is_last != 0;
-}
-
-// sum of a column's partials over nblk blocks by one warp (L2 loads:
-// written by other blocks of this launch)
-__device__ __forceinline__ double warp_sum_parts_cg(const double* part, int nblk, int B, int col) {
-  const int lane = threadIdx.x & 31;
-  double s = 0.0;
-  for (int b = lane; b < nblk; b += 32) s += __ldcg(part + (int64_t)b * B + col);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  return s;
-}
-
-// alpha = rz / p^T q for every column (one warp per column); also clears the
-// counters the beta update accumulates
-__device__ __forceinline__ void fold_alpha(const ColState& st, int B, const double* pq_part, int nblk) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (threadIdx.x < 3) st.counters[threadIdx.x] = 0;
-  for (int col = w; col < B; col += nw) {
-    if (!st.active[col]) {
-      if (lane == 0) st.alpha[col] = 0.0;
-      continue;
-    }
-    const double pq = warp_sum_parts_cg(pq_part, nblk, B, col);
-    if (lane != 0) continue;
-    st.iters[col] += 1;
-    if (!isfinite(pq)) {
-      st.status[col] = ST_NONFINITE;
-      st.active[col] = 0;
-      st.alpha[col] = 0.0;
-    } else if (!(pq > 0.0)) {
-      st.status[col] = ST_BREAKDOWN;
-      st.active[col] = 0;
-      st.alpha[col] = 0.0;
-    } else {
-      st.alpha[col] = st.rz[col] / pq;
-    }
-  }
-}
-
-// rr, recursive convergence and beta for every column (one warp per
-// column); counters by thread 0 after a block barrier
-__device__ __forceinline__ void fold_beta(const ScalarFold& f, int B, const double* rz_part, int nblk_rz) {
-  const ColState& st = f.st;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __shared__ int nvote;
-  if (threadIdx.x == 0) nvote = 0;
-  __syncthreads();
-  for (int col = w; col < B; col += nw) {
-    if (!st.active[col]) continue;
-    const double rr = warp_sum_parts_cg(f.rr_part, f.nblk_rr, B, col);
-    const double rzn = warp_sum_parts_cg(rz_part, nblk_rz, B, col);
-    if (lane != 0) continue;
-    st.rr[col] = rr;
-    if (!isfinite(rr) || !isfinite(rzn)) {
-      st.status[col] = ST_NONFINITE;
-      st.active[col] = 0;
-      st.beta[col] = 0.0;
-    } else if (rr <= st.tol2cc[col]) {
-      mark_pending(st, col, rzn);
-    } else if (st.iters[col] >= f.maxit) {
-      st.status[col] = ST_MAXIT;
-      st.active[col] = 0;
-      st.beta[col] = 0.0;
-    } else if (!(rzn > 0.0)) {
-      st.status[col] = ST_BREAKDOWN;
-      st.active[col] = 0;
-      st.beta[col] = 0.0;
-    } else {
-      st.beta[col] = rzn / st.rz[col];
-      st.rz[col] = rzn;
-      st.rz2[col] = rzn;
-      if (f.rel_trigger > 0.0 && rr < f.rel_trigger * st.rmax[col]) atomicAdd(&nvote, 1);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int na = 0, np = 0;
-    for (int col = 0; col < B; ++col) {
-      na += st.active[col];
-      np += st.pending[col];
-    }
-    st.counters[0] = na;
-    st.counters[1] = np;
-    st.counters[2] = nvote;
-  }
-}
-
 // ---------------------------------------------------------------------------
 // CSR SpMM over B interleaved columns.  One warp per row; the 32 lanes are
 // S = 32/G nnz-groups x G column groups of CPG columns each, so a lane
@@ -416,12 +303,6 @@ struct SpmmArgs {
   int nb;       // columns in [c0, c0 + nb) are handled
   int nl;       // MODE 2: lambdas per right-hand side (b column = col / nl)
   int nrhs;     // MODE 2: columns of b
-  // row chunks for the shared-memory-staged kernel (k_spmm_staged); null
-  // selects the direct kernel
-  const int32_t* ck_row;  // nck + 1 first rows
-  const int64_t* ck_nz;   // nck + 1 first nonzeros (rp[ck_row[c]])
-  int64_t nck;
-  int* err;               // set to 1 when a staging wait gives up
   int variant;            // one-column kernel (k_spmv1): 0 = the pass's default,
                           // 1 = 32 lanes x 4, 2 = 16 lanes x 8, 3 = 8 lanes x 8;
                           // FP32 vectors only (else as 3): 4 = 8 x 8 with at
@@ -438,8 +319,7 @@ __global__ void __launch_bounds__(kBlock)
     k_spmm(SpmmArgs a, const V* __restrict__ va, const T* __restrict__ X, TO* __restrict__ Y,
            FineOp<T> fop, const T* __restrict__ P, const T* __restrict__ C,
            const double* __restrict__ lam2, const double* __restrict__ bvec,
-           double* __restrict__ part, ScalarFold fold) {
-  pdl_entry();
+           double* __restrict__ part) {
   constexpr int S = 32 / G;
   __shared__ double sdot[kBlock / 32][G * CPG];
   const int lane = threadIdx.x & 31, warp_in_block = threadIdx.x >> 5;
@@ -531,10 +411,6 @@ __global__ void __launch_bounds__(kBlock)
       for (int w = 0; w < kBlock / 32; ++w) sum += sdot[w][threadIdx.x];
       part[(int64_t)blockIdx.x * a.B + cfirst + threadIdx.x] = sum;
     }
-    // alpha folded into the last block of the A^T pass
-    if (MODE == 1 && fold.ticket != nullptr) {
-      if (last_block(fold.ticket)) fold_alpha(fold.st, a.B, part, (int)gridDim.x);
-    }
   }
 }
 
@@ -559,8 +435,7 @@ __global__ void __launch_bounds__(kBlock, MINB)
     k_spmv1(SpmmArgs a, const V* __restrict__ va, const T* __restrict__ X, TO* __restrict__ Y,
             FineOp<T> fop, const T* __restrict__ P, const T* __restrict__ C,
             const double* __restrict__ lam2, const double* __restrict__ bvec,
-            double* __restrict__ part, ScalarFold fold) {
-  pdl_entry();
+            double* __restrict__ part) {
   constexpr int RPW = 32 / LPR;  // rows per warp step
   __shared__ double sdot[kBlock / 32];
   const int lane = threadIdx.x & 31;
@@ -657,9 +532,6 @@ __global__ void __launch_bounds__(kBlock, MINB)
       for (int w = 0; w < kBlock / 32; ++w) sum += sdot[w];
       part[(int64_t)blockIdx.x * ld + col] = sum;
     }
-    if (MODE == 1 && fold.ticket != nullptr) {
-      if (last_block(fold.ticket)) fold_alpha(fold.st, a.B, part, (int)gridDim.x);
-    }
   }
 }
 
@@ -673,7 +545,6 @@ template <class Op, class T>
 __global__ void __launch_bounds__(kBlock)
     k_dinv(Op op, int64_t n, int B, const double* __restrict__ lam2, int smoother, double omega,
            T* __restrict__ dinv) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok) return;
   for (int64_t p = cm.first(); p < n; p += cm.stride()) {
@@ -690,7 +561,6 @@ template <class Op, class T>
 __global__ void __launch_bounds__(kBlock)
     k_smooth_zero(Op op, int64_t n, int B, const T* __restrict__ lam2, const T* __restrict__ dinv,
                   const T* __restrict__ r, T* __restrict__ z, int two) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok) return;
   const int col = cm.col;
@@ -714,8 +584,7 @@ template <class Op, class T>
 __global__ void __launch_bounds__(kBlock)
     k_smooth(Op op, int64_t n, int B, const T* __restrict__ lam2, const T* __restrict__ dinv,
              const T* __restrict__ r, const T* __restrict__ zin, T* __restrict__ zout,
-             const int* __restrict__ active, double* __restrict__ part, ScalarFold fold) {
-  pdl_entry();
+             const int* __restrict__ active, double* __restrict__ part) {
   __shared__ double sm[kBlock];
   const ColMap cm(B);
   double dacc = 0.0;
@@ -732,11 +601,7 @@ __global__ void __launch_bounds__(kBlock)
       dacc += to_d(rv) * to_d(zn);
     }
   }
-  if (part) {
-    block_col_sum(dacc, cm, sm, part + (int64_t)blockIdx.x * B);
-    // beta folded into the last block of the final level-0 sweep
-    if (fold.ticket != nullptr && last_block(fold.ticket)) fold_beta(fold, B, part, (int)gridDim.x);
-  }
+  if (part) block_col_sum(dacc, cm, sm, part + (int64_t)blockIdx.x * B);
 }
 
 // res = r - K z
@@ -744,7 +609,6 @@ template <class Op, class T>
 __global__ void __launch_bounds__(kBlock)
     k_residual(Op op, int64_t n, int B, const T* __restrict__ lam2, const T* __restrict__ r,
                const T* __restrict__ z, T* __restrict__ res) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok) return;
   const int col = cm.col;
@@ -760,7 +624,6 @@ __global__ void __launch_bounds__(kBlock)
 template <class T>
 __global__ void __launch_bounds__(kBlock)
     k_restrict(int nvc, int nhc, int B, const T* __restrict__ rf, T* __restrict__ rc) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok) return;
   const int col = cm.col;
@@ -787,7 +650,6 @@ __global__ void __launch_bounds__(kBlock)
 template <class T>
 __global__ void __launch_bounds__(kBlock)
     k_prolong_add(int nvc, int nhc, int B, const T* __restrict__ ec, T* __restrict__ zf) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok) return;
   const int col = cm.col;
@@ -824,7 +686,6 @@ template <class T>
 __global__ void __launch_bounds__(kBlock)
     k_coarse_solve(int nc, int B, const double* __restrict__ kinv, const T* __restrict__ rc,
                    T* __restrict__ ec) {
-  pdl_entry();
   extern __shared__ double rs[];
   const int col = blockIdx.y;
   for (int q = threadIdx.x; q < nc; q += kBlock) rs[q] = to_d(rc[(int64_t)q * B + col]);
@@ -848,7 +709,6 @@ template <class Op>
 __global__ void __launch_bounds__(kBlock)
     k_dense_assemble(Op op, int64_t n, int B, const double* __restrict__ lam2,
                      double* __restrict__ M) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok) return;
   for (int64_t p = cm.first(); p < n; p += cm.stride()) {
@@ -865,7 +725,6 @@ __global__ void __launch_bounds__(kBlock)
 static __global__ void __launch_bounds__(kBlock)
     k_cholesky_inverse(int n, double* __restrict__ Mall, double* __restrict__ Wall,
                        double* __restrict__ Kall, int* __restrict__ info) {
-  pdl_entry();
   const int col = blockIdx.x;
   double* M = Mall + (int64_t)col * n * n;
   double* X = Wall + (int64_t)col * n * n;
@@ -947,7 +806,6 @@ struct RapIn {
 };
 
 static __global__ void __launch_bounds__(kBlock) k_galerkin(RapIn in, int nvc, int nhc, double* __restrict__ out) {
-  pdl_entry();
   const int64_t nc = (int64_t)nvc * nhc;
   const int R = (in.part == 2) ? 2 : 1;
   for (int64_t t = (int64_t)blockIdx.x * kBlock + threadIdx.x; t < nc * kStencil;
@@ -997,7 +855,6 @@ template <class T, class TX>
 __global__ void __launch_bounds__(kBlock)
     k_update_xr(int64_t n, int B, ColState st, const T* __restrict__ p, const T* __restrict__ q,
                 TX* __restrict__ x, T* __restrict__ r, double* __restrict__ part) {
-  pdl_entry();
   __shared__ double sm[kBlock];
   const ColMap cm(B);
   double acc = 0.0;
@@ -1028,7 +885,6 @@ __global__ void __launch_bounds__(kBlock)
     k_update_xr_alpha(int64_t n, ColState st, int nb_pq, const double* __restrict__ pq_part,
                       const T* __restrict__ p, const T* __restrict__ q, TX* __restrict__ x, T* __restrict__ r,
                       double* __restrict__ part) {
-  pdl_entry();
   __shared__ double sm[kBlock / 32];
   double s = 0.0;
   for (int b = threadIdx.x; b < nb_pq; b += kBlock) s += pq_part[b];
@@ -1112,7 +968,6 @@ __global__ void __launch_bounds__(kBlock)
     k_update_p_beta(int64_t n, ColState st, int nb_rr, const double* __restrict__ rr_part, int nb_rz,
                     const double* __restrict__ rz_part, int maxit, double rel_trigger, const T* __restrict__ z,
                     T* __restrict__ p) {
-  pdl_entry();
   __shared__ double sm[kBlock / 32];
   const double rr = fixed_block_sum(rr_part, nb_rr, sm);
   const double rzn = fixed_block_sum(rz_part, nb_rz, sm);
@@ -1157,7 +1012,6 @@ __global__ void __launch_bounds__(kBlock)
 template <class T>
 __global__ void __launch_bounds__(kBlock)
     k_update_p(int64_t n, int B, ColState st, const T* __restrict__ z, T* __restrict__ p) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok || !(st.active[cm.col] || (st.keep && st.pending[cm.col]))) return;
   const int col = cm.col;
@@ -1173,7 +1027,6 @@ template <class T>
 __global__ void __launch_bounds__(kBlock)
     k_copy_cols(int64_t n, int B, const int* __restrict__ flag, const T* __restrict__ src,
                 T* __restrict__ dst) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok || (flag && !flag[cm.col])) return;
   for (int64_t i = cm.first(); i < n; i += cm.stride()) dst[i * B + cm.col] = src[i * B + cm.col];
@@ -1224,7 +1077,6 @@ __device__ __forceinline__ double block_sum_parts(const double* part, int nblk, 
 // k_scalar_col_beta accumulates.
 static __global__ void __launch_bounds__(kColThreads)
     k_scalar_col_alpha(int B, int nblk, const double* __restrict__ pq_part, ColState st) {
-  pdl_entry();
   const int col = blockIdx.x;
   if (col == 0 && threadIdx.x < 3) st.counters[threadIdx.x] = 0;
   if (!st.active[col]) {
@@ -1252,7 +1104,6 @@ static __global__ void __launch_bounds__(kColThreads)
 static __global__ void __launch_bounds__(kColThreads)
     k_scalar_col_beta(int B, int nblk_rr, const double* __restrict__ rr_part, int nblk_rz,
                       const double* __restrict__ rz_part, ColState st, int maxit, double rel_trigger) {
-  pdl_entry();
   const int col = blockIdx.x;
   if (st.active[col]) {
     const double rr = block_sum_parts(rr_part, nblk_rr, B, col);
@@ -1292,7 +1143,6 @@ static __global__ void __launch_bounds__(kColThreads)
 // Sum partials of a column reduction into out[col] (FP64).
 static __global__ void __launch_bounds__(kScalarThreads)
     k_sum_parts(int B, int nblk, const double* __restrict__ part, double* __restrict__ out) {
-  pdl_entry();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int col = w; col < B; col += kScalarThreads / 32) {
     const double s = warp_sum_parts(part, nblk, B, col);
@@ -1307,7 +1157,6 @@ static __global__ void __launch_bounds__(kScalarThreads)
 template <class TS, class TD>
 __global__ void k_expand_cols(int64_t n, int B, int per, int nsrc, const TS* __restrict__ src,
                               TD* __restrict__ dst) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok) return;
   for (int64_t i = cm.first(); i < n; i += cm.stride())
@@ -1317,20 +1166,17 @@ __global__ void k_expand_cols(int64_t n, int B, int per, int nsrc, const TS* __r
 // convert / copy with type change
 template <class TS, class TD>
 __global__ void k_convert(int64_t count, const TS* __restrict__ src, TD* __restrict__ dst) {
-  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < count; i += (int64_t)gridDim.x * kBlock)
     dst[i] = (TD)src[i];
 }
 
 // planar [B][n] <-> interleaved [n][B]
 static __global__ void k_planar_to_inter(int64_t n, int B, const double* __restrict__ src, double* __restrict__ dst) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok) return;
   for (int64_t i = cm.first(); i < n; i += cm.stride()) dst[i * B + cm.col] = src[(int64_t)cm.col * n + i];
 }
 static __global__ void k_inter_to_planar(int64_t n, int B, const double* __restrict__ src, double* __restrict__ dst) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok) return;
   for (int64_t i = cm.first(); i < n; i += cm.stride()) dst[(int64_t)cm.col * n + i] = src[i * B + cm.col];
@@ -1339,7 +1185,6 @@ static __global__ void k_inter_to_planar(int64_t n, int B, const double* __restr
 // dst[i][j] = src_j[i] for planar column pointers src_j (null -> 0)
 static __global__ void k_gather_cols(int64_t n, int B, const double* const* __restrict__ src,
                                      double* __restrict__ dst) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok) return;
   const double* s = src[cm.col];
@@ -1349,7 +1194,6 @@ static __global__ void k_gather_cols(int64_t n, int B, const double* const* __re
 // dst_j[i] = src[i][j] for non-null planar column pointers dst_j
 static __global__ void k_scatter_cols(int64_t n, int B, const double* __restrict__ src,
                                       double* const* __restrict__ dst) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok) return;
   double* d = dst[cm.col];
@@ -1360,7 +1204,6 @@ static __global__ void k_scatter_cols(int64_t n, int B, const double* __restrict
 // dst[i][j] = src[i][map[j]] (src has nsrc columns)
 static __global__ void k_gather_map(int64_t n, int B, int nsrc, const int* __restrict__ map,
                                     const double* __restrict__ src, double* __restrict__ dst) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok) return;
   const int sc = map[cm.col];
@@ -1368,14 +1211,12 @@ static __global__ void k_gather_map(int64_t n, int B, int nsrc, const int* __res
 }
 
 static __global__ void k_negate(int64_t count, double* __restrict__ x) {
-  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < count; i += (int64_t)gridDim.x * kBlock)
     x[i] = -x[i];
 }
 
 // x64 += (double) xlo ; xlo = 0   (reliable update of the mixed path)
 static __global__ void k_flush_x(int64_t count, float* __restrict__ xlo, double* __restrict__ x) {
-  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < count; i += (int64_t)gridDim.x * kBlock) {
     x[i] += (double)xlo[i];
     xlo[i] = 0.0f;
@@ -1386,7 +1227,6 @@ static __global__ void k_flush_x(int64_t count, float* __restrict__ xlo, double*
 template <class V>
 __global__ void k_diag_ata(int64_t n, const int64_t* __restrict__ rpT, const V* __restrict__ vT,
                            double* __restrict__ diag) {
-  pdl_entry();
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * kBlock) >> 5;
@@ -1405,7 +1245,6 @@ __global__ void k_diag_ata(int64_t n, const int64_t* __restrict__ rpT, const V* 
 // edge weights d -> per-pixel squared weights ws, we
 static __global__ void k_edge_to_pixel(int nv, int nh, const double* __restrict__ d, double* __restrict__ ws,
                                 double* __restrict__ we) {
-  pdl_entry();
   const int64_t n = (int64_t)nv * nh;
   const int64_t nvert = (int64_t)nh * (nv - 1);
   for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n; p += (int64_t)gridDim.x * kBlock) {
@@ -1428,7 +1267,6 @@ static __global__ void k_edge_to_pixel(int nv, int nh, const double* __restrict_
 static __global__ void __launch_bounds__(kBlock)
     k_seminorm(int nv, int nh, int B, const double* __restrict__ ws, const double* __restrict__ we,
                const double* __restrict__ x, double* __restrict__ part) {
-  pdl_entry();
   __shared__ double sm[kBlock];
   const ColMap cm(B);
   const int64_t n = (int64_t)nv * nh;
@@ -1453,7 +1291,6 @@ static __global__ void __launch_bounds__(kBlock)
 // weight update (eq. (g)): stage 1 writes |v_e| = |d_e (L x)_e| and block maxima
 static __global__ void k_weighted_grad(int nv, int nh, const double* __restrict__ d, const double* __restrict__ x,
                                 double* __restrict__ absv, double* __restrict__ bmax) {
-  pdl_entry();
   __shared__ double sm[kBlock];
   const int64_t nvert = (int64_t)nh * (nv - 1);
   const int64_t ne = nvert + (int64_t)(nh - 1) * nv;
@@ -1487,7 +1324,6 @@ static __global__ void k_weighted_grad(int nv, int nh, const double* __restrict_
 static __global__ void k_weight_apply(int64_t ne, int nblk, const double* __restrict__ bmax,
                                const double* __restrict__ absv, double q, double d_min,
                                double* __restrict__ d) {
-  pdl_entry();
   __shared__ double vmax;
   if (threadIdx.x == 0) {
     double m = 0.0;
@@ -1507,7 +1343,6 @@ static __global__ void k_weight_apply(int64_t ne, int nblk, const double* __rest
 template <class T>
 __global__ void __launch_bounds__(kBlock)
     k_col_dot(int64_t n, int B, const T* __restrict__ x, const T* __restrict__ y, double* __restrict__ part) {
-  pdl_entry();
   __shared__ double sm[kBlock];
   const ColMap cm(B);
   double acc = 0.0;
@@ -1519,7 +1354,6 @@ __global__ void __launch_bounds__(kBlock)
 // start of a solve: per-column state from ||c||^2 and the true residual
 static __global__ void k_init_state(int B, double tol, const double* __restrict__ cc, const double* __restrict__ rr,
                              ColState st) {
-  pdl_entry();
   const int col = threadIdx.x;
   if (col >= B) return;
   st.tol2cc[col] = tol * tol * cc[col];
@@ -1546,7 +1380,6 @@ static __global__ void k_init_state(int B, double tol, const double* __restrict_
 // of a running column (mixed path), 0 = leave.
 static __global__ void k_true_check(int B, const double* __restrict__ rr_true, ColState st, int replace_active,
                              int* __restrict__ flag) {
-  pdl_entry();
   __shared__ int cnt[2];
   if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
   __syncthreads();
@@ -1588,7 +1421,6 @@ static __global__ void k_true_check(int B, const double* __restrict__ rr_true, C
 template <class T>
 __global__ void k_take_residual(int64_t n, int B, const int* __restrict__ flag, const double* __restrict__ r64,
                                 T* __restrict__ r) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok || !flag[cm.col]) return;
   for (int64_t i = cm.first(); i < n; i += cm.stride()) r[i * B + cm.col] = (T)r64[i * B + cm.col];
@@ -1599,7 +1431,6 @@ template <class T>
 __global__ void k_restart_finish(int64_t n, int B, int nblk, const double* __restrict__ part,
                                  const int* __restrict__ flag, ColState st, const T* __restrict__ z,
                                  T* __restrict__ p) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok || flag[cm.col] != 1) return;
   if (blockIdx.x == 0 && cm.k == 0) st.rz[cm.col] = st.rz2[cm.col] = sum_parts(part, nblk, B, cm.col);
@@ -1608,7 +1439,6 @@ __global__ void k_restart_finish(int64_t n, int B, int nblk, const double* __res
 
 // zero every column of a batch whose flag is set (c = 0 systems)
 static __global__ void k_zero_cols(int64_t n, int B, const double* __restrict__ cc, double* __restrict__ x) {
-  pdl_entry();
   const ColMap cm(B);
   if (!cm.ok || cc[cm.col] != 0.0) return;
   for (int64_t i = cm.first(); i < n; i += cm.stride()) x[i * B + cm.col] = 0.0;
@@ -1646,7 +1476,6 @@ template <class T, int MODE>
 __global__ void __launch_bounds__(kBlock)
     k_psf_forward(PsfArgs a, const T* __restrict__ psf, int B, const T* __restrict__ x, T* __restrict__ y,
                   const double* __restrict__ bvec, int nl, int nrhs, double* __restrict__ part) {
-  pdl_entry();
   __shared__ double sm[kBlock];
   const ColMap cm(B);
   const int64_t n = (int64_t)a.nv * a.nh;
@@ -1673,7 +1502,6 @@ __global__ void __launch_bounds__(kBlock)
     k_psf_normal(PsfArgs a, const T* __restrict__ psf, int B, const T* __restrict__ y, FineOp<T> fop,
                  const T* __restrict__ P, const T* __restrict__ C, const double* __restrict__ lam2,
                  TO* __restrict__ out, double* __restrict__ part) {
-  pdl_entry();
   __shared__ double sm[kBlock];
   const ColMap cm(B);
   const int64_t n = (int64_t)a.nv * a.nh;
@@ -1701,7 +1529,6 @@ __global__ void __launch_bounds__(kBlock)
 
 // c = A^T b for the n_rhs right-hand sides (interleaved [n][nrhs])
 static __global__ void k_psf_rhs(PsfArgs a, int nrhs, const double* __restrict__ b, double* __restrict__ c) {
-  pdl_entry();
   const ColMap cm(nrhs);
   if (!cm.ok) return;
   const int64_t n = (int64_t)a.nv * a.nh;
@@ -1713,7 +1540,6 @@ static __global__ void k_psf_rhs(PsfArgs a, int nrhs, const double* __restrict__
 
 // diag(A^T A)_p = sum of psf^2 over offsets whose row p - (u, v) is inside
 static __global__ void k_psf_diag(PsfArgs a, double* __restrict__ diag) {
-  pdl_entry();
   const int64_t n = (int64_t)a.nv * a.nh;
   const int kw = 2 * a.rh + 1;
   for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n; p += (int64_t)gridDim.x * kBlock) {

@@ -24,11 +24,7 @@ struct LevelView {
 template <class V, class T, class TO, int MODE>
 int launch_spmm(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop,
                 const T* P, const T* C, const double* lam2, const double* bvec, double* part,
-                int max_blocks, cudaStream_t s, const ScalarFold* fold = nullptr);
-// Configure the shared-memory-staged SpMM kernels (dynamic shared memory
-// opt-in, resident blocks) on the current device; launch_spmm does this on
-// first use, but not inside stream capture.
-void prepare_spmm_staged();
+                int max_blocks, cudaStream_t s);
 
 template <class T>
 void launch_dinv(const LevelView<T>& L, int B, const double* lam2, int smoother, double omega,
@@ -40,7 +36,7 @@ void launch_smooth_zero(const LevelView<T>& L, int B, const T* lam2, const T* di
 template <class T>
 int launch_smooth(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const T* r,
                   const T* zin, T* zout, const int* active, double* part, int max_blocks,
-                  cudaStream_t s, const ScalarFold* fold = nullptr);
+                  cudaStream_t s);
 template <class T>
 void launch_residual(const LevelView<T>& L, int B, const T* lam2, const T* r, const T* z, T* res,
                      int max_blocks, cudaStream_t s);

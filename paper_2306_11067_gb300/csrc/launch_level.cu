@@ -30,13 +30,12 @@ void launch_smooth_zero(const LevelView<T>& L, int B, const T* lam2, const T* di
 template <class T>
 int launch_smooth(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const T* r,
                   const T* zin, T* zout, const int* active, double* part, int max_blocks,
-                  cudaStream_t s, const ScalarFold* fold) {
-  const ScalarFold f = fold ? *fold : ScalarFold{};
+                  cudaStream_t s) {
   const int g = grid_for(L.n, B, max_blocks);
   if (L.fine)
-    klaunch(k_smooth<FineOp<T>, T>, dim3(g), dim3(kBlock), 0, s, L.fine_op(), L.n, B, lam2, dinv, r, zin, zout, active, part, f);
+    klaunch(k_smooth<FineOp<T>, T>, dim3(g), dim3(kBlock), 0, s, L.fine_op(), L.n, B, lam2, dinv, r, zin, zout, active, part);
   else
-    klaunch(k_smooth<CoarseOp<T>, T>, dim3(g), dim3(kBlock), 0, s, L.coarse_op(), L.n, B, lam2, dinv, r, zin, zout, active, part, f);
+    klaunch(k_smooth<CoarseOp<T>, T>, dim3(g), dim3(kBlock), 0, s, L.coarse_op(), L.n, B, lam2, dinv, r, zin, zout, active, part);
   LCMG_LAUNCHED();
   return g;
 }
@@ -178,8 +177,7 @@ void launch_copy_cols(int64_t n, int B, const int* flag, const T* src, T* dst, i
   template void launch_smooth_zero<T>(const LevelView<T>&, int, const T*, const T*, const T*,   \
                                       T*, int, int, cudaStream_t);                              \
   template int launch_smooth<T>(const LevelView<T>&, int, const T*, const T*, const T*,         \
-                                const T*, T*, const int*, double*, int, cudaStream_t,           \
-                                const ScalarFold*);                                             \
+                                const T*, T*, const int*, double*, int, cudaStream_t);          \
   template void launch_residual<T>(const LevelView<T>&, int, const T*, const T*, const T*, T*,  \
                                    int, cudaStream_t);                                          \
   template void launch_restrict<T>(int, int, int, const T*, T*, int, cudaStream_t);             \

@@ -6,32 +6,8 @@
 #include <utility>
 
 #include "launch.h"
-#include "spmm_staged.cuh"
 
 namespace lcmg {
-
-// Blocks of the staged kernel resident per SM, with its dynamic shared
-// memory opted in (once per device and instantiation).
-template <class V, class T, class TO, int G, int CPG, int MODE>
-static int staged_blocks_per_sm() {
-  static std::mutex mu;
-  static int per_dev[64] = {0};
-  int dev = 0;
-  LCMG_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) throw ArgError("device ordinal out of range");
-  std::lock_guard<std::mutex> lock(mu);
-  if (per_dev[dev] == 0) {
-    auto k = k_spmm_staged<V, T, TO, G, CPG, MODE>;
-    LCMG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, StageGeo<V>::total));
-    int nb = 0;
-    LCMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kStagedThreads, StageGeo<V>::total));
-    if (nb < 1) throw CudaError("staged SpMM kernel does not fit on an SM");
-    int sms = 0;
-    LCMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    per_dev[dev] = nb * sms;
-  }
-  return per_dev[dev];
-}
 
 // Blocks of a kernel that are resident at once on the current device (the
 // grid of one full wave): a grid-stride kernel launched with more blocks
@@ -59,15 +35,14 @@ static int resident_grid(K kern, int threads, size_t smem) {
 template <class V, class T, class TO, int MODE, int U, int LPR, bool C16, int MINB>
 static int run1c(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop, const T* P,
                  const T* C, const double* lam2, const double* bvec, double* part, int max_blocks,
-                 cudaStream_t s, const ScalarFold* fold) {
+                 cudaStream_t s) {
   auto k = k_spmv1<V, T, TO, MODE, U, LPR, true, C16, MINB>;
   int64_t blocks = resident_grid(k, kBlock, 0);
   const int64_t need = (a.rows * LPR + kBlock - 1) / kBlock;
   if (blocks > need) blocks = need;
   if (blocks > max_blocks) blocks = max_blocks;
   if (blocks < 1) blocks = 1;
-  klaunch(k, dim3((unsigned)blocks), dim3(kBlock), 0, s, a, va, X, Y, fop, P, C, lam2, bvec, part,
-          fold ? *fold : ScalarFold{});
+  klaunch(k, dim3((unsigned)blocks), dim3(kBlock), 0, s, a, va, X, Y, fop, P, C, lam2, bvec, part);
   LCMG_LAUNCHED();
   return (int)blocks;
 }
@@ -75,17 +50,16 @@ static int run1c(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp
 template <class V, class T, class TO, int MODE, int U, int LPR, int MINB = spmv1_minb<T, LPR>()>
 static int run1v(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop, const T* P,
                  const T* C, const double* lam2, const double* bvec, double* part, int max_blocks,
-                 cudaStream_t s, const ScalarFold* fold) {
+                 cudaStream_t s) {
   // 16-bit columns in the 8-lane layout (the transposed pass): measured on
   // GB300 (ct256) it gains (38.2 -> 35.3 us per pass), while y = A p in the
   // 32-lane layout under a 32-register cap loses (31.1 -> 38.3 us) and keeps
   // int32 columns
   if constexpr ((MODE == 0 || MODE == 1) && LPR == 8) {
     if (a.c16 != nullptr)
-      return run1c<V, T, TO, MODE, U, LPR, true, MINB>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s,
-                                                       fold);
+      return run1c<V, T, TO, MODE, U, LPR, true, MINB>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s);
   }
-  return run1c<V, T, TO, MODE, U, LPR, false, MINB>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
+  return run1c<V, T, TO, MODE, U, LPR, false, MINB>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s);
 }
 
 // The pass's configuration: a.variant, or by default (measured on GB300,
@@ -95,40 +69,28 @@ static int run1v(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp
 template <class V, class T, class TO, int MODE>
 static int run1(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop, const T* P,
                 const T* C, const double* lam2, const double* bvec, double* part, int max_blocks,
-                cudaStream_t s, const ScalarFold* fold) {
+                cudaStream_t s) {
   constexpr bool kT = (MODE == 1 || MODE == 3);
   // transposed pass with FP32 vectors: 8 x 8 bounded to 5 blocks per SM
   // (48 registers; 32.8 vs 35.7-36.2 us per pass on GB300, same sums)
   const int v = a.variant != 0 ? a.variant : (kT ? (std::is_same<T, float>::value ? 4 : 3) : 1);
-  if (v == 2) return run1v<V, T, TO, MODE, 8, 16>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
+  if (v == 2) return run1v<V, T, TO, MODE, 8, 16>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s);
   if constexpr (std::is_same<T, float>::value) {  // register-bounded forms of the 8-lane layout
-    if (v == 4) return run1v<V, T, TO, MODE, 8, 8, 5>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
-    if (v == 5) return run1v<V, T, TO, MODE, 8, 8, 6>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
-    if (v == 6) return run1v<V, T, TO, MODE, 4, 8, 8>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
+    if (v == 4) return run1v<V, T, TO, MODE, 8, 8, 5>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s);
+    if (v == 5) return run1v<V, T, TO, MODE, 8, 8, 6>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s);
+    if (v == 6) return run1v<V, T, TO, MODE, 4, 8, 8>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s);
   }
-  if (v >= 3) return run1v<V, T, TO, MODE, 8, 8>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
-  return run1v<V, T, TO, MODE, 4, 32>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
+  if (v >= 3) return run1v<V, T, TO, MODE, 8, 8>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s);
+  return run1v<V, T, TO, MODE, 4, 32>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s);
 }
 
 template <class V, class T, class TO, int G, int CPG, int MODE>
 static int run(const SpmmArgs& a0, const V* va, const T* X, TO* Y, const FineOp<T>& fop,
                const T* P, const T* C, const double* lam2, const double* bvec, double* part,
-               int max_blocks, cudaStream_t s, const ScalarFold* fold) {
+               int max_blocks, cudaStream_t s) {
   SpmmArgs a = a0;
   const int width = G * CPG;
-  if (a.ck_row != nullptr) {
-    // persistent: every resident block walks chunks blockIdx.x + i * gridDim.x
-    int64_t blocks = staged_blocks_per_sm<V, T, TO, G, CPG, MODE>();
-    if (blocks > max_blocks) blocks = max_blocks;
-    if (blocks > a.nck) blocks = a.nck;
-    if (blocks < 1) blocks = 1;
-    dim3 grid((unsigned)blocks, (unsigned)((a.nb + width - 1) / width));
-    klaunch(k_spmm_staged<V, T, TO, G, CPG, MODE>, grid, dim3(kStagedThreads), (size_t)StageGeo<V>::total, s, a, va, X,
-            Y, fop, P, C, lam2, bvec, part, fold ? *fold : ScalarFold{});
-    LCMG_LAUNCHED();
-    return (int)blocks;
-  }
-  if (G == 1 && CPG == 1) return run1<V, T, TO, MODE>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s, fold);
+  if (G == 1 && CPG == 1) return run1<V, T, TO, MODE>(a, va, X, Y, fop, P, C, lam2, bvec, part, max_blocks, s);
   auto k = k_spmm<V, T, TO, G, CPG, MODE>;
   int64_t blocks = (a.rows + (kBlock / 32) - 1) / (kBlock / 32);
   const int64_t wave = resident_grid(k, kBlock, 0);
@@ -136,7 +98,7 @@ static int run(const SpmmArgs& a0, const V* va, const T* X, TO* Y, const FineOp<
   if (blocks > max_blocks) blocks = max_blocks;
   if (blocks < 1) blocks = 1;
   dim3 grid((unsigned)blocks, (unsigned)((a.nb + width - 1) / width));
-  klaunch(k, dim3(grid), dim3(kBlock), 0, s, a, va, X, Y, fop, P, C, lam2, bvec, part, fold ? *fold : ScalarFold{});
+  klaunch(k, dim3(grid), dim3(kBlock), 0, s, a, va, X, Y, fop, P, C, lam2, bvec, part);
   LCMG_LAUNCHED();
   return (int)blocks;
 }
@@ -167,28 +129,18 @@ static int dispatch_split(int nb, F&& f) {
 template <class V, class T, class TO, int MODE>
 int launch_spmm(const SpmmArgs& a, const V* va, const T* X, TO* Y, const FineOp<T>& fop,
                 const T* P, const T* C, const double* lam2, const double* bvec, double* part,
-                int max_blocks, cudaStream_t s, const ScalarFold* fold) {
+                int max_blocks, cudaStream_t s) {
   return dispatch_split<MODE>(a.nb, [&](auto g, auto cpg) {
     return run<V, T, TO, decltype(g)::value, decltype(cpg)::value, MODE>(a, va, X, Y, fop, P, C, lam2, bvec,
-                                                                         part, max_blocks, s, fold);
+                                                                         part, max_blocks, s);
   });
-}
-
-// Opt every staged instantiation of (V, T, TO, MODE) into its dynamic
-// shared memory on the current device.
-template <class V, class T, class TO, int MODE>
-static void prepare_staged() {
-  for (int nb : {1, 2, 4, 8, 12, 16, 20, 24, 32, 64})
-    dispatch_split<MODE>(nb, [&](auto g, auto cpg) {
-      return staged_blocks_per_sm<V, T, TO, decltype(g)::value, decltype(cpg)::value, MODE>();
-    });
 }
 
 #define LCMG_INST(V, T, TO, MODE)                                                             \
   template int launch_spmm<V, T, TO, MODE>(const SpmmArgs&, const V*, const T*, TO*,          \
                                            const FineOp<T>&, const T*, const T*,              \
                                            const double*, const double*, double*, int,        \
-                                           cudaStream_t, const ScalarFold*);
+                                           cudaStream_t);
 // FP32 path
 LCMG_INST(float, float, float, 0)
 LCMG_INST(float, float, float, 1)
@@ -202,18 +154,5 @@ LCMG_INST(double, double, double, 1)
 LCMG_INST(double, double, double, 2)
 LCMG_INST(double, double, double, 3)
 #undef LCMG_INST
-
-void prepare_spmm_staged() {
-  prepare_staged<float, float, float, 0>();
-  prepare_staged<float, float, float, 1>();
-  prepare_staged<float, double, double, 0>();
-  prepare_staged<float, double, double, 1>();
-  prepare_staged<float, double, double, 2>();
-  prepare_staged<float, double, double, 3>();
-  prepare_staged<double, double, double, 0>();
-  prepare_staged<double, double, double, 1>();
-  prepare_staged<double, double, double, 2>();
-  prepare_staged<double, double, double, 3>();
-}
 
 }  // namespace lcmg

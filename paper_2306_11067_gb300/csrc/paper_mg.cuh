@@ -97,7 +97,6 @@ __global__ void __launch_bounds__(kBlock)
     k_pm_lap_add(Op op, int64_t n, const double* __restrict__ lam2, const double* __restrict__ x,
                  const double* __restrict__ t, const double* __restrict__ b, double* __restrict__ q,
                  double* __restrict__ part) {
-  pdl_entry();
   __shared__ double sm[kBlock / 32];
   const double l2 = lam2[0];
   double acc = 0.0;
@@ -120,7 +119,6 @@ template <class Op>
 __global__ void __launch_bounds__(kBlock)
     k_pm_dinv(Op op, int64_t n, const double* __restrict__ lam2, const double* __restrict__ dA,
               double* __restrict__ dinv) {
-  pdl_entry();
   const double l2 = lam2[0];
   for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n; p += (int64_t)gridDim.x * kBlock) {
     const int j = (int)(p / op.nv), i = (int)(p - (int64_t)j * op.nv);
@@ -134,7 +132,6 @@ __global__ void __launch_bounds__(kBlock)
     k_pm_cg_init(int64_t n, int zero_x, const double* __restrict__ b, const double* __restrict__ dinv,
                  double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
                  double* __restrict__ p, double* __restrict__ part_rz) {
-  pdl_entry();
   __shared__ double sm[kBlock / 32];
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
@@ -162,7 +159,6 @@ __global__ void __launch_bounds__(kBlock)
                int nb_pq, const double* __restrict__ p, const double* __restrict__ q,
                const double* __restrict__ dinv, double* __restrict__ x, double* __restrict__ r,
                double* __restrict__ z, double* __restrict__ part_rz_new) {
-  pdl_entry();
   __shared__ double sm[kBlock / 32];
   const double rz = pm_sum_parts(part_rz, nb_rz, sm);
   const double pq = pm_sum_parts(part_pq, nb_pq, sm);
@@ -184,7 +180,6 @@ __global__ void __launch_bounds__(kBlock)
 __global__ void __launch_bounds__(kBlock)
     k_pm_cg_p(int64_t n, const double* __restrict__ part_new, const double* __restrict__ part_old, int nb,
               const double* __restrict__ z, double* __restrict__ p) {
-  pdl_entry();
   __shared__ double sm[kBlock / 32];
   const double rn = pm_sum_parts(part_new, nb, sm);
   const double ro = pm_sum_parts(part_old, nb, sm);
@@ -199,7 +194,6 @@ __global__ void __launch_bounds__(kBlock)
 __global__ void __launch_bounds__(kBlock)
     k_pm_dense(GLOp op, const double* __restrict__ lam2, const double* __restrict__ AtA,
                double* __restrict__ M) {
-  pdl_entry();
   const int64_t n = op.n;
   const double l2 = lam2[0];
   for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * kBlock) {
@@ -219,7 +213,6 @@ __global__ void __launch_bounds__(kBlock)
 __global__ void __launch_bounds__(kBlock)
     k_pm_dense_add(int64_t nn, const double* __restrict__ lam2, const double* __restrict__ AtA,
                    const double* __restrict__ G, double* __restrict__ M) {
-  pdl_entry();
   const double l2 = lam2[0];
   for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < nn; e += (int64_t)gridDim.x * kBlock)
     M[e] = AtA[e] + l2 * G[e];
@@ -232,7 +225,6 @@ template <bool ADD>
 __global__ void __launch_bounds__(kBlock)
     k_pm_csr_mv(int64_t rows, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                 const double* __restrict__ v, const double* __restrict__ x, double* __restrict__ y) {
-  pdl_entry();
   for (int64_t r = (int64_t)blockIdx.x * kBlock + threadIdx.x; r < rows; r += (int64_t)gridDim.x * kBlock) {
     double acc = 0.0;
     for (int64_t k = rp[r]; k < rp[r + 1]; ++k) acc += v[k] * x[ci[k]];
@@ -245,7 +237,6 @@ __global__ void __launch_bounds__(kBlock)
 __global__ void __launch_bounds__(kBlock)
     k_pm_multidot(int64_t n, int m, const double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
                   double* __restrict__ part) {
-  pdl_entry();
   __shared__ double sm[kBlock / 32];
   const int i = blockIdx.y;
   const double* vi = V + (int64_t)i * ldv;
@@ -267,7 +258,6 @@ __global__ void __launch_bounds__(kBlock)
 // h[i] (+)= sum of part[i][0 .. nb); one warp per i
 __global__ void __launch_bounds__(kBlock)
     k_pm_sum_rows(int m, int nb, const double* __restrict__ part, double* __restrict__ h, int accumulate) {
-  pdl_entry();
   const int lane = threadIdx.x & 31;
   for (int i = (int)(blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5)); i < m; i += (int)(gridDim.x * (kBlock / 32))) {
     double s = 0.0;
@@ -282,7 +272,6 @@ __global__ void __launch_bounds__(kBlock)
 __global__ void __launch_bounds__(kBlock)
     k_pm_orth(int64_t n, int m, const double* __restrict__ V, int64_t ldv, const double* __restrict__ h,
               double* __restrict__ w) {
-  pdl_entry();
   for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n; p += (int64_t)gridDim.x * kBlock) {
     double s = w[p];
     for (int i = 0; i < m; ++i) s -= h[i] * V[(int64_t)i * ldv + p];
@@ -294,7 +283,6 @@ __global__ void __launch_bounds__(kBlock)
 __global__ void __launch_bounds__(kBlock)
     k_pm_combine(int64_t n, int m, const double* __restrict__ Z, int64_t ldz, const double* __restrict__ y,
                  double* __restrict__ x) {
-  pdl_entry();
   for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n; p += (int64_t)gridDim.x * kBlock) {
     double s = x[p];
     for (int i = 0; i < m; ++i) s += y[i] * Z[(int64_t)i * ldz + p];
@@ -305,7 +293,6 @@ __global__ void __launch_bounds__(kBlock)
 // y = s x
 __global__ void __launch_bounds__(kBlock)
     k_pm_scale(int64_t n, double s, const double* __restrict__ x, double* __restrict__ y) {
-  pdl_entry();
   for (int64_t p = (int64_t)blockIdx.x * kBlock + threadIdx.x; p < n; p += (int64_t)gridDim.x * kBlock)
     y[p] = s * x[p];
 }

@@ -24,7 +24,6 @@ __device__ __forceinline__ double splitmix_uniform(uint64_t seed, int64_t i) {
 
 static __global__ void k_pmis_init(int64_t n, const int64_t* __restrict__ srp, const int64_t* __restrict__ trp,
                                    uint64_t seed, double* __restrict__ w, int8_t* __restrict__ st) {
-  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t deps = trp[i + 1] - trp[i];
     w[i] = (double)deps + splitmix_uniform(seed, i);
@@ -38,7 +37,6 @@ static __global__ void k_pmis_select(int64_t n, const int64_t* __restrict__ srp,
                                      const int64_t* __restrict__ trp, const int32_t* __restrict__ tci,
                                      const double* __restrict__ w, const int8_t* __restrict__ st,
                                      int8_t* __restrict__ newc) {
-  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     int8_t pick = 0;
     if (st[i] == kU) {
@@ -59,7 +57,6 @@ static __global__ void k_pmis_select(int64_t n, const int64_t* __restrict__ srp,
 }
 
 static __global__ void k_pmis_apply(int64_t n, const int8_t* __restrict__ newc, int8_t* __restrict__ st) {
-  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     if (newc[i]) st[i] = kC;
 }
@@ -69,7 +66,6 @@ static __global__ void k_pmis_apply(int64_t n, const int8_t* __restrict__ newc, 
 // agree); the others are counted
 static __global__ void k_pmis_f(int64_t n, const int64_t* __restrict__ srp, const int32_t* __restrict__ sci,
                                 int8_t* __restrict__ st, int* __restrict__ left) {
-  pdl_entry();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     if (st[i] != kU) continue;
     bool f = false;

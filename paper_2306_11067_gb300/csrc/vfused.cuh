@@ -53,7 +53,6 @@ template <class Op, class T, int NU>
 __global__ void __launch_bounds__(vtile_threads<Op, T, NU>())
     k_vdown(Op op, int B, const T* __restrict__ lam2, const T* __restrict__ dinv, const T* __restrict__ r,
             T* __restrict__ zpre, T* __restrict__ rc, int ntx) {
-  pdl_entry();
   constexpr int NTD = vtile_threads<Op, T, NU>();
   constexpr int H = Op::kRadius;
   constexpr int WR = 2 * kVTile + 2;                  // restriction window
@@ -173,7 +172,6 @@ __global__ void __launch_bounds__(vtile_threads<Op, T, NU>())
     k_vup(Op op, int B, const T* __restrict__ lam2, const T* __restrict__ dinv, const T* __restrict__ r,
           const T* __restrict__ ec, const T* __restrict__ zpre, T* __restrict__ zout, int ntx,
           double* __restrict__ part) {
-  pdl_entry();
   constexpr int NTD = vtile_threads<Op, T, NU>();
   constexpr int H = Op::kRadius;
   constexpr int WF = 2 * kVTile;           // the tile's fine points

@@ -37,10 +37,7 @@ class lcmg_params(C.Structure):
                 ("smoother", C.c_int32), ("omega", C.c_double), ("q", C.c_double),
                 ("d_min", C.c_double), ("tol", C.c_double), ("maxit", C.c_int32),
                 ("precision", C.c_int32), ("mode", C.c_int32), ("check_every", C.c_int32),
-                ("graphs", C.c_int32), ("timing", C.c_int32), ("fused", C.c_int32),
-                ("tail_points", C.c_int32), ("pdl", C.c_int32),
-                ("fold", C.c_int32),
-                ("staged", C.c_int32),
+                ("graphs", C.c_int32), ("timing", C.c_int32),
                 ("vfuse", C.c_int32),
                 ("keep_direction", C.c_int32),
                 ("autotune", C.c_int32),
@@ -48,7 +45,7 @@ class lcmg_params(C.Structure):
                 ("stop_rule", C.c_int32),
                 ("precond", C.c_int32), ("gmres_restart", C.c_int32),
                 ("coarsening", C.c_int32), ("amg_coarse_max", C.c_int32), ("compact_cols", C.c_int32),
-                ("alpha_fuse", C.c_int32), ("beta_fuse", C.c_int32), ("tail_ctas", C.c_int32),
+                ("alpha_fuse", C.c_int32), ("beta_fuse", C.c_int32),
                 ("spmv_variant_at", C.c_int32)]
 
 
@@ -56,7 +53,7 @@ class lcmg_stats(C.Structure):
     _fields_ = [("column_iterations", C.c_int64), ("batch_iterations", C.c_int64),
                 ("kernel_launches", C.c_int64), ("iterate_ms", C.c_double),
                 ("op_ms_a", C.c_double), ("op_ms_at", C.c_double),
-                ("op_launches", C.c_int64), ("op_bytes", C.c_int64), ("fused_ctas", C.c_int32),
+                ("op_launches", C.c_int64), ("op_bytes", C.c_int64),
                 ("tuned_spmv_a", C.c_int32), ("tuned_spmv_at", C.c_int32), ("tuned_vfuse", C.c_int32)]
 
 

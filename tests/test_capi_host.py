@@ -30,7 +30,7 @@ def test_default_params():
     assert (p.nu, p.coarse_max, p.maxit, p.check_every, p.graphs) == (1, 16, 10000, 16, 1)
     assert (p.tol, p.q, p.d_min) == (1e-6, 2.0, 1e-3)
     # execution-path options: the measured-fastest combination on GB300
-    assert (p.fused, p.tail_points, p.pdl, p.fold, p.staged, p.vfuse) == (0, 0, 0, 0, 0, 1)
+    assert (p.vfuse, p.mode, p.precision) == (1, L.MODE_SEQUENTIAL, L.PREC_FP64)
     assert L.lcmg_version().startswith("lcmg")
 
 
@@ -248,5 +248,5 @@ def test_default_params_write_exactly_the_struct():
     L.lib().lcmg_default_params(C.cast(buf, C.POINTER(L.lcmg_params)))
     assert bytes(buf[size:]) == bytes([0xA5]) * 64
     p = L.lcmg_params.from_buffer(buf)
-    assert (p.amg_coarse_max, p.compact_cols, p.alpha_fuse, p.beta_fuse, p.tail_ctas, p.spmv_variant_at) == \
-        (256, 1, 1, 1, 1, 0)
+    assert (p.amg_coarse_max, p.compact_cols, p.alpha_fuse, p.beta_fuse, p.spmv_variant_at) == \
+        (256, 1, 1, 1, 0)
