@@ -174,6 +174,22 @@ typedef struct {
                            computes beta first                             */
   int32_t spmv_variant_at; /* configuration of the transposed pass alone (0 =
                            as spmv_variant; 1..6 as there)                  */
+  int32_t max_blocks;   /* cap on the blocks of every grid-stride launch (0 =
+                           the default, 8 per SM up to 2048).  A small cap
+                           makes each block, and each warp of the one-column
+                           SpMV, walk many rows: the same sums in the same
+                           order per row, for testing those loops           */
+  int32_t smoother_fp16; /* mixed precision, a batch whose columns share one
+                           lambda (the chain; its right-hand-side batches) and
+                           the two-kernels-per-level cycle: 1 = the V-cycle's
+                           smoother data in FP16 with power-of-two scales (the
+                           finest level's edge weights and diag(A^T A); per
+                           lambda the 24 off-diagonal coefficients of each
+                           coarse K_k(lambda), with the diagonal rebuilt from
+                           the FP32 row sums of G_A^k) (default); 0 = FP32.
+                           The cycle stays symmetric positive definite; it
+                           differs from the FP32 cycle by the rounding of its
+                           coefficients to 11 bits                        */
 } lcmg_params;
 
 typedef struct lcmg_ctx lcmg_ctx;
@@ -223,6 +239,29 @@ int lcmg_set_forward_csr(lcmg_ctx* ctx, int64_t m, int64_t n, const int64_t* row
  * over pixels inside the image (rows of A truncated at the boundary, not
  * renormalised).  A^T uses the flipped PSF.  Requires set_grid. */
 int lcmg_set_forward_stencil(lcmg_ctx* ctx, int32_t kh, int32_t kw, const double* psf);
+/* A PSF that is an outer product fv fh^T (every entry within 1e-14 of the
+ * largest of fv[u] fh[v], with fv the row sums and fh the column sums over
+ * their total) is applied in its separable form, the Kronecker product of
+ * two 1-D zero-boundary Toeplitz correlations (the deblurring example of
+ * Sec. 4 builds its blur this way): A^T A = (A_h^T A_h) (x) (A_v^T A_v) as
+ * two banded passes of 4r + 1 taps, A and A^T as passes of 2r + 1 taps.  The
+ * result equals the 2-D form up to rounding.  Radii up to 16 (kh, kw <= 33);
+ * larger PSFs use the 2-D form.  Errors: INVALID_ARG (even or zero sides,
+ * PSF larger than 2 n + 1, non-finite values), STATE (no grid). */
+
+/* Forward operator A given by its 1-D factors: the PSF fv fh^T with fv
+ * (kh values, along i, the image columns) and fh (kw values, along j):
+ *   (A x)(i, j) = sum_{u,v} fv[u + kh/2] fh[v + kw/2] x(i + u, j + v)
+ * with zero boundary, i.e. A = A_h (x) A_v (Sec. 4, the Kronecker form of
+ * the blur).  Uses the separable passes above (kh, kw <= 33), else the 2-D
+ * form of the same PSF.  Requires set_grid; the library copies fv, fh.
+ * Errors as lcmg_set_forward_stencil. */
+int lcmg_set_forward_separable(lcmg_ctx* ctx, int32_t kh, const double* fv, int32_t kw,
+                               const double* fh);
+
+/* How the forward operator is applied: 0 none, 1 CSR, 2 PSF in its 2-D
+ * form, 3 PSF in its separable form. */
+int lcmg_forward_form(lcmg_ctx* ctx, int32_t* form);
 
 /* Edge weights d of D = diag(d) (host array of n_edges values in (0, 1]).
  * Rebuilds the lambda-independent multigrid hierarchy on the device
@@ -356,7 +395,10 @@ int lcmg_lcurve_run_dev(lcmg_ctx* ctx, int32_t m_lambda, const double* lambda,
  * q = K p inside the PCG iteration (A p, then A^T y + lam^2 L^T W L p) are
  * bracketed by CUDA events on the context's stream: op_ms_a / op_ms_at
  * are their summed durations, op_launches the number of timed passes and
- * op_bytes their summed algorithmic (compulsory) DRAM bytes. */
+ * op_bytes their summed algorithmic (compulsory) DRAM bytes; the V-cycle
+ * of the same iterations is bracketed too: vcycle_ms, vcycle_count and
+ * vcycle_bytes (every level's vectors read and written once and its
+ * smoother data read once per visit, as stored). */
 typedef struct {
   int64_t column_iterations;
   int64_t batch_iterations;
@@ -372,6 +414,9 @@ typedef struct {
                            forms; 0 = default) used by the last batch        */
   int32_t tuned_vfuse;  /* V-cycle form of the last batch: 1 fused, 0 per step,
                            -1 the params.vfuse rule                              */
+  double vcycle_ms;
+  int64_t vcycle_count;
+  int64_t vcycle_bytes;
 } lcmg_stats;
 int lcmg_get_stats(lcmg_ctx* ctx, lcmg_stats* out);
 
@@ -397,6 +442,13 @@ int lcmg_num_levels(lcmg_ctx* ctx, int32_t* levels);
 
 /* diag(A^T A) (n doubles, host). */
 int lcmg_get_diag(lcmg_ctx* ctx, double* diag_out);
+
+/* Measured arithmetic peak (TFLOP/s, multiply-add = 2 flops) of the FP64
+ * (precision = LCMG_PREC_FP64) or FP32 (LCMG_PREC_MIXED) pipe of device
+ * `device`: independent multiply-add chains on every SM, best of 5 timed
+ * launches.  A measurement utility that bounds the FP64 kernels of this
+ * library (the paper has no counterpart).  Errors: INVALID_ARG, CUDA. */
+int lcmg_fma_peak(int device, int32_t precision, double* tflops);
 
 /* Allocation-free application of q_j = (A^T A + lambda_j^2 L^T D^2 L) p_j.
  * The paper has no counterpart: this exists for callers that cannot

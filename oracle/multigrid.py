@@ -24,9 +24,23 @@ classical AMG with diagonally preconditioned CG smoothing and FGMRES):
     D_l1 = diag(sum_j |k_ij|) (or damped Jacobi with weight omega), so the
     V(nu, nu) cycle is a symmetric operator and CG applies;
   * the coarsest level is solved exactly by a dense Cholesky factorisation.
+
+The mixed-precision path may store the smoother data of every level above
+the coarsest in FP16 (storage="fp16"; a fixed SPD perturbation of the
+cycle, not of the system solved): each array is scaled by the power of two
+that puts its largest magnitude in (4096, 8192] (``half_scale``) and
+rounded to the nearest FP16 number (``fp16_round``).  On the finest level
+the rounded quantities are the edge weights of G_L^0 = L^T W L and
+diag(A^T A), so the level operator is lam^2 L^T W^ L + diag(ga^).  On a
+coarse level they are the off-diagonal entries of K_k(lam) = lam^2 G_L^k +
+G_A^k (one scale per level and lambda, from lam^2 max|G_L^k| + max|G_A^k|
+over off-diagonal entries), and the diagonal is rebuilt as the row sum of
+G_A^k (the rows of G_L^k sum to zero), rounded to FP32, minus the rounded
+off-diagonals, so the rounded operator keeps K_k 1 = G_A^k 1.
 """
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -95,14 +109,69 @@ def build_hierarchy(G_L0, G_A0, n_v, n_h, levels) -> Hierarchy:
     return Hierarchy(shapes, GL, GA, Ps)
 
 
+def half_scale(mx: float) -> float:
+    """The power of two that puts mx (> 0) in (4096, 8192]."""
+    if not mx > 0.0:
+        return 1.0
+    return 2.0 ** math.floor(math.log2(8192.0 / mx))
+
+
+def fp16_round(v, scale: float):
+    """v rounded as stored: nearest FP16 number of v * scale, divided back."""
+    return (np.asarray(v, dtype=np.float64) * scale).astype(np.float16).astype(np.float64) / scale
+
+
+def _offdiag(M):
+    M = sp.coo_matrix(M)
+    off = M.row != M.col
+    return M.row[off], M.col[off], M.data[off]
+
+
+def fp16_fine_operator(G_L0, G_A0, lam2):
+    """lam^2 L^T W^ L + diag(ga^) with the edge weights (minus the
+    off-diagonal entries of G_L^0) and diag(A^T A) rounded as stored."""
+    r, c, v = _offdiag(G_L0)
+    n = G_L0.shape[0]
+    w = fp16_round(-v, half_scale(np.max(np.abs(v)) if v.size else 0.0))
+    Wo = sp.csr_matrix((-w, (r, c)), shape=(n, n))
+    GLh = Wo - sp.diags(np.asarray(Wo.sum(axis=1)).ravel())
+    ga = G_A0.diagonal()
+    gah = fp16_round(ga, half_scale(np.max(np.abs(ga))))
+    return (lam2 * GLh + sp.diags(gah)).tocsr()
+
+
+def fp16_coarse_operator(G_L, G_A, lam2):
+    """K_k(lam) with its off-diagonal entries rounded as stored and the
+    diagonal rebuilt from the FP32 row sums of G_A."""
+    n = G_L.shape[0]
+    K = (lam2 * G_L + G_A).tocsr()
+    r, c, v = _offdiag(K)
+    _, _, vl = _offdiag(G_L)
+    _, _, va = _offdiag(G_A)
+    bound = lam2 * (np.max(np.abs(vl)) if vl.size else 0.0) + (np.max(np.abs(va)) if va.size else 0.0)
+    vh = fp16_round(v, half_scale(bound))
+    Ko = sp.csr_matrix((vh, (r, c)), shape=(n, n))
+    s = np.asarray(G_A.sum(axis=1)).ravel().astype(np.float32).astype(np.float64)
+    return (Ko + sp.diags(s - np.asarray(Ko.sum(axis=1)).ravel())).tocsr()
+
+
 class VCycle:
-    """B(lam) r: one V(nu, nu) cycle of Algorithm 1 with zero initial guess."""
+    """B(lam) r: one V(nu, nu) cycle of Algorithm 1 with zero initial guess
+    (storage="fp16": the smoothers of every level above the coarsest work on
+    the rounded operators described in the module docstring)."""
 
     def __init__(self, hier: Hierarchy, lam: float, nu: int = 2,
-                 smoother: str = "l1", omega: float = 2.0 / 3.0):
+                 smoother: str = "l1", omega: float = 2.0 / 3.0, storage: str = "fp64"):
         self.h, self.nu = hier, nu
         lam2 = lam * lam
         self.K = [(lam2 * gl + ga).tocsr() for gl, ga in zip(hier.G_L, hier.G_A)]
+        if storage == "fp16":
+            last = len(self.K) - 1
+            for k in range(last):
+                self.K[k] = (fp16_fine_operator(hier.G_L[0], hier.G_A[0], lam2) if k == 0
+                             else fp16_coarse_operator(hier.G_L[k], hier.G_A[k], lam2))
+        elif storage != "fp64":
+            raise ValueError(storage)
         self.Dinv = []
         for K in self.K:
             if smoother == "l1":

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblcmg.so")
-SOURCES = ["capi.cu", "launch_spmm.cu", "launch_level.cu", "noalloc.cu", "server.cu",
+SOURCES = ["capi.cu", "launch_spmm.cu", "launch_level.cu", "separable.cu", "noalloc.cu", "server.cu", "peak.cu",
            "rs_amg.cpp", "pmis.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

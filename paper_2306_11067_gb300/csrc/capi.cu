@@ -66,6 +66,12 @@ struct Level {
   DevBuf<double> gl, ga;   // 25 x n (levels >= 1)
   DevBuf<double> cf64;     // per-point coefficient rows (smoother layout)
   DevBuf<float> cf32;
+  // FP16 smoother data (levels >= 1): per-lambda rows of K's off-diagonals,
+  // the row sums of G_A, and the largest off-diagonal |G_L|, |G_A| (scales)
+  DevBuf<__half> hrows;
+  DevBuf<float> hs;
+  double glmax = 0.0, gamax = 0.0;
+  double hscale = 1.0;     // scale of the rows of the current lambda
 };
 
 struct LevelWork {
@@ -152,11 +158,24 @@ struct lcmg_ctx {
   int rv = 0, rh = 0;
   DevBuf<double> psf64;
   DevBuf<float> psf32;
+  // separable PSF fv fh^T (sep): the banded passes of A^T A along i and j
+  // (with their boundary correction rows in FP64 and FP32), of A and of A^T
+  bool sep = false;
+  lcmg::SepPass sp_vt, sp_ht, sp_va, sp_ha, sp_vat, sp_hat;
+  DevBuf<double> sep_dv64, sep_dh64;
+  DevBuf<float> sep_dv32, sep_dh32;
+  DevBuf<double> sep_tmp;  // intermediate of A^T b and of rho = ||A x - b||
   DevBuf<double> diag;
   DevBuf<float> diag32;
   // weights
   DevBuf<double> d, ws, we;
   DevBuf<float> ws32, we32;
+  // FP16 copies of the finest level's smoother data (w_s, w_e scaled by
+  // hw_scale, diag(A^T A) by hg_scale); h16_on: the current batch uses them
+  DevBuf<__half> h_ws, h_we, h_ga;
+  double hw_scale = 1.0, hg_scale = 1.0;
+  DevBuf<unsigned long long> hmax;
+  bool h16_on = false;
   // hierarchy
   std::vector<Level> lev;
   bool hier_ok = false;
@@ -242,6 +261,8 @@ static void check_params(const lcmg_params& p) {
   if (p.alpha_fuse != 0 && p.alpha_fuse != 1) throw ArgError("alpha_fuse must be 0 or 1");
   if (p.beta_fuse != 0 && p.beta_fuse != 1) throw ArgError("beta_fuse must be 0 or 1");
   if (p.amg_coarse_max < 2 || p.amg_coarse_max > 2048) throw ArgError("amg_coarse_max must be 2..2048");
+  if (p.max_blocks < 0) throw ArgError("max_blocks must be >= 0");
+  if (p.smoother_fp16 != 0 && p.smoother_fp16 != 1) throw ArgError("smoother_fp16 must be 0 or 1");
 }
 
 static int sum_blocks(int nb) { return std::max(1, std::min(nb, kMaxBlocks)); }
@@ -270,6 +291,50 @@ static void refresh_fine(lcmg_ctx& c) {
   LCMG_LAUNCHED();
   c.hier_ok = false;
   c.am_ok = false;  // classical AMG coarsens L^T D^2 L: rebuilt for every D
+}
+
+// The lambda-independent part of the FP16 smoother data: the finest
+// level's w_s, w_e, diag(A^T A) in FP16 with their scales, and per coarse
+// level the FP32 row sums of G_A and the largest off-diagonal |G_L|, |G_A|
+// (the scale of a lambda's rows: lam^2 glmax + gamax bounds |K|'s entries)
+static void build_half(lcmg_ctx& c) {
+  const int L = (int)c.lev.size();
+  unsigned long long* mx = c.hmax.need(2 * L + 2);
+  LCMG_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * (2 * L + 2), c.stream));
+  const int g0 = (int)std::min<int64_t>((c.n + kBlock - 1) / kBlock, c.maxblk);
+  klaunch(k_maxabs, dim3(g0), dim3(kBlock), 0, c.stream, c.n, (const double*)c.ws.p, 0, mx);
+  LCMG_LAUNCHED();
+  klaunch(k_maxabs, dim3(g0), dim3(kBlock), 0, c.stream, c.n, (const double*)c.we.p, 0, mx);
+  LCMG_LAUNCHED();
+  klaunch(k_maxabs, dim3(g0), dim3(kBlock), 0, c.stream, c.n, (const double*)c.diag.p, 0, mx + 1);
+  LCMG_LAUNCHED();
+  for (int k = 1; k < L; ++k) {
+    Level& g = c.lev[k];
+    const int gk = (int)std::min<int64_t>((g.n + kBlock - 1) / kBlock, c.maxblk);
+    klaunch(k_maxabs, dim3(gk), dim3(kBlock), 0, c.stream, g.n, (const double*)g.gl.p, 1, mx + 2 * k);
+    LCMG_LAUNCHED();
+    klaunch(k_maxabs, dim3(gk), dim3(kBlock), 0, c.stream, g.n, (const double*)g.ga.p, 1, mx + 2 * k + 1);
+    LCMG_LAUNCHED();
+    klaunch(k_rowsum25, dim3(gk), dim3(kBlock), 0, c.stream, g.n, (const double*)g.ga.p, g.hs.need(g.n));
+    LCMG_LAUNCHED();
+    g.hrows.need((size_t)kCompactOff * g.n);
+  }
+  std::vector<unsigned long long> hm(2 * L + 2);
+  copy_sync(c.stream, hm.data(), mx, sizeof(unsigned long long) * hm.size(), cudaMemcpyDeviceToHost);
+  auto dbl = [](unsigned long long b) { double v; std::memcpy(&v, &b, sizeof v); return v; };
+  c.hw_scale = half_scale(dbl(hm[0]));
+  c.hg_scale = half_scale(dbl(hm[1]));
+  for (int k = 1; k < L; ++k) {
+    c.lev[k].glmax = dbl(hm[2 * k]);
+    c.lev[k].gamax = dbl(hm[2 * k + 1]);
+  }
+  klaunch(k_half_scaled, dim3(g0), dim3(kBlock), 0, c.stream, c.n, (const double*)c.ws.p, c.hw_scale, c.h_ws.need(c.n));
+  LCMG_LAUNCHED();
+  klaunch(k_half_scaled, dim3(g0), dim3(kBlock), 0, c.stream, c.n, (const double*)c.we.p, c.hw_scale, c.h_we.need(c.n));
+  LCMG_LAUNCHED();
+  klaunch(k_half_scaled, dim3(g0), dim3(kBlock), 0, c.stream, c.n, (const double*)c.diag.p, c.hg_scale,
+          c.h_ga.need(c.n));
+  LCMG_LAUNCHED();
 }
 
 static void build_hierarchy(lcmg_ctx& c) {
@@ -308,6 +373,7 @@ static void build_hierarchy(lcmg_ctx& c) {
     klaunch(k_coef_pack<float>, dim3(gg), dim3(kBlock), 0, c.stream, g.n, gl, ga, g.cf32.need(kCoefStride * g.n));
     LCMG_LAUNCHED();
   }
+  build_half(c);
   c.hier_ok = true;
 }
 
@@ -333,6 +399,11 @@ LevelView<float> view<float>(const lcmg_ctx& c, int k) {
   v.nv = l.nv; v.nh = l.nh; v.n = l.n;
   if (k == 0) { v.fine = true; v.ws = c.ws32.p; v.we = c.we32.p; v.ga = c.diag32.p; }
   else { v.fine = false; v.cf = l.cf32.p; }
+  if (c.h16_on) {
+    v.h16 = true;
+    v.fh = FineOpH{l.nv, l.nh, c.h_ws.p, c.h_we.p, c.h_ga.p, (float)(1.0 / c.hw_scale), (float)(1.0 / c.hg_scale)};
+    v.ch = CoarseOpH{l.nv, l.nh, l.n, reinterpret_cast<const uint4*>(l.hrows.p), l.hs.p, (float)(1.0 / l.hscale)};
+  }
   return v;
 }
 
@@ -393,6 +464,7 @@ struct Batch {
   int tune_key() const { return 2 * B + (std::is_same<T, float>::value ? 1 : 0); }
 
   Batch(lcmg_ctx& c_, int B_) : c(c_), B(B_), s(c_.stream), nlev((int)c_.lev.size()) {
+    c.h16_on = false;
     var_a = var_at = c.prm.spmv_variant;
     if (c.prm.spmv_variant_at) var_at = c.prm.spmv_variant_at;
     auto it = c.tuned.find(tune_key());
@@ -403,7 +475,22 @@ struct Batch {
     }
   }
 
+  ~Batch() { c.h16_on = false; }
+  Batch(const Batch&) = delete;
+  Batch& operator=(const Batch&) = delete;
+
   T* tp(DevBuf<char>& b) { return reinterpret_cast<T*>(b.p); }
+
+  // the finest level of the two-kernels-per-level V(1,1) cycle with FP32
+  // vectors runs k_vfine_down / k_vfine_up
+  bool fine_v11() const { return std::is_same<T, float>::value && c.prm.nu == 1 && vf_on(); }
+
+  // the two-kernels-per-level V-cycle runs for this batch
+  bool vf_on() const {
+    const int nu = c.prm.nu;
+    const bool vf = vf_force >= 0 ? vf_force == 1 : (c.prm.vfuse == 2 || (c.prm.vfuse == 1 && B <= kVfuseAutoB));
+    return nlev >= 2 && vf && (nu == 1 || nu == 2);
+  }
   const T* lam2T() { return reinterpret_cast<const T*>(c.lam2T.p); }
   FineOp<T> fop() { return view<T>(c, 0).fine_op(); }
   FineOp<double> fop64() { return view<double>(c, 0).fine_op(); }
@@ -415,6 +502,16 @@ struct Batch {
     return a;
   }
   const T* psfT();
+  // banded passes of the separable A^T A in precision T (correction rows of
+  // the matching precision)
+  Band<T> band_vt() {
+    return make_band<T>(c.sp_vt, std::is_same<T, double>::value ? reinterpret_cast<const T*>(c.sep_dv64.p)
+                                                                : reinterpret_cast<const T*>(c.sep_dv32.p));
+  }
+  Band<T> band_ht() {
+    return make_band<T>(c.sp_ht, std::is_same<T, double>::value ? reinterpret_cast<const T*>(c.sep_dh64.p)
+                                                                : reinterpret_cast<const T*>(c.sep_dh32.p));
+  }
 
   // q = K p (T precision) with partials of p.q; returns the partial count
   int apply_K(const T* P, T* Q, double* part);
@@ -435,15 +532,19 @@ struct Batch {
     // of the graph (a plain record would only express a dependency)
     LCMG_CUDA(cudaEventRecordWithFlags(c.tev[c.tev_used++], s, cudaEventRecordExternal));
   }
-  // after the stream has been synchronised: add the recorded pass times
+  // after the stream has been synchronised: add the recorded pass and
+  // V-cycle times (five events per timed iteration: the two operator
+  // passes, then the V-cycle)
   void collect_timing() {
     if (!c.prm.timing) return;
     int64_t b0 = 0, b1 = 0;
     op_bytes<T>(c, B, &b0, &b1);
-    for (int i = 0; i + 2 < c.tev_used; i += 3) {
-      float a = 0.f, b = 0.f;
+    const int64_t vb = vcycle_bytes();
+    for (int i = 0; i + 4 < c.tev_used; i += 5) {
+      float a = 0.f, b = 0.f, v = 0.f;
       if (cudaEventElapsedTime(&a, c.tev[i], c.tev[i + 1]) != cudaSuccess ||
-          cudaEventElapsedTime(&b, c.tev[i + 1], c.tev[i + 2]) != cudaSuccess) {
+          cudaEventElapsedTime(&b, c.tev[i + 1], c.tev[i + 2]) != cudaSuccess ||
+          cudaEventElapsedTime(&v, c.tev[i + 3], c.tev[i + 4]) != cudaSuccess) {
         cudaGetLastError();
         continue;
       }
@@ -451,7 +552,35 @@ struct Batch {
       c.stats.op_ms_at += b;
       c.stats.op_launches += 2;
       c.stats.op_bytes += b0 + b1;
+      c.stats.vcycle_ms += v;
+      c.stats.vcycle_count += 1;
+      c.stats.vcycle_bytes += vb;
     }
+  }
+  // Algorithmic DRAM bytes of one V-cycle of this batch in the two-kernels-
+  // per-level form: per level k (n_k points, s-byte vectors) the down kernel
+  // reads r and dinv and writes the pre-smoothed z and the coarse r (n_k / 4);
+  // the up kernel reads the coarse e, the pre-smoothed z, r and dinv and
+  // writes z: 7.5 s n_k per column; the smoother data (as stored) is read by
+  // both kernels; the coarsest level reads its inverse (n_c^2 doubles per
+  // column) and its r and writes its e.
+  int64_t vcycle_bytes() const {
+    const int64_t sT = sizeof(T);
+    int64_t bytes = 0;
+    for (int k = 0; k + 1 < nlev; ++k) {
+      const int64_t nk = c.lev[k].n;
+      int64_t coef = k == 0 ? 3 * sT : (int64_t)kCoefStride * sT;
+      if (c.h16_on) coef = k == 0 ? 3 * 2 : kCompactOff * 2 + 4;  // FP16 rows (+ FP32 row sum)
+      if (k == 0 && fine_v11()) {
+        // r twice, r_c and e_c (a quarter each), z once; no pre-smoothed z, no D^{-1}
+        bytes += (nk * 7 / 2) * sT * B + 2 * coef * nk;
+        continue;
+      }
+      bytes += (nk * 15 / 2) * sT * B + 2 * coef * nk;
+    }
+    const int64_t nc = c.lev[nlev - 1].n;
+    bytes += (nc * nc * 8 + 2 * nc * sT) * B;
+    return bytes;
   }
   // r64 = c64 - K x64 in FP64 with partials of r64.r64
   int true_residual(double* part);
@@ -498,18 +627,30 @@ struct Batch {
     std::vector<T*> zz(nlev);
     rhs[0] = r0; zz[0] = z0;
     for (int k = 1; k < nlev; ++k) { rhs[k] = tp(c.lw[k].rhs); zz[k] = tp(c.lw[k].z); }
-    // (the finest level's tiles hold the r.z partials: at most kMaxBlocks)
-    const int64_t tiles0 = (int64_t)((c.lev[0].nv / 2 + kVTile - 1) / kVTile) * ((c.lev[0].nh / 2 + kVTile - 1) / kVTile);
-    const bool vf = vf_force >= 0 ? vf_force == 1 : (c.prm.vfuse == 2 || (c.prm.vfuse == 1 && B <= kVfuseAutoB));
-    if (vf && (nu == 1 || nu == 2) && tiles0 <= kMaxBlocks) {
-      // two kernels per level: pre-smoothed z of level k goes to t[k]
-      for (int k = 0; k < nlev - 1; ++k)
-        launch_vdown<T>(view<T>(c, k), B, lam2T(), tp(c.lw[k].dinv), rhs[k], tp(c.lw[k].t), tp(c.lw[k + 1].rhs),
-                        nu, s);
+    if (vf_on()) {
+      // two kernels per level: pre-smoothed z of level k goes to t[k]; the
+      // finest level of a V(1,1) cycle in FP32 runs the kernels that form it
+      // on the fly (vfine.cuh)
+      const bool fine1 = fine_v11();
+      for (int k = 0; k < nlev - 1; ++k) {
+        if (k == 0 && fine1)
+          launch_vfine_down(view<float>(c, 0), B, reinterpret_cast<const float*>(lam2T()), c.prm.smoother,
+                            c.prm.omega, reinterpret_cast<const float*>(rhs[0]),
+                            reinterpret_cast<float*>(tp(c.lw[1].rhs)), s);
+        else
+          launch_vdown<T>(view<T>(c, k), B, lam2T(), tp(c.lw[k].dinv), rhs[k], tp(c.lw[k].t), tp(c.lw[k + 1].rhs),
+                          nu, s);
+      }
       launch_coarse_solve<T>((int)c.lev[nlev - 1].n, B, c.kinv.p, rhs[nlev - 1], zz[nlev - 1], s);
       for (int k = nlev - 2; k >= 0; --k) {
-        const int g = launch_vup<T>(view<T>(c, k), B, lam2T(), tp(c.lw[k].dinv), rhs[k], zz[k + 1],
-                                    tp(c.lw[k].t), zz[k], k == 0 ? part : nullptr, nu, s);
+        int g;
+        if (k == 0 && fine1)
+          g = launch_vfine_up(view<float>(c, 0), B, reinterpret_cast<const float*>(lam2T()), c.prm.smoother,
+                              c.prm.omega, reinterpret_cast<const float*>(rhs[0]),
+                              reinterpret_cast<const float*>(zz[1]), reinterpret_cast<float*>(zz[0]), part, s);
+        else
+          g = launch_vup<T>(view<T>(c, k), B, lam2T(), tp(c.lw[k].dinv), rhs[k], zz[k + 1], tp(c.lw[k].t), zz[k],
+                            k == 0 ? part : nullptr, nu, s);
         if (k == 0) nb = g;
       }
       return nb;
@@ -537,6 +678,22 @@ struct Batch {
     for (int j = 0; j < B; ++j) { l2[j] = lam[j] * lam[j]; l2t[j] = (T)l2[j]; }
     LCMG_CUDA(cudaMemcpyAsync(c.lam2.p, l2.data(), sizeof(double) * B, cudaMemcpyHostToDevice, s));
     LCMG_CUDA(cudaMemcpyAsync(c.lam2T.p, l2t.data(), sizeof(T) * B, cudaMemcpyHostToDevice, s));
+    // FP16 smoother data: every column at one lambda, the two-kernels-per-
+    // level cycle, mixed precision; the coarse rows of K(lambda) per lambda
+    bool one_lam = true;
+    for (int j = 1; j < B; ++j) one_lam = one_lam && lam[j] == lam[0];
+    c.h16_on = false;
+    if (std::is_same<T, float>::value && c.prm.smoother_fp16 && one_lam && !c.prm.autotune && vf_on()) {
+      for (int k = 1; k < nlev; ++k) {
+        Level& g = c.lev[k];
+        g.hscale = half_scale(l2[0] * g.glmax + g.gamax);
+        const int gg = (int)std::min<int64_t>((kCompactOff * g.n + kBlock - 1) / kBlock, c.maxblk);
+        klaunch(k_compact_rows, dim3(gg), dim3(kBlock), 0, s, g.n, (const double*)g.gl.p, (const double*)g.ga.p,
+                l2[0], g.hscale, g.hrows.p);
+        LCMG_LAUNCHED();
+      }
+      c.h16_on = true;
+    }
     for (int k = 0; k < nlev; ++k)
       launch_dinv<T>(view<T>(c, k), B, c.lam2.p, c.prm.smoother, c.prm.omega, tp(c.lw[k].dinv), c.maxblk, s);
     launch_dense_setup(view<double>(c, nlev - 1), B, c.lam2.p, c.Mw.p, c.Ww.p, c.kinv.p, c.s_info.p, c.maxblk, s);
@@ -573,7 +730,9 @@ struct Batch {
       LCMG_LAUNCHED();
       nb_rr = launch_update_xr<T, T>(c.n, B, st, P, Q, X, R, c.part_rr.p, c.maxblk, s);
     }
+    mark();
     const int nb_rz = vcycle(R, Z, c.part_rz.p);
+    mark();
     if (alpha_fused && c.prm.beta_fuse && !c.prm.keep_direction) {  // beta inside the p update
       launch_update_p_beta<T>(c.n, st, nb_rr, c.part_rr.p, nb_rz, c.part_rz.p, c.prm.maxit, trig, Z, P, c.maxblk, s);
       return;
@@ -843,6 +1002,13 @@ int Batch<T>::apply_K(const T* P, T* Q, double* part) {
                                                    nullptr, part, c.maxblk, s);
       }
     }
+  } else if (c.sep) {
+    // separable PSF: u = (I (x) T_v) p, then q = (T_h (x) I) u + lam^2 L^T W L p with p.q
+    launch_band<T, T, 0, BAND_STORE>(c.nv, c.nh, B, band_vt(), P, Y, fop(), nullptr, nullptr, nullptr, nullptr,
+                                     nullptr, c.maxblk, s);
+    mark();
+    nb = launch_band<T, T, 1, BAND_NORMAL>(c.nv, c.nh, B, band_ht(), Y, Q, fop(), P, nullptr, c.lam2.p, nullptr,
+                                           part, c.maxblk, s);
   } else {
     // PSF operator
     nb = grid_for(c.n, B, c.maxblk);
@@ -874,6 +1040,13 @@ int Batch<T>::true_residual(double* part) {
     return launch_spmm<float, double, double, 3>(at, c.vT32.p, Y, c.r64.p, fop64(), c.x64.p, c.c64.p, c.lam2.p,
                                                  nullptr, part, c.maxblk, s);
   }
+  if (c.sep) {
+    Band<double> bv = make_band<double>(c.sp_vt, c.sep_dv64.p), bh = make_band<double>(c.sp_ht, c.sep_dh64.p);
+    launch_band<double, double, 0, BAND_STORE>(c.nv, c.nh, B, bv, c.x64.p, Y, fop64(), nullptr, nullptr, nullptr,
+                                               nullptr, nullptr, c.maxblk, s);
+    return launch_band<double, double, 1, BAND_TRUERES>(c.nv, c.nh, B, bh, Y, c.r64.p, fop64(), c.x64.p, c.c64.p,
+                                                        c.lam2.p, nullptr, part, c.maxblk, s);
+  }
   const int g = grid_for(c.n, B, c.maxblk);
   PsfArgs pa = psf();
   klaunch(k_psf_forward<double, 0>, dim3(g), dim3(kBlock), 0, s, pa, c.psf64.p, B, c.x64.p, Y, nullptr, 1, 1, nullptr);
@@ -899,6 +1072,14 @@ static void compute_rhs(lcmg_ctx& c, int nrhs) {
     else
       launch_spmm<float, double, double, 0>(a, c.vT32.p, c.bvec.p, cv, f, nullptr, nullptr, nullptr, nullptr,
                                             nullptr, c.maxblk, c.stream);
+  } else if (c.sep) {
+    // A^T b = (A_h^T (x) A_v^T) b: the flipped 1-D correlations along i, then j
+    double* tmp = c.sep_tmp.need((size_t)c.n * nrhs);
+    FineOp<double> f = view<double>(c, 0).fine_op();
+    launch_band<double, double, 0, BAND_STORE>(c.nv, c.nh, nrhs, make_band<double>(c.sp_vat, nullptr), c.bvec.p, tmp,
+                                               f, nullptr, nullptr, nullptr, nullptr, nullptr, c.maxblk, c.stream);
+    launch_band<double, double, 1, BAND_STORE>(c.nv, c.nh, nrhs, make_band<double>(c.sp_hat, nullptr), tmp, cv, f,
+                                               nullptr, nullptr, nullptr, nullptr, nullptr, c.maxblk, c.stream);
   } else {
     PsfArgs pa{};
     pa.nv = c.nv; pa.nh = c.nh; pa.rv = c.rv; pa.rh = c.rh; pa.psf = c.psf64.p;
@@ -1499,6 +1680,15 @@ static void solve_columns(lcmg_ctx& c, const std::vector<ColSpec>& cols, int nrh
     else
       nb = launch_spmm<float, double, double, 2>(a, c.v32.p, c.x64.p, (double*)nullptr, f, nullptr, nullptr,
                                                  nullptr, bcol, c.part_x.p, c.maxblk, s);
+  } else if (c.sep) {
+    // A x = (A_h (x) A_v) x along i, then j with the partials of (A x - b)^2
+    double* tmp = c.sep_tmp.need((size_t)c.n * B);
+    FineOp<double> f = view<double>(c, 0).fine_op();
+    launch_band<double, double, 0, BAND_STORE>(c.nv, c.nh, B, make_band<double>(c.sp_va, nullptr), c.x64.p, tmp, f,
+                                               nullptr, nullptr, nullptr, nullptr, nullptr, c.maxblk, s);
+    nb = launch_band<double, double, 1, BAND_RESID2>(c.nv, c.nh, B, make_band<double>(c.sp_ha, nullptr), tmp,
+                                                     (double*)nullptr, f, nullptr, nullptr, nullptr, bcol, c.part_x.p,
+                                                     c.maxblk, s);
   } else {
     PsfArgs pa{};
     pa.nv = c.nv; pa.nh = c.nh; pa.rv = c.rv; pa.rh = c.rh; pa.psf = c.psf64.p;
@@ -1567,19 +1757,36 @@ static void solve_all(lcmg_ctx& c, int nl, const double* lam, int nrhs, const do
     }
     return;
   }
-  // sequential: per rhs, largest lambda first, each warm-started from the
-  // previous lambda's solution (Sec. 3.3); the first from x0 (if given)
-  for (int r = 0; r < nrhs; ++r) {
-    const double* prev = nullptr;
+  // sequential: largest lambda first, each right-hand side warm-started
+  // from its own solution at the previous lambda (Sec. 3.3), the first from
+  // x0 (if given).  The chains of the right-hand sides advance together: at
+  // each lambda one batch holds every right-hand side's system (they share
+  // lambda, so the operator, the hierarchy and its coefficients are read
+  // once for all of them); per column the iteration is the chain's own.
+  for (int r0 = 0; r0 < nrhs; r0 += kMaxB) {
+    const int cnt = std::min(kMaxB, nrhs - r0);
+    std::vector<const double*> prev(cnt, nullptr);
     for (int li = nl - 1; li >= 0; --li) {
-      const int64_t idx = (int64_t)r * nl + li;
-      std::vector<ColSpec> cols{{lam[li], r}};
-      const double* start = prev ? prev : (x0 ? x0 + idx * n : nullptr);
-      std::vector<const double*> x0s{start};
-      std::vector<double*> xs{x + idx * n};
-      solve_columns(c, cols, nrhs, x0s, xs, rho ? rho + idx : nullptr, eta ? eta + idx : nullptr,
-                    iters ? iters + idx : nullptr, status ? status + idx : nullptr);
-      prev = x + idx * n;
+      std::vector<ColSpec> cols(cnt);
+      std::vector<const double*> x0s(cnt);
+      std::vector<double*> xs(cnt);
+      std::vector<double> rh(cnt), eh(cnt);
+      std::vector<int> ih(cnt), sh(cnt);
+      for (int j = 0; j < cnt; ++j) {
+        const int64_t idx = (int64_t)(r0 + j) * nl + li;
+        cols[j] = ColSpec{lam[li], r0 + j};
+        x0s[j] = prev[j] ? prev[j] : (x0 ? x0 + idx * n : nullptr);
+        xs[j] = x + idx * n;
+      }
+      solve_columns(c, cols, nrhs, x0s, xs, rh.data(), eh.data(), ih.data(), sh.data());
+      for (int j = 0; j < cnt; ++j) {
+        const int64_t idx = (int64_t)(r0 + j) * nl + li;
+        if (rho) rho[idx] = rh[j];
+        if (eta) eta[idx] = eh[j];
+        if (iters) iters[idx] = ih[j];
+        if (status) status[idx] = sh[j];
+        prev[j] = xs[j];
+      }
     }
   }
 }
@@ -1805,6 +2012,8 @@ void lcmg_default_params(lcmg_params* p) {
   p->alpha_fuse = 1;
   p->beta_fuse = 1;
   p->spmv_variant_at = 0;
+  p->max_blocks = 0;
+  p->smoother_fp16 = 1;
 }
 
 const char* lcmg_last_error(void) { return lcmg::g_err.c_str(); }
@@ -1836,6 +2045,7 @@ int lcmg_create(lcmg_ctx** out, int device, void* stream, const lcmg_params* p) 
   LCMG_CUDA(cudaGetDeviceProperties(&prop, device));
   c->sms = prop.multiProcessorCount;
   c->maxblk = std::min(lcmg::kMaxBlocks, c->sms * 8);
+  if (prm.max_blocks > 0) c->maxblk = std::min(c->maxblk, prm.max_blocks);
   *out = c;
   API_END
 }
@@ -1861,6 +2071,8 @@ int lcmg_set_params(lcmg_ctx* ctx, const lcmg_params* p) {
                           p->coarsening != ctx->prm.coarsening;
   const bool amg_change = lev_change || p->amg_coarse_max != ctx->prm.amg_coarse_max;
   ctx->prm = *p;
+  ctx->maxblk = std::min(lcmg::kMaxBlocks, ctx->sms * 8);
+  if (p->max_blocks > 0) ctx->maxblk = std::min(ctx->maxblk, p->max_blocks);
   if (lev_change) ctx->hier_ok = false;
   if (amg_change) {
     ctx->am_ok = false;
@@ -2002,27 +2214,87 @@ int lcmg_set_forward_csr(lcmg_ctx* ctx, int64_t m, int64_t n, const int64_t* row
   API_END
 }
 
-int lcmg_set_forward_stencil(lcmg_ctx* ctx, int32_t kh, int32_t kw, const double* psf) {
-  API_BEGIN
-  NEED_CTX();
-  if (ctx->nv == 0) throw lcmg::ArgError("set_grid has not been called");
-  if (kh < 1 || kw < 1 || kh % 2 == 0 || kw % 2 == 0 || !psf) throw lcmg::ArgError("PSF sides must be odd");
-  if (kh > 2 * ctx->nv + 1 || kw > 2 * ctx->nh + 1) throw lcmg::ArgError("PSF larger than the image");
+namespace lcmg {
+// psf = fv fh^T to rounding?  fv = the row sums, fh = the column sums over
+// their total (exact for an outer product); accepted when every entry
+// matches the product within 1e-14 of the largest entry
+static bool rank_one(int kh, int kw, const double* psf, std::vector<double>& fv, std::vector<double>& fh) {
+  fv.assign(kh, 0.0);
+  fh.assign(kw, 0.0);
+  double tot = 0.0, amax = 0.0;
+  for (int u = 0; u < kh; ++u)
+    for (int v = 0; v < kw; ++v) {
+      fv[u] += psf[u * kw + v];
+      fh[v] += psf[u * kw + v];
+      tot += psf[u * kw + v];
+      amax = std::max(amax, std::fabs(psf[u * kw + v]));
+    }
+  if (!(tot != 0.0) || amax == 0.0) return false;
+  for (double& x : fh) x /= tot;
+  for (int u = 0; u < kh; ++u)
+    for (int v = 0; v < kw; ++v)
+      if (std::fabs(psf[u * kw + v] - fv[u] * fh[v]) > 1e-14 * amax) return false;
+  return true;
+}
+
+// The blur A = A_h (x) A_v of the 1-D correlations fv (along i) and fh
+// (along j), Sec. 4: banded passes of A^T A, A and A^T, their boundary
+// correction rows on the device, diag(A^T A) = T_v[i][i] T_h[j][j]
+static void set_separable(lcmg_ctx* c, const std::vector<double>& fv, const std::vector<double>& fh) {
+  c->sp_vt = sep_pass_ata(fv, c->nv);
+  c->sp_ht = sep_pass_ata(fh, c->nh);
+  c->sp_va = sep_pass_corr(fv, false);
+  c->sp_ha = sep_pass_corr(fh, false);
+  c->sp_vat = sep_pass_corr(fv, true);
+  c->sp_hat = sep_pass_corr(fh, true);
+  auto up = [&](const std::vector<double>& d, DevBuf<double>& b64, DevBuf<float>& b32) {
+    std::vector<float> f32(d.begin(), d.end());
+    copy_sync(c->stream, b64.need(d.size()), d.data(), sizeof(double) * d.size(), cudaMemcpyHostToDevice);
+    copy_sync(c->stream, b32.need(d.size()), f32.data(), sizeof(float) * d.size(), cudaMemcpyHostToDevice);
+  };
+  up(c->sp_vt.d, c->sep_dv64, c->sep_dv32);
+  up(c->sp_ht.d, c->sep_dh64, c->sep_dh32);
+  const std::vector<double> dv = sep_diag(c->sp_vt, c->nv), dh = sep_diag(c->sp_ht, c->nh);
+  DevBuf<double> ddv, ddh;
+  copy_sync(c->stream, ddv.need(dv.size()), dv.data(), sizeof(double) * dv.size(), cudaMemcpyHostToDevice);
+  copy_sync(c->stream, ddh.need(dh.size()), dh.data(), sizeof(double) * dh.size(), cudaMemcpyHostToDevice);
+  launch_sep_diag(c->nv, c->nh, ddv.p, ddh.p, c->diag.need(c->n), c->maxblk, c->stream);
+  LCMG_CUDA(cudaStreamSynchronize(c->stream));
+  prepare_band();
+  c->sep = true;
+}
+
+// common part of the stencil setters: store the 2-D PSF, pick the form
+static void set_stencil(lcmg_ctx* ctx, int32_t kh, int32_t kw, const double* psf, const std::vector<double>* fv,
+                        const std::vector<double>* fh) {
+  if (ctx->nv == 0) throw ArgError("set_grid has not been called");
+  if (kh > 2 * ctx->nv + 1 || kw > 2 * ctx->nh + 1) throw ArgError("PSF larger than the image");
   for (int i = 0; i < kh * kw; ++i)
-    if (!std::isfinite(psf[i])) throw lcmg::ArgError("PSF values must be finite");
+    if (!std::isfinite(psf[i])) throw ArgError("PSF values must be finite");
   LCMG_CUDA(cudaSetDevice(ctx->device));
   ctx->rv = kh / 2;
   ctx->rh = kw / 2;
   ctx->m = ctx->n;
-  lcmg::copy_sync(ctx->stream, ctx->psf64.need(kh * kw), psf, sizeof(double) * kh * kw, cudaMemcpyHostToDevice);
+  ctx->sep = false;
+  copy_sync(ctx->stream, ctx->psf64.need(kh * kw), psf, sizeof(double) * kh * kw, cudaMemcpyHostToDevice);
   std::vector<float> pf(psf, psf + kh * kw);
-  lcmg::copy_sync(ctx->stream, ctx->psf32.need(kh * kw), pf.data(), sizeof(float) * kh * kw, cudaMemcpyHostToDevice);
-  lcmg::PsfArgs pa{};
-  pa.nv = ctx->nv; pa.nh = ctx->nh; pa.rv = ctx->rv; pa.rh = ctx->rh; pa.psf = ctx->psf64.p;
-  const int g = (int)std::min<int64_t>((ctx->n + lcmg::kBlock - 1) / lcmg::kBlock, ctx->maxblk);
-  klaunch(lcmg::k_psf_diag, dim3(g), dim3(lcmg::kBlock), 0, ctx->stream, pa, ctx->diag.need(ctx->n));
-  LCMG_LAUNCHED();
-  klaunch(lcmg::k_convert<double, float>, dim3(g), dim3(lcmg::kBlock), 0, ctx->stream, ctx->n, ctx->diag.p, ctx->diag32.need(ctx->n));
+  copy_sync(ctx->stream, ctx->psf32.need(kh * kw), pf.data(), sizeof(float) * kh * kw, cudaMemcpyHostToDevice);
+  std::vector<double> av, ah;
+  const bool fits = 2 * ctx->rv <= kBandMaxH && 2 * ctx->rh <= kBandMaxH;
+  if (fits && fv) {
+    set_separable(ctx, *fv, *fh);
+  } else if (fits && rank_one(kh, kw, psf, av, ah)) {
+    set_separable(ctx, av, ah);
+  } else {
+    PsfArgs pa{};
+    pa.nv = ctx->nv; pa.nh = ctx->nh; pa.rv = ctx->rv; pa.rh = ctx->rh; pa.psf = ctx->psf64.p;
+    const int g = (int)std::min<int64_t>((ctx->n + kBlock - 1) / kBlock, ctx->maxblk);
+    klaunch(k_psf_diag, dim3(g), dim3(kBlock), 0, ctx->stream, pa, ctx->diag.need(ctx->n));
+    LCMG_LAUNCHED();
+  }
+  const int g = (int)std::min<int64_t>((ctx->n + kBlock - 1) / kBlock, ctx->maxblk);
+  klaunch(k_convert<double, float>, dim3(g), dim3(kBlock), 0, ctx->stream, ctx->n, ctx->diag.p,
+          ctx->diag32.need(ctx->n));
   LCMG_LAUNCHED();
   LCMG_CUDA(cudaStreamSynchronize(ctx->stream));
   ctx->fwd = 2;
@@ -2031,6 +2303,34 @@ int lcmg_set_forward_stencil(lcmg_ctx* ctx, int32_t kh, int32_t kw, const double
   ctx->pm_levels = 0;
   ctx->am_ok = false;
   ctx->hier_ok = false;
+}
+}  // namespace lcmg
+
+int lcmg_set_forward_stencil(lcmg_ctx* ctx, int32_t kh, int32_t kw, const double* psf) {
+  API_BEGIN
+  NEED_CTX();
+  if (kh < 1 || kw < 1 || kh % 2 == 0 || kw % 2 == 0 || !psf) throw lcmg::ArgError("PSF sides must be odd");
+  lcmg::set_stencil(ctx, kh, kw, psf, nullptr, nullptr);
+  API_END
+}
+
+int lcmg_set_forward_separable(lcmg_ctx* ctx, int32_t kh, const double* fv, int32_t kw, const double* fh) {
+  API_BEGIN
+  NEED_CTX();
+  if (kh < 1 || kw < 1 || kh % 2 == 0 || kw % 2 == 0 || !fv || !fh)
+    throw lcmg::ArgError("filter lengths must be odd");
+  std::vector<double> a(fv, fv + kh), b(fh, fh + kw), psf((size_t)kh * kw);
+  for (int u = 0; u < kh; ++u)
+    for (int v = 0; v < kw; ++v) psf[(size_t)u * kw + v] = a[u] * b[v];
+  lcmg::set_stencil(ctx, kh, kw, psf.data(), &a, &b);
+  API_END
+}
+
+int lcmg_forward_form(lcmg_ctx* ctx, int32_t* form) {
+  API_BEGIN
+  NEED_CTX();
+  if (!form) throw lcmg::ArgError("null output pointer");
+  *form = ctx->fwd == 2 ? (ctx->sep ? 3 : 2) : ctx->fwd;
   API_END
 }
 

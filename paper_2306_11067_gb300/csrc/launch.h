@@ -1,7 +1,11 @@
 // Host-side launchers of the device kernels (explicitly instantiated in
 // launch_spmm.cu and launch_level.cu).
 #pragma once
+#include <vector>
+
 #include "kernels.cuh"
+#include "compact.cuh"
+#include "separable.cuh"
 
 namespace lcmg {
 
@@ -15,6 +19,11 @@ struct LevelView {
   const T* we = nullptr;
   const T* ga = nullptr;  // fine: diag(A^T A)
   const T* cf = nullptr;  // coarse: per-point coefficient rows
+  // FP16 smoother data (T = float, a batch whose columns share lambda): the
+  // level's operators below replace ws/we/ga and cf in the V-cycle
+  bool h16 = false;
+  FineOpH fh{};
+  CoarseOpH ch{};
   FineOp<T> fine_op() const { return FineOp<T>{nv, nh, ws, we, ga}; }
   CoarseOp<T> coarse_op() const { return CoarseOp<T>{nv, nh, n, cf}; }
 };
@@ -52,6 +61,15 @@ int launch_vdown(const LevelView<T>& L, int B, const T* lam2, const T* dinv, con
 template <class T>
 int launch_vup(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const T* r, const T* ec,
                const T* zpre, T* zout, double* part, int nu, cudaStream_t s);
+// The finest level of the V(1,1) cycle for FP32 vectors (vfine.cuh): down
+// = z1 = D^{-1} r, residual and restriction (-> rc); up = z1 + P ec and one
+// sweep (-> zout, r.z partials into part when set).  D^{-1} from the stored
+// weights (smoother 0: l1-Jacobi, 1: damped Jacobi with omega).  Return
+// their block counts.
+int launch_vfine_down(const LevelView<float>& L, int B, const float* lam2, int smoother, double omega,
+                      const float* r, float* rc, cudaStream_t s);
+int launch_vfine_up(const LevelView<float>& L, int B, const float* lam2, int smoother, double omega,
+                    const float* r, const float* ec, float* zout, double* part, cudaStream_t s);
 template <class T>
 void launch_prolong_add(int nvc, int nhc, int B, const T* ec, T* zf, int max_blocks, cudaStream_t s);
 template <class T>
@@ -78,5 +96,37 @@ void launch_update_p_beta(int64_t n, const ColState& st, int nb_rr, const double
 template <class T>
 void launch_copy_cols(int64_t n, int B, const int* flag, const T* src, T* dst, int max_blocks,
                       cudaStream_t s);
+
+// ---- separable blur (separable.cu) ----------------------------------------
+// One banded 1-D pass in FP64 as built on the host: out(o) = sum_k
+// c[k] in(o - H + k), plus the correction rows d of the first nlo and the
+// last nhi outputs of a line (empty for a plain correlation).
+struct SepPass {
+  int H = 0;
+  std::vector<double> c;
+  int nlo = 0, nhi = 0;
+  std::vector<double> d;
+};
+// the 1-D correlation with taps f (2r + 1 values) or its transpose
+SepPass sep_pass_corr(const std::vector<double>& f, bool transpose);
+// A^T A of that correlation on a line of len samples (zero boundary)
+SepPass sep_pass_ata(const std::vector<double>& f, int len);
+// the diagonal of a sep_pass_ata pass (len values)
+std::vector<double> sep_diag(const SepPass& p, int len);
+// device form of a pass whose correction rows live at d_dev
+template <class T>
+Band<T> make_band(const SepPass& p, const T* d_dev);
+// one pass over every line of an n_v x n_h image and B interleaved columns
+// (DIR 0: along i, DIR 1: along j with the epilogue EPI); returns the
+// block count (rows of the partial sums when EPI writes any)
+template <class T, class TO, int DIR, int EPI>
+int launch_band(int nv, int nh, int B, const Band<T>& bd, const T* in, TO* out, const FineOp<T>& fop, const T* P,
+                const T* C, const double* lam2, const double* bvec, double* part, int max_blocks, cudaStream_t s);
+// opt every k_band instantiation into its shared memory on the current
+// device (outside stream capture)
+void prepare_band();
+// diag(A^T A)_p = dv[i] dh[j]
+void launch_sep_diag(int nv, int nh, const double* dv, const double* dh, double* diag, int max_blocks,
+                     cudaStream_t s);
 
 }  // namespace lcmg

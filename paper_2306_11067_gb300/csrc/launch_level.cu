@@ -1,6 +1,13 @@
 // Launchers of the V-cycle level kernels, the coarsest-level dense setup,
 // the Galerkin products and the PCG vector updates.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <type_traits>
+#include <utility>
+
 #include "launch.h"
+#include "vfine.cuh"
 #include "vfused.cuh"
 
 namespace lcmg {
@@ -9,6 +16,16 @@ template <class T>
 void launch_dinv(const LevelView<T>& L, int B, const double* lam2, int smoother, double omega,
                  T* dinv, int max_blocks, cudaStream_t s) {
   const int g = grid_for(L.n, B, max_blocks);
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.h16) {
+      if (L.fine)
+        klaunch(k_dinv<FineOpH, float>, dim3(g), dim3(kBlock), 0, s, L.fh, L.n, B, lam2, smoother, omega, dinv);
+      else
+        klaunch(k_dinv<CoarseOpH, float>, dim3(g), dim3(kBlock), 0, s, L.ch, L.n, B, lam2, smoother, omega, dinv);
+      LCMG_LAUNCHED();
+      return;
+    }
+  }
   if (L.fine)
     klaunch(k_dinv<FineOp<T>, T>, dim3(g), dim3(kBlock), 0, s, L.fine_op(), L.n, B, lam2, smoother, omega, dinv);
   else
@@ -51,36 +68,138 @@ void launch_residual(const LevelView<T>& L, int B, const T* lam2, const T* r, co
   LCMG_LAUNCHED();
 }
 
+// Grid of a tile kernel: every tile once, at most the blocks resident at
+// once on the device and at most kMaxTileBlocks (rows of the partial sums).
+template <class K>
+static int tile_grid(K kern, int threads, int ntiles) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  int dev = 0;
+  LCMG_CUDA(cudaGetDevice(&dev));
+  const auto key = std::make_pair(reinterpret_cast<const void*>(kern), dev);
+  int wave;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+      int nb = 0, sms = 0;
+      LCMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, 0));
+      LCMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      it = cache.emplace(key, std::max(1, nb) * sms).first;
+    }
+    wave = it->second;
+  }
+  return std::max(1, std::min(std::min(ntiles, wave), kMaxTileBlocks));
+}
+
+template <class Op, class T, int NU>
+static int vdown_one(const Op& op, int B, const T* lam2, const T* dinv, const T* r, T* zpre, T* rc, int ntx,
+                     int ntiles, cudaStream_t s) {
+  auto k = k_vdown<Op, T, NU>;
+  const int g = tile_grid(k, vtile_threads<Op, T, NU>(), ntiles);
+  klaunch(k, dim3((unsigned)g, (unsigned)B), dim3(vtile_threads<Op, T, NU>()), 0, s, op, B, lam2, dinv, r, zpre, rc,
+          ntx, ntiles);
+  return g;
+}
+
+template <class Op, class T, int NU>
+static int vup_one(const Op& op, int B, const T* lam2, const T* dinv, const T* r, const T* ec, const T* zpre,
+                   T* zout, double* part, int ntx, int ntiles, cudaStream_t s) {
+  auto k = k_vup<Op, T, NU>;
+  const int g = tile_grid(k, vtile_threads<Op, T, NU>(), ntiles);
+  klaunch(k, dim3((unsigned)g, (unsigned)B), dim3(vtile_threads<Op, T, NU>()), 0, s, op, B, lam2, dinv, r, ec, zpre,
+          zout, ntx, ntiles, part);
+  return g;
+}
+
 template <class T>
 int launch_vdown(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const T* r, T* zpre, T* rc,
                  int nu, cudaStream_t s) {
   const int ntx = (L.nv / 2 + kVTile - 1) / kVTile, nty = (L.nh / 2 + kVTile - 1) / kVTile;
-  const dim3 grid((unsigned)(ntx * nty), (unsigned)B);
-  if (L.fine) {
-    if (nu == 1) klaunch(k_vdown<FineOp<T>, T, 1>, grid, dim3(vtile_threads<FineOp<T>, T, 1>()), 0, s, L.fine_op(), B, lam2, dinv, r, zpre, rc, ntx);
-    else klaunch(k_vdown<FineOp<T>, T, 2>, grid, dim3(vtile_threads<FineOp<T>, T, 2>()), 0, s, L.fine_op(), B, lam2, dinv, r, zpre, rc, ntx);
-  } else {
-    if (nu == 1) klaunch(k_vdown<CoarseOp<T>, T, 1>, grid, dim3(vtile_threads<CoarseOp<T>, T, 1>()), 0, s, L.coarse_op(), B, lam2, dinv, r, zpre, rc, ntx);
-    else klaunch(k_vdown<CoarseOp<T>, T, 2>, grid, dim3(vtile_threads<CoarseOp<T>, T, 2>()), 0, s, L.coarse_op(), B, lam2, dinv, r, zpre, rc, ntx);
+  const int nt = ntx * nty;
+  int g;
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.h16) {
+      if (L.fine)
+        g = nu == 1 ? vdown_one<FineOpH, float, 1>(L.fh, B, lam2, dinv, r, zpre, rc, ntx, nt, s)
+                    : vdown_one<FineOpH, float, 2>(L.fh, B, lam2, dinv, r, zpre, rc, ntx, nt, s);
+      else
+        g = nu == 1 ? vdown_one<CoarseOpH, float, 1>(L.ch, B, lam2, dinv, r, zpre, rc, ntx, nt, s)
+                    : vdown_one<CoarseOpH, float, 2>(L.ch, B, lam2, dinv, r, zpre, rc, ntx, nt, s);
+      LCMG_LAUNCHED();
+      return g;
+    }
   }
+  if (L.fine)
+    g = nu == 1 ? vdown_one<FineOp<T>, T, 1>(L.fine_op(), B, lam2, dinv, r, zpre, rc, ntx, nt, s)
+                : vdown_one<FineOp<T>, T, 2>(L.fine_op(), B, lam2, dinv, r, zpre, rc, ntx, nt, s);
+  else
+    g = nu == 1 ? vdown_one<CoarseOp<T>, T, 1>(L.coarse_op(), B, lam2, dinv, r, zpre, rc, ntx, nt, s)
+                : vdown_one<CoarseOp<T>, T, 2>(L.coarse_op(), B, lam2, dinv, r, zpre, rc, ntx, nt, s);
   LCMG_LAUNCHED();
-  return ntx * nty;
+  return g;
 }
 
 template <class T>
 int launch_vup(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const T* r, const T* ec,
                const T* zpre, T* zout, double* part, int nu, cudaStream_t s) {
   const int ntx = (L.nv / 2 + kVTile - 1) / kVTile, nty = (L.nh / 2 + kVTile - 1) / kVTile;
-  const dim3 grid((unsigned)(ntx * nty), (unsigned)B);
-  if (L.fine) {
-    if (nu == 1) klaunch(k_vup<FineOp<T>, T, 1>, grid, dim3(vtile_threads<FineOp<T>, T, 1>()), 0, s, L.fine_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
-    else klaunch(k_vup<FineOp<T>, T, 2>, grid, dim3(vtile_threads<FineOp<T>, T, 2>()), 0, s, L.fine_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
+  const int nt = ntx * nty;
+  int g;
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.h16) {
+      if (L.fine)
+        g = nu == 1 ? vup_one<FineOpH, float, 1>(L.fh, B, lam2, dinv, r, ec, zpre, zout, part, ntx, nt, s)
+                    : vup_one<FineOpH, float, 2>(L.fh, B, lam2, dinv, r, ec, zpre, zout, part, ntx, nt, s);
+      else
+        g = nu == 1 ? vup_one<CoarseOpH, float, 1>(L.ch, B, lam2, dinv, r, ec, zpre, zout, part, ntx, nt, s)
+                    : vup_one<CoarseOpH, float, 2>(L.ch, B, lam2, dinv, r, ec, zpre, zout, part, ntx, nt, s);
+      LCMG_LAUNCHED();
+      return g;
+    }
+  }
+  if (L.fine)
+    g = nu == 1 ? vup_one<FineOp<T>, T, 1>(L.fine_op(), B, lam2, dinv, r, ec, zpre, zout, part, ntx, nt, s)
+                : vup_one<FineOp<T>, T, 2>(L.fine_op(), B, lam2, dinv, r, ec, zpre, zout, part, ntx, nt, s);
+  else
+    g = nu == 1 ? vup_one<CoarseOp<T>, T, 1>(L.coarse_op(), B, lam2, dinv, r, ec, zpre, zout, part, ntx, nt, s)
+                : vup_one<CoarseOp<T>, T, 2>(L.coarse_op(), B, lam2, dinv, r, ec, zpre, zout, part, ntx, nt, s);
+  LCMG_LAUNCHED();
+  return g;
+}
+
+int launch_vfine_down(const LevelView<float>& L, int B, const float* lam2, int smoother, double omega,
+                      const float* r, float* rc, cudaStream_t s) {
+  const int nt = ((L.nv + kFineTI - 1) / kFineTI) * ((L.nh + kFineTJ - 1) / kFineTJ);
+  int g;
+  if (L.h16) {
+    g = tile_grid(k_vfine_down<FineOpH>, kFineThreads, nt);
+    klaunch(k_vfine_down<FineOpH>, dim3((unsigned)g, (unsigned)B), dim3(kFineThreads), 0, s, L.fh, B, lam2, smoother,
+            (float)omega, r, rc, nt);
   } else {
-    if (nu == 1) klaunch(k_vup<CoarseOp<T>, T, 1>, grid, dim3(vtile_threads<CoarseOp<T>, T, 1>()), 0, s, L.coarse_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
-    else klaunch(k_vup<CoarseOp<T>, T, 2>, grid, dim3(vtile_threads<CoarseOp<T>, T, 2>()), 0, s, L.coarse_op(), B, lam2, dinv, r, ec, zpre, zout, ntx, part);
+    g = tile_grid(k_vfine_down<FineOp<float>>, kFineThreads, nt);
+    klaunch(k_vfine_down<FineOp<float>>, dim3((unsigned)g, (unsigned)B), dim3(kFineThreads), 0, s, L.fine_op(), B,
+            lam2, smoother, (float)omega, r, rc, nt);
   }
   LCMG_LAUNCHED();
-  return ntx * nty;
+  return g;
+}
+
+int launch_vfine_up(const LevelView<float>& L, int B, const float* lam2, int smoother, double omega,
+                    const float* r, const float* ec, float* zout, double* part, cudaStream_t s) {
+  const int nt = ((L.nv + kFineTI - 1) / kFineTI) * ((L.nh + kFineTJ - 1) / kFineTJ);
+  int g;
+  if (L.h16) {
+    g = tile_grid(k_vfine_up<FineOpH>, kFineThreads, nt);
+    klaunch(k_vfine_up<FineOpH>, dim3((unsigned)g, (unsigned)B), dim3(kFineThreads), 0, s, L.fh, B, lam2, smoother,
+            (float)omega, r, ec, zout, nt, part);
+  } else {
+    g = tile_grid(k_vfine_up<FineOp<float>>, kFineThreads, nt);
+    klaunch(k_vfine_up<FineOp<float>>, dim3((unsigned)g, (unsigned)B), dim3(kFineThreads), 0, s, L.fine_op(), B,
+            lam2, smoother, (float)omega, r, ec, zout, nt, part);
+  }
+  LCMG_LAUNCHED();
+  return g;
 }
 
 template <class T>

@@ -23,6 +23,7 @@
 namespace lcmg {
 
 constexpr int kVTile = 8;  // coarse points per tile side
+constexpr int kMaxTileBlocks = 2048;  // grid cap of the tile kernels (rows of their partial sums)
 // threads of a tile block: enough for one point per thread in every phase
 // (the widest window is 22 x 22 on the 5-point finest level and 26 x 26 on
 // the 25-point levels with nu = 2; with nu = 1 the 25-point windows are at
@@ -49,10 +50,11 @@ __device__ __forceinline__ void vblock_sum(double v, double* sred, double* part,
   }
 }
 
+// k_vdown on tile (tx, ty) of column blockIdx.y
 template <class Op, class T, int NU>
-__global__ void __launch_bounds__(vtile_threads<Op, T, NU>())
-    k_vdown(Op op, int B, const T* __restrict__ lam2, const T* __restrict__ dinv, const T* __restrict__ r,
-            T* __restrict__ zpre, T* __restrict__ rc, int ntx) {
+__device__ __forceinline__ void vdown_tile(const Op& op, int B, const T* __restrict__ lam2,
+                                           const T* __restrict__ dinv, const T* __restrict__ r,
+                                           T* __restrict__ zpre, T* __restrict__ rc, int tx, int ty) {
   constexpr int NTD = vtile_threads<Op, T, NU>();
   constexpr int H = Op::kRadius;
   constexpr int WR = 2 * kVTile + 2;                  // restriction window
@@ -62,7 +64,6 @@ __global__ void __launch_bounds__(vtile_threads<Op, T, NU>())
   __shared__ T sz[(NU == 2) ? WZ * WZ : 1];
   __shared__ T sres[WR * WR];
   const int col = blockIdx.y;
-  const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
   const int nv = op.nv, nh = op.nh, nvc = nv / 2, nhc = nh / 2;
   const int I0 = tx * kVTile, J0 = ty * kVTile;
   const int ri = 2 * I0 - 1, rj = 2 * J0 - 1;  // window origins (fine coordinates)
@@ -167,11 +168,12 @@ __global__ void __launch_bounds__(vtile_threads<Op, T, NU>())
   }
 }
 
+// k_vup on tile (tx, ty) of column blockIdx.y; returns the tile's part of r.z
 template <class Op, class T, int NU>
-__global__ void __launch_bounds__(vtile_threads<Op, T, NU>())
-    k_vup(Op op, int B, const T* __restrict__ lam2, const T* __restrict__ dinv, const T* __restrict__ r,
-          const T* __restrict__ ec, const T* __restrict__ zpre, T* __restrict__ zout, int ntx,
-          double* __restrict__ part) {
+__device__ __forceinline__ double vup_tile(const Op& op, int B, const T* __restrict__ lam2,
+                                           const T* __restrict__ dinv, const T* __restrict__ r,
+                                           const T* __restrict__ ec, const T* __restrict__ zpre,
+                                           T* __restrict__ zout, int tx, int ty) {
   constexpr int NTD = vtile_threads<Op, T, NU>();
   constexpr int H = Op::kRadius;
   constexpr int WF = 2 * kVTile;           // the tile's fine points
@@ -179,10 +181,7 @@ __global__ void __launch_bounds__(vtile_threads<Op, T, NU>())
   constexpr int W1 = WF + 2 * H;           // window after the first of two sweeps
   __shared__ T s0[W0 * W0];
   __shared__ T s1[(NU == 2) ? W1 * W1 : 1];
-  constexpr int NT = vtile_threads<Op, T, NU>();
-  __shared__ double sred[NT / 32];
   const int col = blockIdx.y;
-  const int tx = blockIdx.x % ntx, ty = blockIdx.x / ntx;
   const int nv = op.nv, nh = op.nh, nvc = nv / 2, nhc = nh / 2;
   const int fi = 2 * tx * kVTile, fj = 2 * ty * kVTile;
   const int oi = fi - NU * H, oj = fj - NU * H;
@@ -283,7 +282,34 @@ __global__ void __launch_bounds__(vtile_threads<Op, T, NU>())
     zout[p * B + col] = zn;
     dacc += to_d(rv) * to_d(zn);
   }
-  if (part) vblock_sum<NT>(dacc, sred, part, B, col);
+  return dacc;
+}
+
+// Grid-stride over the tiles (any number of them: the grid is capped at
+// the blocks resident at once); r.z partials per block.
+template <class Op, class T, int NU>
+__global__ void __launch_bounds__(vtile_threads<Op, T, NU>())
+    k_vdown(Op op, int B, const T* __restrict__ lam2, const T* __restrict__ dinv, const T* __restrict__ r,
+            T* __restrict__ zpre, T* __restrict__ rc, int ntx, int ntiles) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    vdown_tile<Op, T, NU>(op, B, lam2, dinv, r, zpre, rc, t % ntx, t / ntx);
+    __syncthreads();  // the tile's shared arrays are refilled by the next tile
+  }
+}
+
+template <class Op, class T, int NU>
+__global__ void __launch_bounds__(vtile_threads<Op, T, NU>())
+    k_vup(Op op, int B, const T* __restrict__ lam2, const T* __restrict__ dinv, const T* __restrict__ r,
+          const T* __restrict__ ec, const T* __restrict__ zpre, T* __restrict__ zout, int ntx, int ntiles,
+          double* __restrict__ part) {
+  constexpr int NT = vtile_threads<Op, T, NU>();
+  __shared__ double sred[NT / 32];
+  double dacc = 0.0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    dacc += vup_tile<Op, T, NU>(op, B, lam2, dinv, r, ec, zpre, zout, t % ntx, t / ntx);
+    __syncthreads();
+  }
+  if (part) vblock_sum<NT>(dacc, sred, part, B, blockIdx.y);
 }
 
 }  // namespace lcmg

@@ -46,7 +46,8 @@ class lcmg_params(C.Structure):
                 ("precond", C.c_int32), ("gmres_restart", C.c_int32),
                 ("coarsening", C.c_int32), ("amg_coarse_max", C.c_int32), ("compact_cols", C.c_int32),
                 ("alpha_fuse", C.c_int32), ("beta_fuse", C.c_int32),
-                ("spmv_variant_at", C.c_int32)]
+                ("spmv_variant_at", C.c_int32), ("max_blocks", C.c_int32),
+                ("smoother_fp16", C.c_int32)]
 
 
 class lcmg_stats(C.Structure):
@@ -54,7 +55,8 @@ class lcmg_stats(C.Structure):
                 ("kernel_launches", C.c_int64), ("iterate_ms", C.c_double),
                 ("op_ms_a", C.c_double), ("op_ms_at", C.c_double),
                 ("op_launches", C.c_int64), ("op_bytes", C.c_int64),
-                ("tuned_spmv_a", C.c_int32), ("tuned_spmv_at", C.c_int32), ("tuned_vfuse", C.c_int32)]
+                ("tuned_spmv_a", C.c_int32), ("tuned_spmv_at", C.c_int32), ("tuned_vfuse", C.c_int32),
+                ("vcycle_ms", C.c_double), ("vcycle_count", C.c_int64), ("vcycle_bytes", C.c_int64)]
 
 
 class lcmg_problem(C.Structure):
@@ -101,6 +103,8 @@ _SIGS = {
     "lcmg_set_grid": (C.c_int, [_P, _I32, _I32]),
     "lcmg_set_forward_csr": (C.c_int, [_P, _I64, _I64, _P, _P, _P, _I32]),
     "lcmg_set_forward_stencil": (C.c_int, [_P, _I32, _I32, _P]),
+    "lcmg_set_forward_separable": (C.c_int, [_P, _I32, _P, _I32, _P]),
+    "lcmg_forward_form": (C.c_int, [_P, _PI32]),
     "lcmg_set_weights": (C.c_int, [_P, _P, _I64]),
     "lcmg_set_weights_dev": (C.c_int, [_P, _P, _I64]),
     "lcmg_get_weights": (C.c_int, [_P, _P, _I64]),
@@ -122,6 +126,7 @@ _SIGS = {
     "lcmg_get_level": (C.c_int, [_P, _I32, _PI32, _PI32, _P, _P]),
     "lcmg_num_levels": (C.c_int, [_P, _PI32]),
     "lcmg_get_diag": (C.c_int, [_P, _P]),
+    "lcmg_fma_peak": (C.c_int, [C.c_int, _I32, _PD]),
     "lcmg_apply_normal_noalloc": (C.c_int, [C.c_int, _P, _I32, _I32, _I64, _P, _P, _P, _P, _P, _P, _I32, _P,
                                             _I32, _P, _P, _P]),
     "lcmg_server_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_size_t, _I32, C.POINTER(lcmg_params)]),
@@ -222,6 +227,20 @@ def lcmg_set_forward_csr(ctx, m, n, row_ptr, col, val):
 def lcmg_set_forward_stencil(ctx, psf):
     p = _f64(psf)
     _check(lib().lcmg_set_forward_stencil(ctx, p.shape[0], p.shape[1], _ptr(p)))
+
+
+def lcmg_set_forward_separable(ctx, fv, fh):
+    a, b = _f64(fv), _f64(fh)
+    _check(lib().lcmg_set_forward_separable(ctx, a.size, _ptr(a), b.size, _ptr(b)))
+
+
+FORM_NONE, FORM_CSR, FORM_PSF2D, FORM_SEPARABLE = 0, 1, 2, 3
+
+
+def lcmg_forward_form(ctx) -> int:
+    f = C.c_int32(0)
+    _check(lib().lcmg_forward_form(ctx, C.byref(f)))
+    return int(f.value)
 
 
 def lcmg_set_weights(ctx, d):
@@ -408,6 +427,13 @@ def lcmg_apply_normal_noalloc(device, stream, n_v, n_h, m, row_ptr, col, val, ro
                                            _ptr(lam), _ptr(p), _ptr(q)))
 
 
+def lcmg_fma_peak(device: int, precision: int) -> float:
+    """Measured FP64 (PREC_FP64) or FP32 (PREC_MIXED) multiply-add peak, TFLOP/s."""
+    v = C.c_double(0.0)
+    _check(lib().lcmg_fma_peak(device, precision, C.byref(v)))
+    return float(v.value)
+
+
 def lcmg_get_diag(ctx, n: int):
     out = np.empty(n)
     _check(lib().lcmg_get_diag(ctx, _ptr(out)))
@@ -440,6 +466,12 @@ class Solver:
 
     def set_forward_stencil(self, psf):
         lcmg_set_forward_stencil(self.ctx, psf)
+
+    def set_forward_separable(self, fv, fh):
+        lcmg_set_forward_separable(self.ctx, fv, fh)
+
+    def forward_form(self):
+        return lcmg_forward_form(self.ctx)
 
     def set_weights(self, d):
         lcmg_set_weights(self.ctx, d)

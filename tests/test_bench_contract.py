@@ -29,10 +29,11 @@ def test_command_line_modes_parse(monkeypatch):
     for argv in (["bench.py"], ["bench.py", "--gpus", "2", "--steps", "4", "--warmup", "3"],
                  ["bench.py", "--impl", "reference"], ["bench.py", "--compare-precond"],
                  ["bench.py", "--compare-algorithm2"], ["bench.py", "--profile-iters", "48", "--profile-precond", "2"],
-                 ["bench.py", "--no-serve", "--no-cpu", "--no-plain", "--precision", "fp64", "--mode", "batched"]):
+                 ["bench.py", "--no-serve", "--no-cpu", "--no-plain", "--precision", "fp64", "--mode", "batched"],
+                 ["bench.py", "--workload", "ct256"], ["bench.py", "--workload", "deblur2048", "--impl", "reference"]):
         monkeypatch.setattr(sys, "argv", argv)
         args = bench.parse()
         assert args.warmup >= 3 or "--warmup" not in argv
     monkeypatch.setattr(sys, "argv", ["bench.py"])
     a = bench.parse()
-    assert (a.gpus, a.steps, a.warmup, a.impl) == (1, 3, 3, "ours")
+    assert (a.gpus, a.steps, a.warmup, a.impl, a.workload) == (1, 5, 3, "ours", "deblur2048")

@@ -47,12 +47,14 @@ def test_every_spmv_variant_reaches_oracle(variant, precision, bound):
     assert abs(out["rho"][0, 0] - rho) <= 1e-10 * rho
 
 
-@pytest.mark.parametrize("nlam", [1, 3])
-def test_autotuned_solves_reach_oracle_and_keep_their_choice(nlam):
+@pytest.mark.parametrize("nlam,mode", [(1, L.MODE_SEQUENTIAL), (3, L.MODE_SEQUENTIAL), (3, L.MODE_BATCHED)])
+def test_autotuned_solves_reach_oracle_and_keep_their_choice(nlam, mode):
+    """One-column batches (any lambda count in the chain) tune the SpMV
+    configurations; a batch of 3 lambdas keeps the batched SpMM."""
     P = pg.make_problem("ct256", size=64)
     d = np.ones(ops.n_edges(64, 64))
     lams = np.array([0.05, 0.3, 2.0])[:nlam]
-    s = Solver(64, 64, autotune=1, precision=L.PREC_MIXED, tol=1e-12, maxit=20000)
+    s = Solver(64, 64, autotune=1, precision=L.PREC_MIXED, tol=1e-12, maxit=20000, mode=mode)
     s.set_forward_csr(P.A)
     out = s.solve(lams, P.b[:, 0])
     st1 = s.stats()
@@ -60,7 +62,7 @@ def test_autotuned_solves_reach_oracle_and_keep_their_choice(nlam):
     st2 = s.stats()
     levels = L.lcmg_num_levels(s.ctx)
     s.close()
-    if nlam == 1:
+    if mode == L.MODE_SEQUENTIAL:
         assert st1["tuned_spmv_a"] in (1, 2, 3) and st1["tuned_spmv_at"] in (1, 2, 3, 4, 5, 6)
     else:
         assert (st1["tuned_spmv_a"], st1["tuned_spmv_at"]) == (0, 0)

@@ -1,0 +1,250 @@
+"""Parity on the paths the benchmark runs, at the benchmark's sizes.
+
+* The one-column SpMV's multi-row loops (row-pointer prefetch, the 16-bit
+  column base carried from row to row): with the grid capped at one or two
+  blocks every warp walks hundreds of rows, so those loops run in full on a
+  problem the oracle solves in seconds.
+* The full 256 x 256 CT workload (65,340 x 65,536, 15.0M nonzeros) with the
+  library's defaults: one V(1,1) cycle and the solutions at lambda = 1 and
+  0.05, against sampled oracle outputs stored in tests/golden (written by
+  make_golden.py from the oracle alone).
+* Algorithm 2 on the 128 x 128 CT recipe at tol 1e-9: the selected lambda
+  indices equal the oracle's.
+* The 512 x 512 deblurring recipe (19 x 19 PSF, 4 right-hand sides) and the
+  2048 x 2048 one (31 x 31 PSF, 10 levels): solutions, operator and cycle.
+
+Sampled comparisons use the relative 2-norm error over the sample, with the
+tolerances of the element-wise tests (1e-12 cycles and operators in FP64,
+1e-5 cycles in mixed precision, 1e-8 / 1e-6 solutions, 1e-6 rho and eta).
+"""
+import functools
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import problemgen as pg
+from oracle import operators as ops
+from oracle import multigrid as mg
+from oracle import krylov
+from oracle import lcurve
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2306_11067_gb300 import lcmg as L  # noqa: E402
+from paper_2306_11067_gb300 import Solver  # noqa: E402
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+def _load(name):
+    """{'idx': indices, 'blocks': [(header tokens, {tag: (norm, values)} , extras)]}"""
+    idx, blocks, cur = None, [], None
+    for line in open(os.path.join(GOLD, name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        tok = line.split()
+        if tok[0] == "idx":
+            idx = np.array([int(v) for v in tok[1:]])
+        elif tok[0] in ("lam", "case"):
+            cur = {"head": [float(v) for v in tok[1:]], "vec": {}, "extra": {}}
+            blocks.append(cur)
+        elif tok[0] in ("vcycle", "x") and cur is not None:
+            cur["vec"][tok[0]] = (float(tok[1]), np.array([float(v) for v in tok[2:]]))
+        elif tok[0] in ("apply", "vcycle"):
+            blocks.append({"head": [tok[0], float(tok[1])], "vec": {tok[0]: (float(tok[2]),
+                           np.array([float(v) for v in tok[3:]]))}, "extra": {}})
+        else:
+            cur["extra"][tok[0]] = [float(v) for v in tok[1:]]
+    return idx, blocks
+
+
+def _have(name):
+    path = os.path.join(GOLD, name)
+    return os.path.exists(path) and os.path.getsize(path) > 0
+
+
+def _need(name):
+    path = os.path.join(GOLD, name)
+    if not os.path.exists(path) or os.path.getsize(path) == 0:
+        pytest.skip(f"{name} not generated (python tests/golden/make_golden.py full {name})")
+
+
+# --------------------------------------------------------------------------
+@functools.lru_cache(maxsize=None)
+def _ct48():
+    N = 48
+    P = pg.make_problem("ct256", size=N)
+    d = pg.random_weights(ops.n_edges(N, N), 5, d_min=0.05)
+    lams = (0.05, 0.5)
+    F = ops.ForwardCSR(P.A.to_scipy())
+    Lg = ops.gradient(N, N)
+    H = mg.build_hierarchy(mg.weighted_laplacian(Lg, d), sp.diags(F.diag_AtA()), N, N, mg.default_levels(N, N))
+    c = ops.rhs(F, P.b[:, 0])
+    ref = []
+    for lam in lams:
+        x, it, st, _ = krylov.pcg(lambda v: ops.normal_apply(F, Lg, d, lam, v), c, None, mg.VCycle(H, lam, nu=1),
+                                  tol=1e-12, maxit=20000)
+        assert st == 0
+        ref.append((x, lcurve.lcurve_values(F, Lg, d, P.b[:, 0], x)[0]))
+    return P, d, np.array(lams), ref
+
+
+@pytest.mark.parametrize("max_blocks", [1, 2])
+@pytest.mark.parametrize("precision,bound", [(L.PREC_FP64, 1e-8), (L.PREC_MIXED, 1e-6)])
+@pytest.mark.parametrize("compact", [1, 0])
+def test_spmv_multirow_loops_match_oracle(max_blocks, precision, bound, compact):
+    P, d, lams, ref = _ct48()
+    N = P.n_v
+    s = Solver(N, N, tol=1e-12, maxit=20000, precision=precision, max_blocks=max_blocks, compact_cols=compact)
+    s.set_forward_csr(P.A)
+    s.set_weights(d)
+    out = s.solve(lams, P.b[:, 0])
+    s.close()
+    for j, (x, rho) in enumerate(ref):
+        assert out["status"][0, j] == 0
+        assert _rel(out["x"][0, j], x) <= bound, (lams[j], _rel(out["x"][0, j], x))
+        assert abs(out["rho"][0, j] - rho) <= 1e-6 * rho
+
+
+# --------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def ct256():
+    return pg.make_problem("ct256")
+
+
+@pytest.mark.parametrize("precision", [L.PREC_FP64, L.PREC_MIXED])
+def test_ct256_full_vcycle_and_solve(ct256, precision):
+    _need("ct256_full.txt")
+    idx, blocks = _load("ct256_full.txt")
+    P = ct256
+    d = pg.random_weights(ops.n_edges(P.n_v, P.n_h), 41, d_min=0.05)
+    s = Solver(P.n_v, P.n_h, precision=precision, tol=1e-12, maxit=60000)
+    s.set_forward_csr(P.A)
+    s.set_weights(d)
+    r = pg.rng(42).standard_normal(P.n)
+    lams = np.array([b["head"][0] for b in blocks])
+    rd = torch.tensor(r, device="cuda", dtype=torch.float64).reshape(1, -1)
+
+    def cycles():
+        out = []
+        for lam in lams:  # one column per call: the benchmark's one-column cycle
+            zd = torch.empty_like(rd)
+            L.lcmg_apply_vcycle_dev(s.ctx, np.array([lam]), rd, zd)
+            out.append(zd[0].cpu().numpy())
+        return out
+    if precision == L.PREC_MIXED:
+        # the default FP16 smoother data against the oracle's model of it
+        _, b16 = _load("ct256_vcycle16.txt") if _have("ct256_vcycle16.txt") else (None, [])
+        for j, zz in enumerate(cycles() if b16 else []):
+            nz, vz = b16[j]["vec"]["vcycle"]
+            assert _rel(zz[idx], vz) <= 1e-5, (lams[j], _rel(zz[idx], vz))
+        s.set_params(smoother_fp16=0)  # FP32 smoother data against the exact cycle
+    Z = cycles()
+    order = np.argsort(lams)
+    out = s.solve(lams[order], P.b[:, 0])
+    s.close()
+    vb = 1e-12 if precision == L.PREC_FP64 else 1e-5
+    xb = 1e-8 if precision == L.PREC_FP64 else 1e-6
+    for j, b in enumerate(blocks):
+        nz, vz = b["vec"]["vcycle"]
+        assert _rel(Z[j][idx], vz) <= vb, (b["head"], _rel(Z[j][idx], vz))
+        assert abs(np.linalg.norm(Z[j]) - nz) <= vb * nz
+        k = int(np.where(order == j)[0][0])
+        nx, vx = b["vec"]["x"]
+        x = out["x"][0, k]
+        assert out["status"][0, k] == 0
+        assert _rel(x[idx], vx) <= xb, (b["head"], _rel(x[idx], vx))
+        assert abs(np.linalg.norm(x) - nx) <= xb * nx
+        rho, eta, _ = b["extra"]["rho_eta_its"]
+        assert abs(out["rho"][0, k] - rho) <= 1e-6 * rho
+        assert abs(out["eta"][0, k] - eta) <= 1e-6 * eta
+
+
+@pytest.mark.parametrize("precision", [L.PREC_FP64, L.PREC_MIXED])
+def test_ct128_algorithm2_history(precision):
+    _need("ct128_alg2.txt")
+    hist = None
+    for line in open(os.path.join(GOLD, "ct128_alg2.txt")):
+        if line.startswith("history"):
+            hist = [int(v) for v in line.split()[1:]]
+    P = pg.make_problem("ct256", size=128)
+    s = Solver(128, 128, precision=precision, tol=1e-9, maxit=50000)
+    s.set_forward_csr(P.A)
+    r = s.lcurve_run(P.lambdas, P.b[:, 0], max_outer=15)
+    s.close()
+    assert [int(h) for h in r["history"]] == hist
+
+
+@pytest.mark.parametrize("precision,bound", [(L.PREC_FP64, 1e-8), (L.PREC_MIXED, 1e-6)])
+@pytest.mark.parametrize("mode", [L.MODE_SEQUENTIAL, L.MODE_BATCHED])
+def test_deblur512_solve(precision, bound, mode):
+    _need("deblur512_solve.txt")
+    idx, blocks = _load("deblur512_solve.txt")
+    P = pg.make_problem("deblur512")
+    d = pg.random_weights(ops.n_edges(P.n_v, P.n_h), 51, d_min=0.05)
+    s = Solver(P.n_v, P.n_h, levels=P.levels, precision=precision, mode=mode, tol=1e-12, maxit=20000)
+    s.set_forward_stencil(P.psf)
+    assert s.forward_form() == L.FORM_SEPARABLE
+    s.set_weights(d)
+    lams = np.array([0.05, 0.5])
+    out = s.solve(lams, P.b.T)
+    s.close()
+    for b in blocks:
+        r, lam = int(b["head"][0]), b["head"][1]
+        k = int(np.argmin(np.abs(lams - lam)))
+        nx, vx = b["vec"]["x"]
+        x = out["x"][r, k]
+        assert out["status"][r, k] == 0
+        assert _rel(x[idx], vx) <= bound, (r, lam, _rel(x[idx], vx))
+        rho, eta, _ = b["extra"]["rho_eta_its"]
+        assert abs(out["rho"][r, k] - rho) <= 1e-6 * rho
+        assert abs(out["eta"][r, k] - eta) <= 1e-6 * eta
+
+
+@pytest.mark.parametrize("precision", [L.PREC_FP64, L.PREC_MIXED])
+def test_deblur2048_operator_and_vcycle(precision):
+    _need("deblur2048_ops.txt")
+    idx, blocks = _load("deblur2048_ops.txt")
+    N = 2048
+    psf = pg.gaussian_psf(15, 5.0)
+    d = pg.random_weights(ops.n_edges(N, N), 61, d_min=0.05)
+    p = pg.rng(62).standard_normal(N * N)
+    s = Solver(N, N, levels=10, precision=precision, smoother_fp16=0)
+    s.set_forward_stencil(psf)
+    assert s.forward_form() == L.FORM_SEPARABLE
+    s.set_weights(d)
+    pd = torch.tensor(p, device="cuda", dtype=torch.float64).reshape(1, -1)
+    if precision == L.PREC_MIXED and _have("deblur2048_vcycle16.txt"):
+        # the default FP16 smoother data against the oracle's model of it
+        s.set_params(smoother_fp16=1)
+        for b in _load("deblur2048_vcycle16.txt")[1]:
+            lam = b["head"][1]
+            nrm, vals = b["vec"]["vcycle"]
+            yd = torch.empty_like(pd)
+            L.lcmg_apply_vcycle_dev(s.ctx, np.array([lam]), pd, yd)
+            y = yd[0].cpu().numpy()
+            assert _rel(y[idx], vals) <= 1e-5, (lam, _rel(y[idx], vals))
+        s.set_params(smoother_fp16=0)
+    for b in blocks:
+        kind, lam = b["head"]
+        nrm, vals = b["vec"][kind]
+        yd = torch.empty_like(pd)
+        if kind == "apply":
+            if precision != L.PREC_FP64:
+                continue  # the operator entry point computes in FP64
+            L.lcmg_apply_normal_dev(s.ctx, np.array([lam]), pd, yd)
+            bound = 1e-12
+        else:
+            L.lcmg_apply_vcycle_dev(s.ctx, np.array([lam]), pd, yd)
+            bound = 1e-12 if precision == L.PREC_FP64 else 1e-5
+        y = yd[0].cpu().numpy()
+        assert _rel(y[idx], vals) <= bound, (kind, lam, _rel(y[idx], vals))
+        assert abs(np.linalg.norm(y) - nrm) <= bound * nrm
+    s.close()

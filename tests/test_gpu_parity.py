@@ -197,7 +197,7 @@ def test_solve_ct_batched_parity(precision, bound, N):
     P = _ct(N)
     lams = np.array([0.03, 0.3, 3.0, 30.0])
     d = pg.random_weights(ops.n_edges(N, N), 5, d_min=0.05)
-    s = _solver(P, tol=1e-13, precision=precision, maxit=20000)
+    s = _solver(P, tol=1e-13, precision=precision, maxit=20000, mode=L.MODE_BATCHED)
     s.set_weights(d)
     levels = mg.default_levels(N, N)
     out = s.solve(lams, P.b[:, 0])

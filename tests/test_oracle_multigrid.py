@@ -154,3 +154,84 @@ def test_default_levels_rule():
     assert mg.default_levels(33, 32) == 1        # odd side: no coarsening
     with pytest.raises(ValueError):
         mg.level_shapes(12, 12, 4)               # 12 -> 6 -> 3 -> (odd)
+
+
+# --------------------------------------------------------------------------
+# FP16 storage of the smoother data (the mixed path's rounded cycle)
+# --------------------------------------------------------------------------
+def test_fp16_round_is_round_to_nearest():
+    """Against brute force: the stored value is the FP16 number closest to
+    v * scale (ties to even), so no neighbouring FP16 number is closer."""
+    g = pg.rng(5)
+    v = 10.0 ** g.uniform(-9, 1, 4000) * g.choice([-1.0, 1.0], 4000)
+    scale = mg.half_scale(np.abs(v).max())
+    h = (mg.fp16_round(v, scale) * scale).astype(np.float16)
+    x = v * scale
+    up = np.nextafter(h, np.float16(np.inf)).astype(np.float64)
+    dn = np.nextafter(h, np.float16(-np.inf)).astype(np.float64)
+    err = np.abs(h.astype(np.float64) - x)
+    assert np.all(err <= np.abs(up - x)) and np.all(err <= np.abs(dn - x))
+    # normal range: 11 significant bits
+    big = np.abs(x) >= 2.0 ** -14
+    assert np.all(err[big] <= 2.0 ** -11 * np.abs(x[big]))
+
+
+@pytest.mark.parametrize("mx", [1e-12, 3.1e-3, 1.0, 8192.0, 7.7e5])
+def test_half_scale_range(mx):
+    s = mg.half_scale(mx)
+    assert 4096.0 < mx * s <= 8192.0
+    assert np.log2(s) == np.round(np.log2(s))  # a power of two: exact scaling
+
+
+def _hier16(n_v, n_h, levels, seed):
+    L = ops.gradient(n_v, n_h)
+    d = pg.random_weights(ops.n_edges(n_v, n_h), seed, d_min=0.02)
+    ga = pg.rng(seed + 1).uniform(1e-3, 4e-3, n_v * n_h)
+    return mg.build_hierarchy(mg.weighted_laplacian(L, d), sp.diags(ga), n_v, n_h, levels)
+
+
+@pytest.mark.parametrize("lam", [1e-4, 0.05, 2.0])
+def test_fp16_coarse_operator_keeps_row_sums_and_is_close(lam):
+    H = _hier16(24, 16, 3, 7)
+    for k in (1, 2):
+        K = (lam ** 2 * H.G_L[k] + H.G_A[k]).toarray()
+        Kh = mg.fp16_coarse_operator(H.G_L[k], H.G_A[k], lam ** 2).toarray()
+        s32 = np.asarray(H.G_A[k].sum(axis=1)).ravel().astype(np.float32).astype(np.float64)
+        # K^ 1 = fl32(G_A 1): the rounding adds a zero-row-sum term
+        assert np.abs(Kh.sum(axis=1) - s32).max() <= 1e-14 * np.abs(s32).max()
+        off = ~np.eye(K.shape[0], dtype=bool)
+        scale = np.abs(K[off]).max()
+        assert np.abs(Kh[off] - K[off]).max() <= 2.0 ** -11 * scale + 1e-300
+        # K is symmetric to FP64 rounding: a mirrored pair rounds alike, or
+        # (a value at a rounding boundary) one FP16 step apart
+        assert np.abs(Kh - Kh.T).max() <= 2.0 ** -10 * scale
+        assert np.linalg.eigvalsh(0.5 * (Kh + Kh.T)).min() > 0.0
+
+
+def test_fp16_fine_operator_structure():
+    H = _hier16(20, 12, 2, 3)
+    lam2 = 0.3
+    K = (lam2 * H.G_L[0] + H.G_A[0]).toarray()
+    Kh = mg.fp16_fine_operator(H.G_L[0], H.G_A[0], lam2).toarray()
+    ga = H.G_A[0].diagonal()
+    gah = mg.fp16_round(ga, mg.half_scale(ga.max()))
+    # rows sum to the rounded diag(A^T A); symmetric; off-diagonals within 2^-11
+    assert np.abs(Kh.sum(axis=1) - gah).max() <= 1e-15 * np.abs(K).max()
+    assert np.array_equal(Kh, Kh.T)
+    off = ~np.eye(K.shape[0], dtype=bool)
+    assert np.all(np.abs(Kh[off] - K[off]) <= 2.0 ** -11 * np.abs(K[off]) + 1e-300)
+
+
+@pytest.mark.parametrize("lam", [1e-3, 0.3])
+def test_fp16_vcycle_symmetric_positive_and_close(lam):
+    H = _hier16(16, 16, 3, 11)
+    V = mg.VCycle(H, lam, nu=1, storage="fp16")
+    g = pg.rng(13)
+    u, v = g.standard_normal(256), g.standard_normal(256)
+    Bu, Bv = V(u), V(v)
+    assert abs(Bu @ v - u @ Bv) <= 1e-12 * abs(Bu @ v)
+    assert Bu @ u > 0
+    ref = mg.VCycle(H, lam, nu=1)(u)
+    assert np.linalg.norm(Bu - ref) <= 1e-2 * np.linalg.norm(ref)
+    with pytest.raises(ValueError):
+        mg.VCycle(H, lam, storage="fp8")
