@@ -471,13 +471,20 @@ int lcmg_fma_peak(int device, int32_t precision, double* tflops);
  *   n_cols           columns, 1..64, with n_cols * m <= 2^19
  *   lambda[n_cols]   host array
  *   p, q             [n_cols][n] device arrays (each column contiguous)
- * Arithmetic is FP64.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress, once per device, with that device
- * current); make that first call before any stream capture.  Every call
+ * Preconditions the library cannot check on the device: 0 <= col < n and
+ * 0 <= col_t < m; (row_ptr_t, col_t, val_t) is the transpose of the m-row A
+ * given by (row_ptr, col, val), with m its true row count; every pointer is
+ * valid for the sizes above.  p and q must not overlap (q is written while
+ * neighbouring entries of p are read; checked on the host).
+ * Arithmetic is FP64.  Every call looks up the array's device address in
+ * the current context (cudaGetSymbolAddress, with `device` current; no
+ * allocation).  The first call on a device loads the library's device image
+ * there if it is not loaded yet, which commits the 4 MiB array on that
+ * device: make that first call before any stream capture.  Every call
  * shares the one array and overwrites what it reads, so calls whose kernels
  * overlap on the GPU (other streams, other threads) race: order them.
- * Errors: INVALID_ARG (sizes, null pointers, n_cols * m above the limit),
- * CUDA. */
+ * Errors: INVALID_ARG (sizes, null pointers, p and q overlapping, n_cols * m
+ * above the limit), CUDA. */
 int lcmg_apply_normal_noalloc(int device, void* stream, int32_t n_v, int32_t n_h, int64_t m,
                               const int64_t* row_ptr, const int32_t* col, const void* val,
                               const int64_t* row_ptr_t, const int32_t* col_t, const void* val_t,

@@ -18,13 +18,46 @@ namespace lcmg {
 // (of nc) to fine cell a (of 2 nc): 3/4 from the parent, 1/4 from the
 // nearest other coarse cell; a missing neighbour's weight goes to the parent.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double pw1(int a, int I, int nc) {
+// (In the precision of the kernel that uses it: the weights 1, 3/4, 1/4
+// are exact in any format, and an FP32 kernel then needs no FP64 work.)
+template <class T = double>
+__device__ __forceinline__ T pw1(int a, int I, int nc) {
   const int d = a - 2 * I;
-  if (d == 0) return I == 0 ? 1.0 : 0.75;
-  if (d == 1) return I == nc - 1 ? 1.0 : 0.75;
-  if (d == -1 || d == 2) return 0.25;
-  return 0.0;
+  if (d == 0) return I == 0 ? T(1) : T(0.75);
+  if (d == 1) return I == nc - 1 ? T(1) : T(0.75);
+  if (d == -1 || d == 2) return T(0.25);
+  return T(0);
 }
+
+// Compensated dot product in the working precision (Ogita, Rump and Oishi,
+// "Accurate sum and dot product", 2005, Algorithm Dot2): each product is
+// split exactly into p + e with one FMA, the running sum is kept exact to
+// rounding as s + c with TwoSum, so the result is as accurate as a dot
+// product in twice the working precision.  The mixed path's FP32 kernels
+// accumulate their dot products this way and convert s + c to FP64 once per
+// thread: on this GPU the FP64 pipe runs at a small fraction of the FP32 one.
+struct Dot2 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);  // a b = p + e exactly
+    const float t = s + p;
+    const float z = t - s;
+    c += (s - (t - z)) + (p - z) + e;  // TwoSum error of s + p, plus e
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// A thread's dot-product accumulator: FP64 for FP64 vectors, Dot2 for FP32
+template <class T>
+struct DotAcc {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { s += a * b; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> : Dot2 {};
 
 // ---------------------------------------------------------------------------
 // Level operators
@@ -635,11 +668,11 @@ __global__ void __launch_bounds__(kBlock)
 #pragma unroll
     for (int b = 2 * J - 1; b <= 2 * J + 2; ++b) {
       if (b < 0 || b >= nhf) continue;
-      const T wb = (T)pw1(b, J, nhc);
+      const T wb = pw1<T>(b, J, nhc);
 #pragma unroll
       for (int a2 = 2 * I - 1; a2 <= 2 * I + 2; ++a2) {
         if (a2 < 0 || a2 >= nvf) continue;
-        acc += wb * (T)pw1(a2, I, nvc) * rf[((int64_t)a2 + (int64_t)b * nvf) * B + col];
+        acc += wb * pw1<T>(a2, I, nvc) * rf[((int64_t)a2 + (int64_t)b * nvf) * B + col];
       }
     }
     rc[p * B + col] = acc;
@@ -666,12 +699,12 @@ __global__ void __launch_bounds__(kBlock)
     for (int u = 0; u < 2; ++u) {
       const int J = Js[u];
       if (J < 0 || J >= nhc) continue;
-      const T wb = (T)pw1(b, J, nhc);
+      const T wb = pw1<T>(b, J, nhc);
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const int I = Is[t];
         if (I < 0 || I >= nvc) continue;
-        acc += wb * (T)pw1(a2, I, nvc) * ec[((int64_t)I + (int64_t)J * nvc) * B + col];
+        acc += wb * pw1<T>(a2, I, nvc) * ec[((int64_t)I + (int64_t)J * nvc) * B + col];
       }
     }
     zf[p * B + col] += acc;
@@ -918,16 +951,18 @@ __global__ void __launch_bounds__(kBlock)
       }
     }
   }
-  double acc = 0.0;
+  DotAcc<T> dacc;
   if (ok) {
     const T alT = (T)al;
+    const TX alX = (TX)al;
     for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kBlock) {
-      x[i] = (TX)(x[i] + (TX)al * (TX)p[i]);
+      x[i] = (TX)(x[i] + alX * (TX)p[i]);
       const T rn = r[i] - alT * q[i];
       r[i] = rn;
-      acc += to_d(rn) * to_d(rn);
+      dacc.add(rn, rn);
     }
   }
+  double acc = dacc.value();
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;

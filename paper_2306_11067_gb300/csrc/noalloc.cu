@@ -12,7 +12,6 @@
 // keeps its only intermediate, the vector A p, in a fixed array that is
 // part of the library's device image.
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -30,8 +29,6 @@ constexpr int kMaxCols = 64;
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
-static std::mutex g_mu;
-static double* g_ptr[kMaxDevices] = {};
 
 struct Lam2 {  // lambda^2 per column, passed by value (kernel parameter space)
   double v[kMaxCols];
@@ -106,17 +103,19 @@ __global__ void __launch_bounds__(kBlock)
   }
 }
 
-// Set-up, once per device and with that device current: the device address
-// of g_scratch.  In host code the name g_scratch denotes a host-side
-// stand-in, never the device array, so only this address reaches kernels.
-static double* scratch_for(int device) {
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (g_ptr[device]) return g_ptr[device];
+// The device address of g_scratch in the current context, looked up with
+// the device current on every call (a cheap query of the loaded module, no
+// allocation): a cached address would go stale after cudaDeviceReset or
+// under another context of the same device.  In host code the name
+// g_scratch denotes a host-side stand-in, never the device array, so only
+// this address reaches the kernels.  The first call on a device loads the
+// library's device image there if it is not loaded yet, which commits the
+// 4 MiB array on that device.
+static double* scratch_address() {
   void* ptr = nullptr;
   const cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
   if (e != cudaSuccess) throw CudaError(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-  g_ptr[device] = static_cast<double*>(ptr);
-  return g_ptr[device];
+  return static_cast<double*>(ptr);
 }
 
 }  // namespace noalloc
@@ -137,6 +136,12 @@ extern "C" int lcmg_apply_normal_noalloc(int device, void* stream, int32_t n_v, 
       throw ArgError("null device pointer");
     if (val_dtype != 0 && val_dtype != 1) throw ArgError("val_dtype must be 0 (FP32) or 1 (FP64)");
     if (device < 0 || device >= noalloc::kMaxDevices) throw ArgError("invalid device");
+    {  // p is read at neighbouring pixels while q is written: they must not overlap
+      const int64_t bytes = (int64_t)n_cols * n_v * n_h * (int64_t)sizeof(double);
+      const char* pb = reinterpret_cast<const char*>(p);
+      const char* qb = reinterpret_cast<const char*>(q);
+      if (pb < qb + bytes && qb < pb + bytes) throw ArgError("p and q overlap");
+    }
     if ((int64_t)n_cols * m > noalloc::kScratchDoubles)
       throw ArgError("n_cols * m = " + std::to_string((long long)n_cols * m) +
                      " exceeds the fixed scratch of " + std::to_string((long long)noalloc::kScratchDoubles) +
@@ -148,7 +153,7 @@ extern "C" int lcmg_apply_normal_noalloc(int device, void* stream, int32_t n_v, 
     }
     LCMG_CUDA(cudaGetDevice(&prev));
     if (prev != device) LCMG_CUDA(cudaSetDevice(device));
-    double* scratch = noalloc::scratch_for(device);
+    double* scratch = noalloc::scratch_address();
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t n = (int64_t)n_v * n_h;
     const int bf = (int)std::min<int64_t>((m * n_cols * 32 + kBlock - 1) / kBlock, 4096);

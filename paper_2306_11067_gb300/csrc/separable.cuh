@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kBandThreads)
   auto gpt = [&](int along, int line) -> int64_t {
     return DIR == 0 ? (int64_t)along + (int64_t)line * nv : (int64_t)line + (int64_t)along * nv;
   };
-  double dacc = 0.0;
+  DotAcc<T> dot;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int seg0 = (tile % nseg) * kBandSeg;
     const int line0 = (tile / nseg) * kBandLines;
@@ -192,17 +192,17 @@ __global__ void __launch_bounds__(kBandThreads)
             out[p * B + col] = (TO)acc[t];
           } else if (EPI == BAND_RESID2) {
             const double e = to_d(acc[t]) - bvec[p * B + col];
-            dacc += e * e;
+            dot.add(e, e);
           } else {
             auto pv = [&](int64_t qq) { return P[qq * B + col]; };
             const T kv = acc[t] + l2 * fop.lap(p, i, j, pv);
             if (EPI == BAND_NORMAL) {
               out[p * B + col] = (TO)kv;
-              dacc += to_d(P[p * B + col]) * to_d(kv);
+              dot.add(P[p * B + col], kv);
             } else {
               const T rv = C[p * B + col] - kv;
               out[p * B + col] = (TO)rv;
-              dacc += to_d(rv) * to_d(rv);
+              dot.add(rv, rv);
             }
           }
         }
@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(kBandThreads)
     __syncthreads();  // the tile buffer is reloaded by the next tile
   }
   if (EPI != BAND_STORE) {
+    double dacc = dot.value();
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, off);
     if (lane == 0) sred[w] = dacc;

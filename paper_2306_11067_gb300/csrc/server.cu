@@ -143,8 +143,12 @@ void destroy_ctx(Ctx& c) {
 
 // Pick the next request to admit and the context it runs on (server lock
 // held).  Returns false when nothing can start now.  `create_bytes` > 0
-// means a new context of that many bytes must be created for it.
-bool admit_one(lcmg_server& S, std::shared_ptr<Request>& out, Ctx*& ctx_out, size_t& create_bytes) {
+// means a new context of that many bytes must be created for it.  Idle
+// contexts evicted to make room are moved to `evicted` (their bytes already
+// released from the account): the caller destroys them after unlocking, so
+// submit and wait never stall on a context's teardown.
+bool admit_one(lcmg_server& S, std::shared_ptr<Request>& out, Ctx*& ctx_out, size_t& create_bytes,
+               std::vector<std::unique_ptr<Ctx>>& evicted) {
   for (auto it = S.pending.begin(); it != S.pending.end(); ++it) {
     Request& r = **it;
     const Problem& P = *S.problems.at(r.problem);
@@ -177,18 +181,26 @@ bool admit_one(lcmg_server& S, std::shared_ptr<Request>& out, Ctx*& ctx_out, siz
       r.t_done = now_s();
       S.pending.erase(it);
       S.cv_done.notify_all();
-      return admit_one(S, out, ctx_out, create_bytes);
+      return admit_one(S, out, ctx_out, create_bytes, evicted);
     }
-    // evict idle contexts, least recently used first, until it fits
-    while (S.resident + need > S.budget) {
+    // evict idle contexts, least recently used first, until it fits; only
+    // when evicting every idle one would make it fit (busy contexts keep
+    // their bytes), so hierarchies and warm starts are not thrown away for
+    // a request that must wait anyway
+    size_t idle = 0;
+    for (auto& c : S.ctxs)
+      if (!c->busy) idle += c->bytes;
+    while (S.resident + need > S.budget && S.resident - idle + need <= S.budget) {
       Ctx* lru = nullptr;
       for (auto& c : S.ctxs)
         if (!c->busy && (!lru || c->last_used < lru->last_used)) lru = c.get();
       if (!lru) break;
-      destroy_ctx(*lru);
       S.resident -= lru->bytes;
+      idle -= lru->bytes;
       ++S.evictions;
-      S.ctxs.erase(std::find_if(S.ctxs.begin(), S.ctxs.end(), [&](const std::unique_ptr<Ctx>& c) { return c.get() == lru; }));
+      auto pos = std::find_if(S.ctxs.begin(), S.ctxs.end(), [&](const std::unique_ptr<Ctx>& c) { return c.get() == lru; });
+      evicted.push_back(std::move(*pos));
+      S.ctxs.erase(pos);
     }
     if (S.resident + need <= S.budget) {
       auto c = std::make_unique<Ctx>();
@@ -247,8 +259,17 @@ void execute(lcmg_server& S, Request& r, Ctx& C, const Problem& P) {
     r.iters.assign(nl, 0);
     r.status.assign(nl, 0);
     const bool warm = r.warm && C.last_lam == r.lam && C.last_x.size() == r.x.size();
+    // a warm request starts every lambda from its own resident solution (the
+    // chain would start only the largest one there)
+    const bool rebatch = warm && S.prm.mode == LCMG_MODE_SEQUENTIAL;
+    if (rebatch) {
+      lcmg_params p = S.prm;
+      p.mode = LCMG_MODE_BATCHED;
+      lcmg_set_params(C.ctx, &p);
+    }
     st = lcmg_solve(C.ctx, nl, r.lam.data(), 1, r.b.data(), warm ? C.last_x.data() : nullptr, r.x.data(),
                     r.rho.data(), r.eta.data(), r.iters.data(), r.status.data());
+    if (rebatch) lcmg_set_params(C.ctx, &S.prm);
     if (st == LCMG_OK) {
       C.last_lam = r.lam;
       C.last_x = r.x;
@@ -275,8 +296,12 @@ void worker(lcmg_server* Sp) {
     std::shared_ptr<Request> r;
     Ctx* C = nullptr;
     size_t create = 0;
-    S.cv_work.wait(lk, [&] { return S.stop || admit_one(S, r, C, create); });
+    std::vector<std::unique_ptr<Ctx>> evicted;
+    S.cv_work.wait(lk, [&] { return S.stop || admit_one(S, r, C, create, evicted); });
     if (!r) {
+      lk.unlock();
+      for (auto& e : evicted) destroy_ctx(*e);
+      lk.lock();
       if (S.stop) return;
       continue;
     }
@@ -288,6 +313,8 @@ void worker(lcmg_server* Sp) {
     S.peak_running = std::max(S.peak_running, S.running);
     std::shared_ptr<Problem> P = S.problems.at(r->problem);
     lk.unlock();
+    for (auto& e : evicted) destroy_ctx(*e);  // outside the lock
+    evicted.clear();
     bool ok = true;
     if (create) {
       const int st = make_ctx(S, *P, &C->ctx);

@@ -113,11 +113,11 @@ __global__ void __launch_bounds__(kFineThreads)
 #pragma unroll
       for (int b = 2 * J - 1; b <= 2 * J + 2; ++b) {
         if (b < 0 || b >= nh) continue;
-        const float wb = (float)pw1(b, J, nhc);
+        const float wb = pw1<float>(b, J, nhc);
 #pragma unroll
         for (int a2 = 2 * I - 1; a2 <= 2 * I + 2; ++a2) {
           if (a2 < 0 || a2 >= nv) continue;
-          acc += wb * (float)pw1(a2, I, nvc) * sres[(a2 - (i0 - 1)) + (b - (j0 - 1)) * RI];
+          acc += wb * pw1<float>(a2, I, nvc) * sres[(a2 - (i0 - 1)) + (b - (j0 - 1)) * RI];
         }
       }
       rc[((int64_t)I + (int64_t)J * nvc) * B + col] = acc;
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kFineThreads)
   const int nv = op.nv, nh = op.nh, nvc = nv / 2, nhc = nh / 2;
   const int nti = (nv + kFineTI - 1) / kFineTI;
   const float l2 = lam2[col];
-  double dacc = 0.0;
+  Dot2 dot;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int i0 = (tile % nti) * kFineTI, j0 = (tile / nti) * kFineTJ;
     const int I0 = i0 / 2 - 1, J0 = j0 / 2 - 1;
@@ -165,12 +165,12 @@ __global__ void __launch_bounds__(kFineThreads)
         for (int u = 0; u < 2; ++u) {
           const int J = Js[u];
           if (J < 0 || J >= nhc) continue;
-          const float wb = (float)pw1(b, J, nhc);
+          const float wb = pw1<float>(b, J, nhc);
 #pragma unroll
           for (int w = 0; w < 2; ++w) {
             const int I = Is[w];
             if (I < 0 || I >= nvc) continue;
-            acc += wb * (float)pw1(a2, I, nvc) * sc[(I - I0) + (J - J0) * CI];
+            acc += wb * pw1<float>(a2, I, nvc) * sc[(I - I0) + (J - J0) * CI];
           }
         }
         v = z1 + acc;
@@ -189,11 +189,12 @@ __global__ void __launch_bounds__(kFineThreads)
       const float rv = r[p * B + col];
       const float zn = s0[q] + fine_dinv(f, l2, smoother, omega) * (rv - fine_kz(f, l2, s0, q, WI));
       zout[p * B + col] = zn;
-      dacc += (double)rv * (double)zn;
+      dot.add(rv, zn);
     }
     __syncthreads();
   }
   if (part) {
+    double dacc = dot.value();
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, off);
     if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = dacc;

@@ -157,11 +157,11 @@ __device__ __forceinline__ void vdown_tile(const Op& op, int B, const T* __restr
 #pragma unroll
     for (int b = 2 * J - 1; b <= 2 * J + 2; ++b) {
       if (b < 0 || b >= nh) continue;
-      const T wb = (T)pw1(b, J, nhc);
+      const T wb = pw1<T>(b, J, nhc);
 #pragma unroll
       for (int a2 = 2 * I - 1; a2 <= 2 * I + 2; ++a2) {
         if (a2 < 0 || a2 >= nv) continue;
-        acc += wb * (T)pw1(a2, I, nvc) * sres[(a2 - ri) + (b - rj) * WR];
+        acc += wb * pw1<T>(a2, I, nvc) * sres[(a2 - ri) + (b - rj) * WR];
       }
     }
     rc[((int64_t)I + (int64_t)J * nvc) * B + col] = acc;
@@ -225,12 +225,12 @@ __device__ __forceinline__ double vup_tile(const Op& op, int B, const T* __restr
       for (int u = 0; u < 2; ++u) {
         const int J = Js[u];
         if (J < 0 || J >= nhc) continue;
-        const T wb = (T)pw1(b, J, nhc);
+        const T wb = pw1<T>(b, J, nhc);
 #pragma unroll
         for (int w = 0; w < 2; ++w) {
           const int I = Is[w];
           if (I < 0 || I >= nvc) continue;
-          acc += wb * (T)pw1(a2, I, nvc) * ec[((int64_t)I + (int64_t)J * nvc) * B + col];
+          acc += wb * pw1<T>(a2, I, nvc) * ec[((int64_t)I + (int64_t)J * nvc) * B + col];
         }
       }
       v = zpre[((int64_t)a2 + (int64_t)b * nv) * B + col] + acc;
@@ -258,7 +258,7 @@ __device__ __forceinline__ double vup_tile(const Op& op, int B, const T* __restr
   constexpr int WS = (NU == 2) ? W1 : W0;
   const int si = (NU == 2) ? ai : oi, sj = (NU == 2) ? aj : oj;
   // last sweep on the tile's fine points
-  double dacc = 0.0;
+  DotAcc<T> dacc;
   if constexpr (kPre) {
     if (phave) {
       const int64_t p = (int64_t)pi + (int64_t)pj * nv;
@@ -267,7 +267,7 @@ __device__ __forceinline__ double vup_tile(const Op& op, int B, const T* __restr
       const T kz = op.apply_k(kpre, pi, pj, vz);
       const T zn = zs[q] + dpre * (rpre - kz);
       zout[p * B + col] = zn;
-      dacc += to_d(rpre) * to_d(zn);
+      dacc.add(rpre, zn);
     }
   }
   for (int t = kPre ? WF * WF : (int)threadIdx.x; t < WF * WF; t += NTD) {
@@ -280,9 +280,9 @@ __device__ __forceinline__ double vup_tile(const Op& op, int B, const T* __restr
     const T rv = r[p * B + col];
     const T zn = zs[q] + dinv[p * B + col] * (rv - kz);
     zout[p * B + col] = zn;
-    dacc += to_d(rv) * to_d(zn);
+    dacc.add(rv, zn);
   }
-  return dacc;
+  return dacc.value();
 }
 
 // Grid-stride over the tiles (any number of them: the grid is capped at

@@ -65,7 +65,9 @@ def test_paper_fgmres_solve_matches_oracle(kind, levels, restart):
     n_v, n_h = P.n_v, P.n_h
     d = pg.random_weights(ops.n_edges(n_v, n_h), 7, d_min=0.05)
     lams = np.array([0.2, 0.5, 2.0])
-    s = Solver(n_v, n_h, levels=levels, precond=1, tol=1e-12, maxit=2000, gmres_restart=restart)
+    # every lambda from zero, as the oracle solves it
+    s = Solver(n_v, n_h, levels=levels, precond=1, tol=1e-12, maxit=2000, gmres_restart=restart,
+               mode=L.MODE_BATCHED)
     s.set_forward_csr(A)
     s.set_weights(d)
     out = s.solve(lams, P.b[:, 0])

@@ -236,11 +236,13 @@ def test_solve_psf_parity(precision):
     P = pg.make_problem("deblur512", size=32, n_rhs=1)
     d = pg.random_weights(ops.n_edges(32, 32), 8, d_min=0.05)
     lams = np.array([1e-2, 0.2])
-    s = _solver(P, levels=2, tol=1e-12, precision=precision)
+    # FP64: both sides to 1e-13 (forward errors up to cond(K) x tol each)
+    tol = 1e-13 if precision == L.PREC_FP64 else 1e-12
+    s = _solver(P, levels=2, tol=tol, precision=precision)
     s.set_weights(d)
     out = s.solve(lams, P.b[:, 0])
     for j, lam in enumerate(lams):
-        x, it, st, rho, eta = _oracle(P, d, 2, lam, tol=1e-12)
+        x, it, st, rho, eta = _oracle(P, d, 2, lam, tol=tol)
         assert _rel(out["x"][0, j], x) <= (1e-8 if precision == L.PREC_FP64 else 1e-6)
         assert abs(out["rho"][0, j] - rho) <= 1e-6 * rho
     s.close()
@@ -336,7 +338,10 @@ def test_iteration_reaches_oracle(nu, levels, nrhs, precision, mode):
     P = pg.make_problem("deblur512", size=n, n_rhs=nrhs)
     lams = np.array([0.01, 0.2, 3.0])
     d = pg.random_weights(ops.n_edges(n, n), 21, d_min=0.05)
-    s = _solver(P, levels=levels, nu=nu, tol=1e-12, precision=precision, mode=mode, maxit=20000)
+    # FP64: both sides to 1e-13 (forward errors up to cond(K) x tol each; the
+    # chain's warm starts and the oracle's zero starts reach different points)
+    tol = 1e-13 if precision == L.PREC_FP64 else 1e-12
+    s = _solver(P, levels=levels, nu=nu, tol=tol, precision=precision, mode=mode, maxit=20000)
     s.set_weights(d)
     out = s.solve(lams, P.b.T)
     s.close()
@@ -348,7 +353,7 @@ def test_iteration_reaches_oracle(nu, levels, nrhs, precision, mode):
         c = ops.rhs(F, P.b[:, r])
         for j, lam in enumerate(lams):
             x, it, st, _ = krylov.pcg(lambda v: ops.normal_apply(F, Lg, d, lam, v), c, None,
-                                      mg.VCycle(H, lam, nu=nu), tol=1e-12, maxit=20000)
+                                      mg.VCycle(H, lam, nu=nu), tol=tol, maxit=20000)
             assert out["status"][r, j] == 0
             assert _rel(out["x"][r, j], x) <= bound
 

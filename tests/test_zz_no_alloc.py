@@ -91,3 +91,40 @@ def test_noalloc_rejects_sizes_beyond_the_scratch():
         L.lcmg_apply_normal_noalloc(0, None, P.n_v, P.n_h, m_big, rp, ci, va, rpT, ciT, vaT, d, lams, p, q)
     assert e.value.status == L.LCMG_ERR_INVALID_ARG
     assert "scratch" in L.lcmg_last_error()
+
+
+def test_noalloc_allocates_no_device_memory():
+    """After one call has loaded the library's device image on the GPU, two
+    more calls leave the free device memory and the caching allocator's
+    counters unchanged: nothing is allocated on the device."""
+    P = pg.make_problem("ct256", size=48)
+    A, n_v, n_h = P.A, P.n_v, P.n_h
+    rp, ci, va, rpT, ciT, vaT = _dev_csr(A)
+    d = torch.tensor(pg.random_weights(n_h * (n_v - 1) + (n_h - 1) * n_v, 3), dtype=torch.float64, device="cuda")
+    lams = np.array([0.1, 1.0])
+    p = torch.tensor(pg.rng(7).standard_normal((2, P.n)), dtype=torch.float64, device="cuda")
+    q = torch.empty_like(p)
+    L.lcmg_apply_normal_noalloc(0, None, n_v, n_h, A.m, rp, ci, va, rpT, ciT, vaT, d, lams, p, q)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    for _ in range(2):
+        L.lcmg_apply_normal_noalloc(0, None, n_v, n_h, A.m, rp, ci, va, rpT, ciT, vaT, d, lams, p, q)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    alloc1 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    assert free1 == free0
+    assert alloc1 == alloc0
+
+
+def test_noalloc_rejects_overlapping_p_and_q():
+    P = pg.make_problem("ct256", size=48)
+    A = P.A
+    rp, ci, va, rpT, ciT, vaT = _dev_csr(A)
+    d = torch.ones(P.n_h * (P.n_v - 1) + (P.n_h - 1) * P.n_v, dtype=torch.float64, device="cuda")
+    buf = torch.zeros((3, P.n), dtype=torch.float64, device="cuda")
+    with pytest.raises(L.LcmgError) as e:
+        L.lcmg_apply_normal_noalloc(0, None, P.n_v, P.n_h, A.m, rp, ci, va, rpT, ciT, vaT, d, np.array([0.1, 1.0]),
+                                    buf[0:2], buf[1:3])
+    assert e.value.status == L.LCMG_ERR_INVALID_ARG
+    assert "overlap" in L.lcmg_last_error()
