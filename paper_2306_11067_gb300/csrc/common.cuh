@@ -41,6 +41,26 @@ inline int64_t& launch_counter() {
     LCMG_CUDA(cudaGetLastError());       \
   } while (0)
 
+// Asynchronous global -> shared copies of one element (cp.async, 4 or 8
+// bytes), zero-filled when `valid` is false (source size 0; the source
+// address is then `fallback`, an address inside the array, and no byte is
+// read).  A thread issues all of its copies of a tile before it waits, so a
+// block keeps its whole tile's loads in flight instead of one per thread.
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* src, const T* fallback, bool valid) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  const T* g = valid ? src : fallback;
+  const int n = valid ? (int)sizeof(T) : 0;
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(g), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(g), "r"(n) : "memory");
+}
+// wait for every cp.async this thread issued (a __syncthreads must follow
+// before other threads read the copied data)
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 constexpr int kBlock = 256;      // threads per block of the point x column kernels
 constexpr int kMaxB = 256;       // widest batch one launch handles
 constexpr int kStencil = 25;     // coarse-level stencils are 5 x 5

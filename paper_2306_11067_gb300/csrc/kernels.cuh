@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(kBlock)
              const int* __restrict__ active, double* __restrict__ part) {
   __shared__ double sm[kBlock];
   const ColMap cm(B);
-  double dacc = 0.0;
+  DotAcc<T> dacc;
   if (cm.ok) {
     const int col = cm.col;
     const T l2 = lam2[col];
@@ -631,10 +631,10 @@ __global__ void __launch_bounds__(kBlock)
       const T rv = r[p * B + col];
       const T zn = zin[p * B + col] + dinv[p * B + col] * (rv - kz);
       zout[p * B + col] = zn;
-      dacc += to_d(rv) * to_d(zn);
+      dacc.add(rv, zn);
     }
   }
-  if (part) block_col_sum(dacc, cm, sm, part + (int64_t)blockIdx.x * B);
+  if (part) block_col_sum(dacc.value(), cm, sm, part + (int64_t)blockIdx.x * B);
 }
 
 // res = r - K z
@@ -890,7 +890,7 @@ __global__ void __launch_bounds__(kBlock)
                 TX* __restrict__ x, T* __restrict__ r, double* __restrict__ part) {
   __shared__ double sm[kBlock];
   const ColMap cm(B);
-  double acc = 0.0;
+  DotAcc<T> acc;
   if (cm.ok && st.active[cm.col]) {
     const int col = cm.col;
     const double al = st.alpha[col];
@@ -900,10 +900,23 @@ __global__ void __launch_bounds__(kBlock)
       x[e] = (TX)(x[e] + (TX)al * (TX)p[e]);
       const T rn = r[e] - alT * q[e];
       r[e] = rn;
-      acc += to_d(rn) * to_d(rn);
+      acc.add(rn, rn);
     }
   }
-  block_col_sum(acc, cm, sm, part + (int64_t)blockIdx.x * B);
+  block_col_sum(acc.value(), cm, sm, part + (int64_t)blockIdx.x * B);
+}
+
+// The sum of nb partials in a fixed order (the same in every block), by the
+// block's first warp; valid in lane 0 of warp 0 only.  One warp keeps the
+// FP64 work per block to nb additions: on this GPU the FP64 pipe runs at a
+// small fraction of the FP32 one, and every block of the fused updates
+// repeats the sum.
+__device__ __forceinline__ double warp0_sum(const double* __restrict__ part, int nb) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += 32) s += part[b];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  return s;
 }
 
 // One column (B = 1) with alpha taken in the update: every block sums the
@@ -918,22 +931,21 @@ __global__ void __launch_bounds__(kBlock)
     k_update_xr_alpha(int64_t n, ColState st, int nb_pq, const double* __restrict__ pq_part,
                       const T* __restrict__ p, const T* __restrict__ q, TX* __restrict__ x, T* __restrict__ r,
                       double* __restrict__ part) {
+  __shared__ double s_al;
+  __shared__ int s_ok;
   __shared__ double sm[kBlock / 32];
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nb_pq; b += kBlock) s += pq_part[b];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
-  __syncthreads();
   double pq = 0.0;
-#pragma unroll
-  for (int w = 0; w < kBlock / 32; ++w) pq += sm[w];
-  __syncthreads();
+  if (threadIdx.x < 32) pq = warp0_sum(pq_part, nb_pq);
   const int act = st.active[0];
   const double rzc = st.rz2[0];
   const bool fin = isfinite(pq);
-  const bool ok = act && fin && pq > 0.0;
-  const double al = ok ? rzc / pq : 0.0;
+  if (threadIdx.x == 0) {  // the step length once per block
+    s_ok = act && fin && pq > 0.0;
+    s_al = s_ok ? rzc / pq : 0.0;
+  }
+  __syncthreads();
+  const bool ok = s_ok != 0;
+  const double al = s_al;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st.rz[0] = rzc;
     st.counters[0] = 0;
@@ -974,20 +986,6 @@ __global__ void __launch_bounds__(kBlock)
   }
 }
 
-// sum of part[0 .. nb) in a fixed order, the same in every block
-__device__ __forceinline__ double fixed_block_sum(const double* __restrict__ part, int nb, double* sm) {
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += kBlock) s += part[b];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
-  __syncthreads();
-  double t = 0.0;
-#pragma unroll
-  for (int w = 0; w < kBlock / 32; ++w) t += sm[w];
-  __syncthreads();
-  return t;
-}
 
 // One column (B = 1, st.keep = 0) with beta taken in the p update: every
 // block sums the r.r and r.z partials in the same fixed order and takes the
@@ -1003,20 +1001,29 @@ __global__ void __launch_bounds__(kBlock)
     k_update_p_beta(int64_t n, ColState st, int nb_rr, const double* __restrict__ rr_part, int nb_rz,
                     const double* __restrict__ rz_part, int maxit, double rel_trigger, const T* __restrict__ z,
                     T* __restrict__ p) {
-  __shared__ double sm[kBlock / 32];
-  const double rr = fixed_block_sum(rr_part, nb_rr, sm);
-  const double rzn = fixed_block_sum(rz_part, nb_rz, sm);
-  const int act = st.active[0];
-  const double rzo = st.rz[0];
-  int kind = -1;  // -1 inactive, 0 regular, 1 converged, 2 limit, 3 breakdown, 4 non-finite
-  if (act) {
-    if (!isfinite(rr) || !isfinite(rzn)) kind = 4;
-    else if (rr <= st.tol2cc[0]) kind = 1;
-    else if (st.iters[0] >= maxit) kind = 2;
-    else if (!(rzn > 0.0)) kind = 3;
-    else kind = 0;
+  __shared__ double s_be;
+  __shared__ int s_kind;
+  double rr = 0.0, rzn = 0.0;
+  if (threadIdx.x < 32) {
+    rr = warp0_sum(rr_part, nb_rr);
+    rzn = warp0_sum(rz_part, nb_rz);
   }
-  const double be = kind == 0 ? rzn / rzo : 0.0;
+  const int act = st.active[0];
+  if (threadIdx.x == 0) {  // the decision and beta once per block
+    int kd = -1;  // -1 inactive, 0 regular, 1 converged, 2 limit, 3 breakdown, 4 non-finite
+    if (act) {
+      if (!isfinite(rr) || !isfinite(rzn)) kd = 4;
+      else if (rr <= st.tol2cc[0]) kd = 1;
+      else if (st.iters[0] >= maxit) kd = 2;
+      else if (!(rzn > 0.0)) kd = 3;
+      else kd = 0;
+    }
+    s_kind = kd;
+    s_be = kd == 0 ? rzn / st.rz[0] : 0.0;
+  }
+  __syncthreads();
+  const int kind = s_kind;
+  const double be = s_be;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (act) {
       st.rr[0] = rr;
@@ -1380,10 +1387,10 @@ __global__ void __launch_bounds__(kBlock)
     k_col_dot(int64_t n, int B, const T* __restrict__ x, const T* __restrict__ y, double* __restrict__ part) {
   __shared__ double sm[kBlock];
   const ColMap cm(B);
-  double acc = 0.0;
+  DotAcc<T> acc;
   if (cm.ok)
-    for (int64_t i = cm.first(); i < n; i += cm.stride()) acc += to_d(x[i * B + cm.col]) * to_d(y[i * B + cm.col]);
-  block_col_sum(acc, cm, sm, part + (int64_t)blockIdx.x * B);
+    for (int64_t i = cm.first(); i < n; i += cm.stride()) acc.add(x[i * B + cm.col], y[i * B + cm.col]);
+  block_col_sum(acc.value(), cm, sm, part + (int64_t)blockIdx.x * B);
 }
 
 // start of a solve: per-column state from ||c||^2 and the true residual
@@ -1540,7 +1547,7 @@ __global__ void __launch_bounds__(kBlock)
   __shared__ double sm[kBlock];
   const ColMap cm(B);
   const int64_t n = (int64_t)a.nv * a.nh;
-  double acc = 0.0;
+  DotAcc<T> acc;
   if (cm.ok) {
     const int col = cm.col;
     const T l2 = (T)lam2[col];
@@ -1551,15 +1558,15 @@ __global__ void __launch_bounds__(kBlock)
       const T qv = aty + l2 * fop.lap(p, i, j, pv);
       if (MODE == 1) {
         out[p * B + col] = (TO)qv;
-        acc += to_d(P[p * B + col]) * to_d(qv);
+        acc.add(P[p * B + col], qv);
       } else {
         const T rv = C[p * B + col] - qv;
         out[p * B + col] = (TO)rv;
-        acc += to_d(rv) * to_d(rv);
+        acc.add(rv, rv);
       }
     }
   }
-  block_col_sum(acc, cm, sm, part + (int64_t)blockIdx.x * B);
+  block_col_sum(acc.value(), cm, sm, part + (int64_t)blockIdx.x * B);
 }
 
 // c = A^T b for the n_rhs right-hand sides (interleaved [n][nrhs])

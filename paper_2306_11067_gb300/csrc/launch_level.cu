@@ -168,6 +168,19 @@ int launch_vup(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const
   return g;
 }
 
+// Grid of the fused one-column updates: every block re-sums the partials of
+// the dot products it needs (FP64), so the grid stays at 4 blocks of 256
+// threads per SM (a full SM of resident warps streams the vectors)
+static int fused_update_grid(int64_t n, int max_blocks) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    LCMG_CUDA(cudaGetDevice(&dev));
+    LCMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return std::min(grid_for(n, 1, max_blocks), std::max(1, 4 * sms));
+}
+
 int launch_vfine_down(const LevelView<float>& L, int B, const float* lam2, int smoother, double omega,
                       const float* r, float* rc, cudaStream_t s) {
   const int nt = ((L.nv + kFineTI - 1) / kFineTI) * ((L.nh + kFineTJ - 1) / kFineTJ);
@@ -258,7 +271,7 @@ int launch_update_xr(int64_t n, int B, const ColState& st, const T* p, const T* 
 template <class T, class TX>
 int launch_update_xr_alpha(int64_t n, const ColState& st, int nb_pq, const double* pq_part, const T* p,
                            const T* q, TX* x, T* r, double* part, int max_blocks, cudaStream_t s) {
-  const int g = grid_for(n, 1, max_blocks);
+  const int g = fused_update_grid(n, max_blocks);
   klaunch(k_update_xr_alpha<T, TX>, dim3(g), dim3(kBlock), 0, s, n, st, nb_pq, pq_part, p, q, x, r, part);
   LCMG_LAUNCHED();
   return g;
@@ -268,7 +281,7 @@ template <class T>
 void launch_update_p_beta(int64_t n, const ColState& st, int nb_rr, const double* rr_part, int nb_rz,
                           const double* rz_part, int maxit, double rel_trigger, const T* z, T* p, int max_blocks,
                           cudaStream_t s) {
-  const int g = grid_for(n, 1, max_blocks);
+  const int g = fused_update_grid(n, max_blocks);
   klaunch(k_update_p_beta<T>, dim3(g), dim3(kBlock), 0, s, n, st, nb_rr, rr_part, nb_rz, rz_part, maxit, rel_trigger,
           z, p);
   LCMG_LAUNCHED();

@@ -19,7 +19,8 @@
 // per-row corrections of the boundary rows, to every line of the image
 // along the contiguous axis (DIR 0) or the strided axis (DIR 1).  A block
 // stages a tile of 32 lines x (128 + 2H) samples in shared memory with
-// coalesced loads; each thread then owns 16 consecutive outputs of one line.
+// coalesced asynchronous copies; each thread then owns 16 consecutive
+// outputs of one line.
 // With the tap count TAPS fixed at compile time (the A^T A passes of the
 // common radii) the thread streams its 15 + TAPS samples once each from
 // shared memory and adds every one into each output it touches, so the
@@ -66,10 +67,11 @@ enum : int {
 template <class T>
 __host__ __device__ constexpr int band_smem_line(int nch) { return kBandSeg + kBandChunk * nch; }
 
-// shared memory of one block (the staged tile; reused for the DIR 0 store)
+// shared memory of one block: the staged input tile (line stride LEN + 1)
+// and the output tile (line stride kBandSeg + 1)
 template <class T>
 __host__ __device__ constexpr size_t band_smem_bytes(int nch) {
-  return (size_t)kBandLines * (band_smem_line<T>(nch) + 1) * sizeof(T);
+  return (size_t)kBandLines * ((band_smem_line<T>(nch) + 1) + (kBandSeg + 1)) * sizeof(T);
 }
 
 template <class T, class TO, int DIR, int EPI, int TAPS>
@@ -100,26 +102,24 @@ __global__ void __launch_bounds__(kBandThreads)
     const int seg0 = (tile % nseg) * kBandSeg;
     const int line0 = (tile / nseg) * kBandLines;
     // stage in(seg0 - H + m) for m in [0, LEN) of the tile's lines (zero
-    // outside), the lanes of a warp along the contiguous axis
+    // outside) with asynchronous copies, consecutive threads along the
+    // contiguous axis; every copy of the tile is in flight before the wait
     if (DIR == 0) {
-      for (int line = w; line < kBandLines; line += kBandThreads / 32) {
-        const int ln = line0 + line;
-        for (int m = lane; m < LEN; m += 32) {
-          const int a = seg0 - H + m;
-          T v = 0;
-          if (a >= 0 && a < len && ln < nlines) v = in[gpt(a, ln) * B + col];
-          sm[sidx(line, m)] = v;
-        }
+      for (int e = threadIdx.x; e < kBandLines * LEN; e += kBandThreads) {
+        const int line = e / LEN, m = e - line * LEN;
+        const int a = seg0 - H + m, ln = line0 + line;
+        const bool ok = a >= 0 && a < len && ln < nlines;
+        cp_async_elem(sm + sidx(line, m), in + (ok ? gpt(a, ln) * B + col : 0), in, ok);
       }
     } else {
-      const int ln = line0 + lane;
-      for (int m = w; m < LEN; m += kBandThreads / 32) {
+      for (int e = threadIdx.x; e < kBandLines * LEN; e += kBandThreads) {
+        const int ln = line0 + (e & (kBandLines - 1)), m = e / kBandLines;
         const int a = seg0 - H + m;
-        T v = 0;
-        if (a >= 0 && a < len && ln < nlines) v = in[gpt(a, ln) * B + col];
-        sm[sidx(lane, m)] = v;
+        const bool ok = a >= 0 && a < len && ln < nlines;
+        cp_async_elem(sm + sidx(e & (kBandLines - 1), m), in + (ok ? gpt(a, ln) * B + col : 0), in, ok);
       }
     }
+    cp_async_wait_all();
     __syncthreads();
     const int o0 = w * kBandR;  // first output of this thread (tile-local)
     T acc[kBandR];
@@ -151,36 +151,51 @@ __global__ void __launch_bounds__(kBandThreads)
           for (int k = 0; k < kBandChunk; ++k) acc[t] += cc[k] * win[t + k];
       }
     }
-    // rows near the ends of the line whose coefficients differ (zero boundary)
-    if (bd.d != nullptr) {
-      const int taps = 2 * H + 1;
+    // The rows near the ends of the line whose coefficients differ (zero
+    // boundary) add sum_k d[row][k] in(o - H + k).  Only the tiles at the
+    // ends of a line hold such rows; there every thread of the block takes
+    // a share of the (row, line) sums, on the output tile in shared memory
+    // (the owners of the first and last outputs alone would hold the block
+    // at the barrier for the whole of these sums).
+    constexpr int OS = kBandSeg + 1;
+    T* so = sm + kBandLines * LS;
+    const bool corr = bd.d != nullptr && (seg0 < bd.nlo || seg0 + kBandSeg > len - bd.nhi);  // block-uniform
+    if (DIR == 0 || corr) {
 #pragma unroll
-      for (int t = 0; t < kBandR; ++t) {
-        const int o = seg0 + o0 + t;
-        if (o >= len) continue;
-        int row = -1;
-        if (o < bd.nlo) row = o;
-        else if (o >= len - bd.nhi) row = bd.nlo + o - (len - bd.nhi);
-        if (row < 0) continue;
+      for (int t = 0; t < kBandR; ++t) so[lane * OS + o0 + t] = acc[t];
+    }
+    if (corr) {
+      __syncthreads();
+      const int taps = 2 * H + 1;
+      const int ohi = min(seg0 + kBandSeg, len);
+      const int hend = min(ohi, bd.nlo);                             // head rows [seg0, hend)
+      const int tbeg = max(seg0, max(len - bd.nhi, bd.nlo));         // tail rows [tbeg, ohi)
+      const int nhead = max(0, hend - seg0), nrows = nhead + max(0, ohi - tbeg);
+      for (int e = threadIdx.x; e < nrows * kBandLines; e += kBandThreads) {
+        const int line = e & (kBandLines - 1), rr = e / kBandLines;
+        const int o = rr < nhead ? seg0 + rr : tbeg + (rr - nhead);
+        const int row = o < bd.nlo ? o : bd.nlo + o - (len - bd.nhi);
         const T* dr = bd.d + (int64_t)row * taps;
-        T s = 0;
-        for (int k = 0; k < taps; ++k) s += dr[k] * sm[sidx(lane, o0 + t + k)];
-        acc[t] += s;
+        const int ol = o - seg0;
+        T sum = 0;
+        for (int k = 0; k < taps; ++k) sum += dr[k] * sm[sidx(line, ol + k)];
+        so[line * OS + ol] += sum;
       }
     }
     if constexpr (DIR == 0) {
       // through shared memory, so that the stores run along the contiguous axis
       __syncthreads();
-      constexpr int OS = kBandSeg + 1;
-#pragma unroll
-      for (int t = 0; t < kBandR; ++t) sm[lane * OS + o0 + t] = acc[t];
-      __syncthreads();
       for (int t = threadIdx.x; t < kBandLines * kBandSeg; t += kBandThreads) {
         const int line = t / kBandSeg, m = t - line * kBandSeg;
         const int a = seg0 + m, ln = line0 + line;
-        if (a < len && ln < nlines) out[gpt(a, ln) * B + col] = (TO)sm[line * OS + m];
+        if (a < len && ln < nlines) out[gpt(a, ln) * B + col] = (TO)so[line * OS + m];
       }
     } else {
+      if (corr) {
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < kBandR; ++t) acc[t] = so[lane * OS + o0 + t];
+      }
       const int i = line0 + lane;
       if (i < nv) {
 #pragma unroll
