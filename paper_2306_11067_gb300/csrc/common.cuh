@@ -57,9 +57,23 @@ __device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* src, const T
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(g), "r"(n) : "memory");
 }
+// 16 bytes (both addresses 16-byte aligned), zero-filled when !valid
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* src, const void* fallback, bool valid) {
+  const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  const void* g = valid ? src : fallback;
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(g), "r"(n) : "memory");
+}
 // wait for every cp.async this thread issued (a __syncthreads must follow
 // before other threads read the copied data)
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// close the group of copies issued so far; wait until at most N groups of
+// this thread are still in flight
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 constexpr int kBlock = 256;      // threads per block of the point x column kernels
 constexpr int kMaxB = 256;       // widest batch one launch handles

@@ -108,7 +108,11 @@ struct CoarseOpH {
 
   // k[o] of K(lam) for o < 25 (lam2 is already in the stored rows)
   __device__ __forceinline__ void coefs(int64_t p, float, float (&k)[28]) const {
-    const uint4 q0 = rows[3 * p], q1 = rows[3 * p + 1], q2 = rows[3 * p + 2];
+    decode(rows[3 * p], rows[3 * p + 1], rows[3 * p + 2], s[p], k);
+  }
+  // the same from a row's three 16-byte words and its row sum
+  __device__ __forceinline__ void decode(const uint4 q0, const uint4 q1, const uint4 q2, const float sp,
+                                        float (&k)[28]) const {
     const uint32_t w[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
     float off[kCompactOff];
 #pragma unroll
@@ -122,7 +126,7 @@ struct CoarseOpH {
     for (int o = 0; o < kCompactOff; ++o) sum += off[o];
 #pragma unroll
     for (int o = 0; o < 12; ++o) k[o] = off[o];
-    k[12] = s[p] - sum;
+    k[12] = sp - sum;
 #pragma unroll
     for (int o = 13; o < 25; ++o) k[o] = off[o - 1];
     k[25] = k[26] = k[27] = 0;

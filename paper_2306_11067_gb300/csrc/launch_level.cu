@@ -7,6 +7,7 @@
 #include <utility>
 
 #include "launch.h"
+#include "vcoarse.cuh"
 #include "vfine.cuh"
 #include "vfused.cuh"
 
@@ -71,7 +72,7 @@ void launch_residual(const LevelView<T>& L, int B, const T* lam2, const T* r, co
 // Grid of a tile kernel: every tile once, at most the blocks resident at
 // once on the device and at most kMaxTileBlocks (rows of the partial sums).
 template <class K>
-static int tile_grid(K kern, int threads, int ntiles) {
+static int tile_grid(K kern, int threads, int ntiles, size_t smem = 0) {
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, int> cache;
   int dev = 0;
@@ -83,7 +84,7 @@ static int tile_grid(K kern, int threads, int ntiles) {
     auto it = cache.find(key);
     if (it == cache.end()) {
       int nb = 0, sms = 0;
-      LCMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, 0));
+      LCMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem));
       LCMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
       it = cache.emplace(key, std::max(1, nb) * sms).first;
     }
@@ -112,6 +113,24 @@ static int vup_one(const Op& op, int B, const T* lam2, const T* dinv, const T* r
   return g;
 }
 
+// FP16 coarse levels with one sweep: the staged, double-buffered tile kernels
+static int vdown_h(const CoarseOpH& op, int B, const float* dinv, const float* r, float* zpre, float* rc, int ntx,
+                   int ntiles, cudaStream_t s) {
+  const size_t smem = 2 * sizeof(VcDownStage);
+  const int g = tile_grid(k_vdown_h, kVcThreads, ntiles, smem);
+  klaunch(k_vdown_h, dim3((unsigned)g, (unsigned)B), dim3(kVcThreads), smem, s, op, B, dinv, r, zpre, rc, ntx,
+          ntiles);
+  return g;
+}
+static int vup_h(const CoarseOpH& op, int B, const float* dinv, const float* r, const float* ec, const float* zpre,
+                 float* zout, double* part, int ntx, int ntiles, cudaStream_t s) {
+  const size_t smem = 2 * sizeof(VcUpStage);
+  const int g = tile_grid(k_vup_h, kVcThreads, ntiles, smem);
+  klaunch(k_vup_h, dim3((unsigned)g, (unsigned)B), dim3(kVcThreads), smem, s, op, B, dinv, r, ec, zpre, zout, ntx,
+          ntiles, part);
+  return g;
+}
+
 template <class T>
 int launch_vdown(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const T* r, T* zpre, T* rc,
                  int nu, cudaStream_t s) {
@@ -124,7 +143,7 @@ int launch_vdown(const LevelView<T>& L, int B, const T* lam2, const T* dinv, con
         g = nu == 1 ? vdown_one<FineOpH, float, 1>(L.fh, B, lam2, dinv, r, zpre, rc, ntx, nt, s)
                     : vdown_one<FineOpH, float, 2>(L.fh, B, lam2, dinv, r, zpre, rc, ntx, nt, s);
       else
-        g = nu == 1 ? vdown_one<CoarseOpH, float, 1>(L.ch, B, lam2, dinv, r, zpre, rc, ntx, nt, s)
+        g = nu == 1 ? vdown_h(L.ch, B, dinv, r, zpre, rc, ntx, nt, s)
                     : vdown_one<CoarseOpH, float, 2>(L.ch, B, lam2, dinv, r, zpre, rc, ntx, nt, s);
       LCMG_LAUNCHED();
       return g;
@@ -152,7 +171,7 @@ int launch_vup(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const
         g = nu == 1 ? vup_one<FineOpH, float, 1>(L.fh, B, lam2, dinv, r, ec, zpre, zout, part, ntx, nt, s)
                     : vup_one<FineOpH, float, 2>(L.fh, B, lam2, dinv, r, ec, zpre, zout, part, ntx, nt, s);
       else
-        g = nu == 1 ? vup_one<CoarseOpH, float, 1>(L.ch, B, lam2, dinv, r, ec, zpre, zout, part, ntx, nt, s)
+        g = nu == 1 ? vup_h(L.ch, B, dinv, r, ec, zpre, zout, part, ntx, nt, s)
                     : vup_one<CoarseOpH, float, 2>(L.ch, B, lam2, dinv, r, ec, zpre, zout, part, ntx, nt, s);
       LCMG_LAUNCHED();
       return g;
@@ -185,7 +204,14 @@ int launch_vfine_down(const LevelView<float>& L, int B, const float* lam2, int s
                       const float* r, float* rc, cudaStream_t s) {
   const int nt = ((L.nv + kFineTI - 1) / kFineTI) * ((L.nh + kFineTJ - 1) / kFineTJ);
   int g;
-  if (L.h16) {
+  if (L.h16 && L.nv % 2 == 0 && L.nh % 2 == 0 && (int64_t)L.nv * L.nh * B < (int64_t(1) << 31)) {  // row streaming
+    const int nsi = (L.nv / 2 + kDownCols - 1) / kDownCols;
+    const int nst = nsi * ((L.nh / 2 + kStripCoarse - 1) / kStripCoarse);
+    auto k = B == 1 ? k_vfine_down_s<true> : k_vfine_down_s<false>;
+    g = tile_grid(k, kFineThreads, (nst + kFineThreads / 32 - 1) / (kFineThreads / 32));
+    klaunch(k, dim3((unsigned)g, (unsigned)B), dim3(kFineThreads), 0, s, L.fh, B, lam2, smoother, (float)omega, r,
+            rc, nsi, nst);
+  } else if (L.h16) {
     g = tile_grid(k_vfine_down<FineOpH>, kFineThreads, nt);
     klaunch(k_vfine_down<FineOpH>, dim3((unsigned)g, (unsigned)B), dim3(kFineThreads), 0, s, L.fh, B, lam2, smoother,
             (float)omega, r, rc, nt);
@@ -202,7 +228,14 @@ int launch_vfine_up(const LevelView<float>& L, int B, const float* lam2, int smo
                     const float* r, const float* ec, float* zout, double* part, cudaStream_t s) {
   const int nt = ((L.nv + kFineTI - 1) / kFineTI) * ((L.nh + kFineTJ - 1) / kFineTJ);
   int g;
-  if (L.h16) {
+  if (L.h16 && L.nv % 2 == 0 && L.nh % 2 == 0 && (int64_t)L.nv * L.nh * B < (int64_t(1) << 31)) {  // row streaming
+    const int nsi = (L.nv + kUpCols - 1) / kUpCols;
+    const int nst = nsi * ((L.nh + kStripRows - 1) / kStripRows);
+    auto k = B == 1 ? k_vfine_up_s<true> : k_vfine_up_s<false>;
+    g = tile_grid(k, kFineThreads, (nst + kFineThreads / 32 - 1) / (kFineThreads / 32));
+    klaunch(k, dim3((unsigned)g, (unsigned)B), dim3(kFineThreads), 0, s, L.fh, B, lam2, smoother, (float)omega, r,
+            ec, zout, nsi, nst, part);
+  } else if (L.h16) {
     g = tile_grid(k_vfine_up<FineOpH>, kFineThreads, nt);
     klaunch(k_vfine_up<FineOpH>, dim3((unsigned)g, (unsigned)B), dim3(kFineThreads), 0, s, L.fh, B, lam2, smoother,
             (float)omega, r, ec, zout, nt, part);

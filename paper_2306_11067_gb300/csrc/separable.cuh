@@ -105,11 +105,13 @@ __global__ void __launch_bounds__(kBandThreads)
     // outside) with asynchronous copies, consecutive threads along the
     // contiguous axis; every copy of the tile is in flight before the wait
     if (DIR == 0) {
-      for (int e = threadIdx.x; e < kBandLines * LEN; e += kBandThreads) {
-        const int line = e / LEN, m = e - line * LEN;
-        const int a = seg0 - H + m, ln = line0 + line;
-        const bool ok = a >= 0 && a < len && ln < nlines;
-        cp_async_elem(sm + sidx(line, m), in + (ok ? gpt(a, ln) * B + col : 0), in, ok);
+      for (int line = w; line < kBandLines; line += kBandThreads / 32) {
+        const int ln = line0 + line;
+        for (int m = lane; m < LEN; m += 32) {
+          const int a = seg0 - H + m;
+          const bool ok = a >= 0 && a < len && ln < nlines;
+          cp_async_elem(sm + sidx(line, m), in + (ok ? gpt(a, ln) * B + col : 0), in, ok);
+        }
       }
     } else {
       for (int e = threadIdx.x; e < kBandLines * LEN; e += kBandThreads) {

@@ -207,4 +207,256 @@ __global__ void __launch_bounds__(kFineThreads)
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Row-streaming forms of the two FP16 kernels (the default).  A warp owns
+// 32 consecutive points along i (one per lane) and walks down a strip of
+// rows j: the neighbours along j of the point a lane is at are values it
+// computed one row earlier or one row ahead (kept in registers), those
+// along i are the neighbouring lanes' values (warp shuffles).  The two edge
+// lanes of a warp compute only what their neighbours need (the halo), so a
+// warp produces 30 points of z (k_vfine_up_s) or 14 coarse points of r_c
+// (k_vfine_down_s) per row.  No shared memory, no barrier; a row's loads
+// are issued one row ahead of their use, from addresses clamped into the
+// arrays, and every per-point step is branch-free (selects), so that a
+// lane's work per row is its arithmetic and little else.
+//
+// Each point's formulas are those of k_vfine_up / k_vfine_down, with two
+// changes of rounding: D^{-1} = 1 / (2 lam^2 sum w + g) (or omega / (lam^2
+// sum w + g)) is taken with the fast division (__fdividef, within 2 ulp),
+// the same value in both kernels, so the cycle stays one fixed symmetric
+// operator; and r_c = P^T res is summed per fine row along i first, then
+// along j.  32-bit indices: the launcher takes this path while
+// n_v n_h B < 2^31.
+// ---------------------------------------------------------------------------
+constexpr int kStripRows = 32;    // fine rows of z per k_vfine_up_s strip
+constexpr int kStripCoarse = 16;  // coarse rows of r_c per k_vfine_down_s strip
+constexpr int kUpCols = 30;       // z columns per warp
+constexpr int kDownCols = 14;     // r_c columns per warp
+
+// the raw data of the lane's point p = i + j n_v of one row: FP16 w_s(p),
+// w_s(p - 1), w_e(p), diag(A^T A)(p), r(p) and, for the up kernel, the four
+// coarse corrections of P e_c (element stride S of the interleaved vectors)
+struct RawRow {
+  __half s, n, e, g;
+  float r;
+  float c[4];
+};
+template <bool kCoarse>
+__device__ __forceinline__ RawRow fine_load(const __half* __restrict__ ws, const __half* __restrict__ we,
+                                            const __half* __restrict__ ga, const float* __restrict__ r,
+                                            const float* __restrict__ ec, int S, int col, bool in, int p, int ea,
+                                            int eb, int Iac, int Ibc) {
+  RawRow q;
+  const int pc = in ? p : 0;
+  q.s = ws[pc];
+  q.n = ws[pc > 0 ? pc - 1 : 0];
+  q.e = we[pc];
+  q.g = ga[pc];
+  q.r = r[pc * S + col];
+  if (kCoarse) {
+    q.c[0] = ec[(ea + Iac) * S + col];
+    q.c[1] = ec[(ea + Ibc) * S + col];
+    q.c[2] = ec[(eb + Iac) * S + col];
+    q.c[3] = ec[(eb + Ibc) * S + col];
+  }
+  return q;
+}
+
+// the point data a lane carries from one row to the next
+struct FineRow {
+  float z;     // z1 = D^{-1} r (down) or z0 = z1 + P e_c (up)
+  float r, d;  // r and D^{-1}
+  float s, n, e, w, g;
+};
+
+// weights, D^{-1} and z1 of the lane's point (all zero outside the grid);
+// w_prev = e of (i, j - 1)
+__device__ __forceinline__ FineRow fine_row(const RawRow& q, float sw, float sg, float l2, int smoother, float omega,
+                                            bool in, bool has_s, bool has_n, bool has_e, float w_prev) {
+  FineRow f;
+  f.s = (in && has_s) ? __half2float(q.s) * sw : 0.f;
+  f.n = (in && has_n) ? __half2float(q.n) * sw : 0.f;
+  f.e = (in && has_e) ? __half2float(q.e) * sw : 0.f;
+  f.w = w_prev;
+  f.g = in ? __half2float(q.g) * sg : 0.f;
+  f.r = in ? q.r : 0.f;
+  const float sum = f.s + f.n + f.e + f.w;
+  const float dv = smoother == 0 ? __fdividef(1.0f, 2.0f * l2 * sum + f.g) : __fdividef(omega, l2 * sum + f.g);
+  f.d = in ? dv : 0.f;
+  f.z = f.d * f.r;
+  return f;
+}
+
+// (K z)_p from the lane's row record and its neighbours' z
+__device__ __forceinline__ float fine_row_kz(const FineRow& f, float l2, float zs, float zn, float ze, float zw) {
+  const float zp = f.z;
+  const float acc = f.s * (zp - zs) + f.n * (zp - zn) + f.e * (zp - ze) + f.w * (zp - zw);
+  return l2 * acc + f.g * zp;
+}
+
+// pw1 of the two coarse neighbours of fine index a on a line of n = 2 nc
+// points: the nearer one (3/4, or 1 at the ends of the line) and the other
+// one (1/4, or 0 at the ends, where it falls outside)
+__device__ __forceinline__ void pw1_pair(int a, int n, float& wnear, float& wfar) {
+  const bool edge = a == 0 || a == n - 1;
+  wnear = edge ? 1.f : 0.75f;
+  wfar = edge ? 0.f : 0.25f;
+}
+
+template <bool kUnit>
+__global__ void __launch_bounds__(kFineThreads)
+    k_vfine_up_s(FineOpH op, int B, const float* __restrict__ lam2, int smoother, float omega,
+                 const float* __restrict__ r, const float* __restrict__ ec, float* __restrict__ zout, int nsi,
+                 int nstrips, double* __restrict__ part) {
+  __shared__ double sred[kFineThreads / 32];
+  const unsigned FULL = 0xffffffffu;
+  const int S = kUnit ? 1 : B;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.y;
+  const int nv = op.nv, nh = op.nh, nvc = nv / 2, nhc = nh / 2;
+  const __half* __restrict__ ws = op.ws;
+  const __half* __restrict__ we = op.we;
+  const __half* __restrict__ ga = op.ga;
+  const float sw = op.sw, sg = op.sg;
+  const float l2 = lam2[col];
+  Dot2 dot;
+  for (int st = blockIdx.x * (kFineThreads / 32) + warp; st < nstrips; st += gridDim.x * (kFineThreads / 32)) {
+    const int i = (st % nsi) * kUpCols - 1 + lane;
+    const int j0 = (st / nsi) * kStripRows, j1 = min(j0 + kStripRows, nh);
+    const bool in_i = i >= 0 && i < nv, has_s = i + 1 < nv, has_n = i > 0;
+    const bool out = lane >= 1 && lane <= kUpCols && i < nv;
+    // interpolation along i (fixed for the lane): coarse columns Ia, Ib
+    const int Ia = i >> 1;
+    float waA, waB;
+    pw1_pair(i, nv, waA, waB);
+    const int Iac = min(max(Ia, 0), nvc - 1);
+    const int Ibc = min(max((i & 1) ? Ia + 1 : Ia - 1, 0), nvc - 1);
+    auto load = [&](int j, int q) {
+      const int Ja = min(max(j >> 1, 0), nhc - 1);
+      const int Jb = min(max((j & 1) ? Ja + 1 : Ja - 1, 0), nhc - 1);
+      return fine_load<true>(ws, we, ga, r, ec, S, col, in_i && j >= 0 && j < nh, q, Ja * nvc, Jb * nvc, Iac, Ibc);
+    };
+    // z0 = D^{-1} r + P e_c at row j (zero outside the grid)
+    auto row = [&](const RawRow& q, int j, float w_prev) {
+      const bool in = in_i && j >= 0 && j < nh;
+      FineRow f = fine_row(q, sw, sg, l2, smoother, omega, in, has_s, has_n, j + 1 < nh, w_prev);
+      float wbA, wbB;
+      pw1_pair(j, nh, wbA, wbB);
+      float acc = 0.f;  // the terms in the order of k_vfine_up (a zero weight adds nothing)
+      acc += wbA * waA * q.c[0];
+      acc += wbA * waB * q.c[1];
+      acc += wbB * waA * q.c[2];
+      acc += wbB * waB * q.c[3];
+      f.z += in ? acc : 0.f;
+      return f;
+    };
+    int p = i + (j0 - 1) * nv;  // the lane's point in row j0 - 1
+    float we_prev = 0.f;        // e of the row above, the w of the next row
+    if (j0 - 2 >= 0 && in_i && j0 - 1 < nh) we_prev = __half2float(we[p - nv]) * sw;
+    RawRow qn = load(j0 + 1, p + 2 * nv);  // in flight while rows j0 - 1 and j0 are finished
+    FineRow fm = row(load(j0 - 1, p), j0 - 1, we_prev);
+    p += nv;
+    FineRow fc = row(load(j0, p), j0, fm.e);
+    for (int j = j0; j < j1; ++j) {
+      const RawRow qj = qn;
+      qn = load(j + 2, p + 2 * nv);  // the loads of the row after next
+      const FineRow fp = row(qj, j + 1, fc.e);
+      const float zs = __shfl_down_sync(FULL, fc.z, 1);
+      const float zn = __shfl_up_sync(FULL, fc.z, 1);
+      const float zn1 = fc.z + fc.d * (fc.r - fine_row_kz(fc, l2, zs, zn, fp.z, fm.z));
+      if (out) zout[p * S + col] = zn1;
+      dot.add(out ? fc.r : 0.f, out ? zn1 : 0.f);
+      fm = fc;
+      fc = fp;
+      p += nv;
+    }
+  }
+  if (part) {
+    double dacc = dot.value();
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dacc += __shfl_xor_sync(FULL, dacc, off);
+    if (lane == 0) sred[warp] = dacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int k = 0; k < kFineThreads / 32; ++k) sum += sred[k];
+      part[(int64_t)blockIdx.x * B + col] = sum;
+    }
+  }
+}
+
+template <bool kUnit>
+__global__ void __launch_bounds__(kFineThreads)
+    k_vfine_down_s(FineOpH op, int B, const float* __restrict__ lam2, int smoother, float omega,
+                   const float* __restrict__ r, float* __restrict__ rc, int nsi, int nstrips) {
+  const unsigned FULL = 0xffffffffu;
+  const int S = kUnit ? 1 : B;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.y;
+  const int nv = op.nv, nh = op.nh, nvc = nv / 2, nhc = nh / 2;
+  const __half* __restrict__ ws = op.ws;
+  const __half* __restrict__ we = op.we;
+  const __half* __restrict__ ga = op.ga;
+  const float sw = op.sw, sg = op.sg;
+  const float l2 = lam2[col];
+  for (int st = blockIdx.x * (kFineThreads / 32) + warp; st < nstrips; st += gridDim.x * (kFineThreads / 32)) {
+    const int I0 = (st % nsi) * kDownCols, J0 = (st / nsi) * kStripCoarse;
+    const int i = 2 * I0 - 2 + lane;  // z1 at every lane, res at lanes 1..30
+    const bool in_i = i >= 0 && i < nv, has_s = i + 1 < nv, has_n = i > 0;
+    // restriction along i: coarse column I = I0 + lane (lanes < 14) from the
+    // residual at fine columns 2I - 1 .. 2I + 2 (lanes 2 lane + 1 .. 2 lane + 4)
+    const int I = I0 + lane;
+    const bool out = lane < kDownCols && I < nvc;
+    float wa[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int a2 = 2 * I - 1 + m;
+      wa[m] = (a2 >= 0 && a2 < nv && I < nvc) ? pw1<float>(a2, I, nvc) : 0.f;
+    }
+    const int jb0 = 2 * J0 - 1, jb1 = min(2 * (J0 + kStripCoarse), nh);  // residual rows [jb0, jb1]
+    int p = i + (jb0 - 1) * nv;  // the lane's point in row jb0 - 1
+    float we_prev = 0.f;
+    if (jb0 - 2 >= 0 && in_i && jb0 - 1 < nh) we_prev = __half2float(we[p - nv]) * sw;
+    auto load = [&](int j, int q) {
+      return fine_load<false>(ws, we, ga, r, nullptr, S, col, in_i && j >= 0 && j < nh, q, 0, 0, 0, 0);
+    };
+    auto row = [&](const RawRow& q, int j, float w_prev) {
+      return fine_row(q, sw, sg, l2, smoother, omega, in_i && j >= 0 && j < nh, has_s, has_n, j + 1 < nh, w_prev);
+    };
+    RawRow qn = load(jb0 + 1, p + 2 * nv);  // in flight while rows jb0 - 1 and jb0 are finished
+    FineRow fm = row(load(jb0 - 1, p), jb0 - 1, we_prev);
+    p += nv;
+    FineRow fc = row(load(jb0, p), jb0, fm.e);
+    float prev = 0.f, cur = 0.f;  // r_c of coarse rows (b - 1) / 2 and (b + 1) / 2 being summed
+    for (int b = jb0; b <= jb1; ++b) {
+      const RawRow qb = qn;
+      qn = load(b + 2, p + 2 * nv);  // the loads of the row after next
+      const FineRow fp = row(qb, b + 1, fc.e);
+      const float zs = __shfl_down_sync(FULL, fc.z, 1);
+      const float zn = __shfl_up_sync(FULL, fc.z, 1);
+      // res = r - K z1, zero outside the grid (so that it adds nothing below)
+      const bool in = in_i && b >= 0 && b < nh;
+      const float res = in ? fc.r - fine_row_kz(fc, l2, zs, zn, fp.z, fm.z) : 0.f;
+      float ti = 0.f;  // sum over a of pw1(a, I) res(a, b)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) ti += wa[m] * __shfl_sync(FULL, res, (2 * lane + 1 + m) & 31);
+      const float wb = (b == 0 || b == nh - 1) ? 1.f : 0.75f;  // pw1(b, b / 2)
+      const int m = b >> 1;
+      if ((b & 1) == 0) {  // b = 2m: the last term of coarse row m - 1, the second of row m
+        prev += 0.25f * ti;
+        if (out && m - 1 >= J0 && m - 1 < nhc) rc[(I + (m - 1) * nvc) * S + col] = prev;
+        prev = cur + wb * ti;
+        cur = 0.f;
+      } else {  // b = 2m + 1: the third term of row m, the first of row m + 1
+        prev += wb * ti;
+        cur += 0.25f * ti;
+      }
+      fm = fc;
+      fc = fp;
+      p += nv;
+    }
+  }
+}
+
 }  // namespace lcmg
