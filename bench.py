@@ -60,6 +60,16 @@ MAXIT = 10000
 KERNEL_SRC = os.path.join(ROOT, "paper_2306_11067_gb300", "csrc", "kernels.cuh")
 LAUNCH_SRC = os.path.join(ROOT, "paper_2306_11067_gb300", "csrc", "launch_spmm.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_spmv1_ct256_traffic.txt")
+CSRC = os.path.join(ROOT, "paper_2306_11067_gb300", "csrc")
+# ncu DRAM records of the deblur2048 kernels: (file, source files whose
+# contents the record is valid for)
+RECORDS = {
+    "k_band": (os.path.join(ROOT, "profiles", "k_band_deblur2048_traffic.txt"),
+               ("separable.cuh", "separable.cu", "kernels.cuh", "common.cuh")),
+    "vcycle": (os.path.join(ROOT, "profiles", "vcycle_deblur2048_traffic.txt"),
+               ("vfine.cuh", "vcoarse.cuh", "vfused.cuh", "compact.cuh", "kernels.cuh", "launch_level.cu",
+                "common.cuh")),
+}
 
 
 def parse():
@@ -309,6 +319,38 @@ def kernel_fingerprint():
     return hashlib.sha256((src[i:j] + lsrc[a:b]).encode()).hexdigest()[:16]
 
 
+def source_fingerprint(kind):
+    """sha256[:16] over the source files a deblur2048 DRAM record covers."""
+    h = hashlib.sha256()
+    for name in RECORDS[kind][1]:
+        h.update(open(os.path.join(CSRC, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded(kind):
+    """The key: value pairs of a committed deblur2048 ncu record, if it was
+    taken on the current sources; else None."""
+    path = RECORDS[kind][0]
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_sha256_16") != source_fingerprint(kind):
+        return None
+    return kv
+
+
+def recorded_float(kind, key):
+    kv = recorded(kind)
+    try:
+        return float(kv[key]) if kv else None
+    except (KeyError, ValueError):
+        return None
+
+
 def recorded_traffic():
     """DRAM bytes per launch of the operator passes from the committed ncu
     summary, if it was taken on the current kernel source; else None."""
@@ -418,9 +460,22 @@ def serving_leg(device, n_requests=40, rates=(1.0,)):
 def profile_workload(args):
     """A short run for profiler captures: the workload's operator and
     hierarchy, one lambda (the middle of the grid) solved from zero for
-    args.profile_iters PCG iterations (mixed precision, one column)."""
+    args.profile_iters PCG iterations (mixed precision, one column).  For
+    deblur2048 the solver is the timed step's (same sizes, levels, kernels
+    and launch shapes) with seeded stand-in edge weights in place of D^(2)."""
     import problemgen as pg
     from paper_2306_11067_gb300 import lcmg as L
+    if args.workload == "deblur2048":
+        P = pg.make_problem("deblur2048")
+        prec = L.PREC_MIXED if args.precision == "mixed" else L.PREC_FP64
+        s = L.Solver(P.n_v, P.n_h, precision=prec, mode=L.MODE_SEQUENTIAL, nu=NU, tol=1e-30,
+                     maxit=args.profile_iters, levels=P.levels)
+        s.set_forward_stencil(P.psf)
+        s.set_weights(pg.random_weights(P.n_h * (P.n_v - 1) + (P.n_h - 1) * P.n_v, 3, d_min=0.05))
+        lam = P.lambdas[len(P.lambdas) // 2: len(P.lambdas) // 2 + 1]
+        s.solve(lam, P.b[:, 0])
+        s.close()
+        return
     P = pg.make_problem("ct256")
     kw = {0: dict(precision=L.PREC_MIXED),
           1: dict(precision=L.PREC_FP64, precond=1),
@@ -706,7 +761,8 @@ def main_deblur(args, world, rank, local):
         "avg_us_pass_h": (sum(s_["op_ms_at"] for s_ in st) * 2e3 / op_launches) if op_launches else None,
         "fp32_gflop_per_apply": 2.0 * P.n * 2 * 61 / 1e9,
         "share_of_iteration_time": ((op_ms * 2 / op_launches) * b_its / it_ms) if (it_ms > 0 and op_launches) else None,
-        "traffic": None,
+        "traffic": recorded_float("k_band", "dram_bytes_per_apply") if prec == L.PREC_MIXED else None,
+        "traffic_unit": "DRAM bytes per apply (both passes), ncu, profiles/k_band_deblur2048_traffic.txt",
     }
     band["frac"] = band["achieved"] / peak if band["achieved"] else None
     vcyc = {
@@ -716,8 +772,12 @@ def main_deblur(args, world, rank, local):
         "algorithmic_bytes_per_cycle": (v_bytes / v_cnt) if v_cnt else None,
         "avg_us_per_cycle": (v_ms * 1e3 / v_cnt) if v_cnt else None,
         "share_of_iteration_time": ((v_ms / v_cnt) * b_its / it_ms) if (it_ms > 0 and v_cnt) else None,
-        "traffic": None,
+        "traffic": recorded_float("vcycle", "dram_bytes_per_cycle") if prec == L.PREC_MIXED else None,
+        "traffic_unit": "DRAM bytes per cycle (all its kernels), ncu, profiles/vcycle_deblur2048_traffic.txt",
     }
+    vrec = recorded("vcycle") if prec == L.PREC_MIXED else None
+    if vrec:  # per-level DRAM GB/s of the cycle's kernels (ncu, cold cache, serialised)
+        vcyc["levels_ncu"] = {k[len("level_"):]: v for k, v in vrec.items() if k.startswith("level_")}
     vcyc["frac"] = vcyc["achieved"] / peak if vcyc["achieved"] else None
     dominant, other = (vcyc, band) if (vcyc["share_of_iteration_time"] or 0) >= (band["share_of_iteration_time"] or 0) \
         else (band, vcyc)

@@ -632,7 +632,13 @@ struct Batch {
       // finest level of a V(1,1) cycle in FP32 runs the kernels that form it
       // on the fly (vfine.cuh)
       const bool fine1 = fine_v11();
-      for (int k = 0; k < nlev - 1; ++k) {
+      // FP16 coarse levels of at most kTailPoints points and the coarsest
+      // solve: one single-block kernel (vtail.cuh)
+      int t0 = nlev - 1;
+      if (std::is_same<T, float>::value && c.h16_on && nu == 1)
+        while (t0 - 1 >= 1 && c.lev[t0 - 1].n <= kTailPoints) --t0;
+      if (!vtail_fits(nlev - t0)) t0 = nlev - 1;
+      for (int k = 0; k < t0; ++k) {
         if (k == 0 && fine1)
           launch_vfine_down(view<float>(c, 0), B, reinterpret_cast<const float*>(lam2T()), c.prm.smoother,
                             c.prm.omega, reinterpret_cast<const float*>(rhs[0]),
@@ -641,8 +647,21 @@ struct Batch {
           launch_vdown<T>(view<T>(c, k), B, lam2T(), tp(c.lw[k].dinv), rhs[k], tp(c.lw[k].t), tp(c.lw[k + 1].rhs),
                           nu, s);
       }
-      launch_coarse_solve<T>((int)c.lev[nlev - 1].n, B, c.kinv.p, rhs[nlev - 1], zz[nlev - 1], s);
-      for (int k = nlev - 2; k >= 0; --k) {
+      if (t0 < nlev - 1) {
+        std::vector<TailLevelIn> tl(nlev - t0);
+        for (int k = t0; k < nlev; ++k) {
+          TailLevelIn& e = tl[k - t0];
+          const LevelView<float> v = view<float>(c, k);
+          e.op = v.ch;
+          e.dinv = reinterpret_cast<const float*>(tp(c.lw[k].dinv));
+          e.rhs = reinterpret_cast<const float*>(rhs[k]);
+          e.z = reinterpret_cast<float*>(zz[k]);
+        }
+        launch_vtail(tl.data(), nlev - t0, c.kinv.p, (int)c.lev[nlev - 1].n, B, s);
+      } else {
+        launch_coarse_solve<T>((int)c.lev[nlev - 1].n, B, c.kinv.p, rhs[nlev - 1], zz[nlev - 1], s);
+      }
+      for (int k = t0 - 1; k >= 0; --k) {
         int g;
         if (k == 0 && fine1)
           g = launch_vfine_up(view<float>(c, 0), B, reinterpret_cast<const float*>(lam2T()), c.prm.smoother,

@@ -74,6 +74,21 @@ template <class T>
 void launch_prolong_add(int nvc, int nhc, int B, const T* ec, T* zf, int max_blocks, cudaStream_t s);
 template <class T>
 void launch_coarse_solve(int nc, int B, const double* kinv, const T* rc, T* ec, cudaStream_t s);
+
+// The small FP16 coarse levels of a V(1,1) cycle and the coarsest solve in
+// one single-block kernel per column: levels[0 .. nlev - 2] are the levels
+// run there (the first of at most kTailPoints points, FP16 operators), the
+// last entry the coarsest level; only levels[0].rhs is read and
+// levels[0].z written.  See vtail.cuh.
+constexpr int64_t kTailPoints = 1024;  // levels of at most this many points run in the tail kernel
+struct TailLevelIn {
+  CoarseOpH op;
+  const float* dinv;
+  const float* rhs;  // read on the first tail level
+  float* z;          // written on the first tail level
+};
+void launch_vtail(const TailLevelIn* levels, int nlev, const double* kinv, int nc, int B, cudaStream_t s);
+bool vtail_fits(int nlev);
 void launch_dense_setup(const LevelView<double>& L, int B, const double* lam2, double* M,
                         double* W, double* K, int* info, int max_blocks, cudaStream_t s);
 void launch_galerkin(const RapIn& in, int nvc, int nhc, double* out, int max_blocks, cudaStream_t s);

@@ -8,6 +8,7 @@
 
 #include "launch.h"
 #include "vcoarse.cuh"
+#include "vtail.cuh"
 #include "vfine.cuh"
 #include "vfused.cuh"
 
@@ -185,6 +186,50 @@ int launch_vup(const LevelView<T>& L, int B, const T* lam2, const T* dinv, const
                 : vup_one<CoarseOp<T>, T, 2>(L.coarse_op(), B, lam2, dinv, r, ec, zpre, zout, part, ntx, nt, s);
   LCMG_LAUNCHED();
   return g;
+}
+
+bool vtail_fits(int nlev) { return nlev >= 2 && nlev <= kTailMaxLevels; }
+
+void launch_vtail(const TailLevelIn* levels, int nlev, const double* kinv, int nc, int B, cudaStream_t s) {
+  if (!vtail_fits(nlev)) throw ArgError("tail of the V-cycle: level count out of range");
+  TailArgs a{};
+  a.nlev = nlev;
+  int off = 0;
+  auto take = [&](int bytes) {
+    const int o = off;
+    off += (bytes + 15) / 16 * 16;
+    return o;
+  };
+  for (int k = 0; k < nlev; ++k) {
+    const TailLevelIn& in = levels[k];
+    const int n = in.op.nv * in.op.nh;
+    TailLevel& L = a.lv[k];
+    L.op = in.op;
+    L.dinv = in.dinv;
+    L.rhs = in.rhs;
+    L.z = in.z;
+    const bool coarsest = k == nlev - 1;
+    L.o_rows = coarsest ? 0 : take(48 * n);
+    L.o_s = coarsest ? 0 : take(4 * n);
+    L.o_d = coarsest ? 0 : take(4 * n);
+    L.o_r = take(4 * n);
+    L.o_t = coarsest ? 0 : take(4 * n);
+    L.o_res = coarsest ? 0 : take(4 * n);
+    L.o_z = take(4 * n);
+  }
+  a.kinv = kinv;
+  a.nc = nc;
+  static int optin_dev = -1;
+  int dev = 0;
+  LCMG_CUDA(cudaGetDevice(&dev));
+  if (optin_dev != dev) {
+    int maxsm = 0;
+    LCMG_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    LCMG_CUDA(cudaFuncSetAttribute(k_vtail_h, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm));
+    optin_dev = dev;
+  }
+  klaunch(k_vtail_h, dim3(1, (unsigned)B), dim3(kTailThreads), (size_t)off, s, a, B);
+  LCMG_LAUNCHED();
 }
 
 // Grid of the fused one-column updates: every block re-sums the partials of
