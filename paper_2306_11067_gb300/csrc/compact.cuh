@@ -131,6 +131,36 @@ struct CoarseOpH {
     for (int o = 13; o < 25; ++o) k[o] = off[o - 1];
     k[25] = k[26] = k[27] = 0;
   }
+  // (K v)_p from the point's three row words and row sum, every one of the
+  // 25 terms taken (the caller's v is zero outside the grid, so the terms
+  // apply_k leaves out add nothing).  The products are formed with the
+  // stored FP16 values and the sum scaled by sc at the end: sc and its
+  // inverse are powers of two, so every product and partial sum is the one
+  // apply_k forms, times 2^e exactly, and the result is the same float.
+  template <class F>
+  __device__ __forceinline__ float apply_rows(const uint4 q0, const uint4 q1, const uint4 q2, const float sp,
+                                              float inv_sc, F v) const {
+    const uint32_t w[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
+    float off[kCompactOff];
+#pragma unroll
+    for (int h = 0; h < 12; ++h) {
+      const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w[h]));
+      off[2 * h] = f.x;
+      off[2 * h + 1] = f.y;
+    }
+    float sum = 0;
+#pragma unroll
+    for (int o = 0; o < kCompactOff; ++o) sum += off[o];
+    const float center = sp * inv_sc - sum;
+    float acc = 0;
+#pragma unroll
+    for (int o = 0; o < 25; ++o) {
+      const int dj = o / 5 - 2, di = o % 5 - 2;
+      const float k = o < 12 ? off[o] : (o == 12 ? center : off[o - 1]);
+      acc += k * v(di, dj);
+    }
+    return acc * sc;
+  }
   template <class F>
   __device__ __forceinline__ float apply_k(const float (&k)[28], int i, int j, F v) const {
     float acc = 0;

@@ -43,41 +43,39 @@ struct VcUpStage {
   float ec[kVcCW * kVcCW];        // coarse correction
 };
 
-__device__ __forceinline__ bool vc_inside(const CoarseOpH& op, int i, int j) {
-  return i >= 0 && i < op.nv && j >= 0 && j < op.nh;
+// Staging: consecutive threads take consecutive elements of the window
+// (W and H compile-time, so the row and column of an element cost a
+// multiply-shift); entries outside the level are zero-filled.
+template <int W, int H>
+__device__ __forceinline__ void vc_stage_rows(uint4* dst, const CoarseOpH& op, int i0, int j0) {
+  for (int e = threadIdx.x; e < 3 * W * H; e += kVcThreads) {
+    const int rr = e / (3 * W), c = e - rr * (3 * W);
+    const int i = i0 + c / 3, j = j0 + rr;
+    const bool ok = i >= 0 && i < op.nv && j >= 0 && j < op.nh;
+    cp_async16(dst + e, op.rows + (ok ? 3 * ((int64_t)i + (int64_t)j * op.nv) + (c - 3 * (c / 3)) : 0), op.rows,
+               ok);
+  }
 }
-
-// copies of the element (i, j) of column col of an interleaved vector
-__device__ __forceinline__ void vc_copy_vec(float* dst, const float* v, const CoarseOpH& op, int B, int col, int i,
-                                            int j) {
-  const bool ok = vc_inside(op, i, j);
-  cp_async_elem(dst, v + (ok ? ((int64_t)i + (int64_t)j * op.nv) * B + col : 0), v, ok);
-}
-// the row of point (i, j): three 16-byte words, word w of it
-__device__ __forceinline__ void vc_copy_row(uint4* dst, const CoarseOpH& op, int i, int j, int w) {
-  const bool ok = vc_inside(op, i, j);
-  cp_async16(dst, op.rows + (ok ? 3 * ((int64_t)i + (int64_t)j * op.nv) + w : 0), op.rows, ok);
+// a window of one column of an interleaved level vector (nv x nh points)
+template <int W, int H>
+__device__ __forceinline__ void vc_stage_vec(float* dst, const float* __restrict__ v, int B, int col, int nv, int nh,
+                                             int i0, int j0) {
+  for (int e = threadIdx.x; e < W * H; e += kVcThreads) {
+    const int rr = e / W, c = e - rr * W;
+    const int i = i0 + c, j = j0 + rr;
+    const bool ok = i >= 0 && i < nv && j >= 0 && j < nh;
+    cp_async_elem(dst + e, v + (ok ? ((int64_t)i + (int64_t)j * nv) * B + col : 0), v, ok);
+  }
 }
 
 __device__ __forceinline__ void vc_stage_down(VcDownStage& st, const CoarseOpH& op, int B, int col,
                                               const float* __restrict__ dinv, const float* __restrict__ r, int tx,
                                               int ty) {
   const int ri = 2 * kVTile * tx - 1, rj = 2 * kVTile * ty - 1;
-  const int oi = ri - 2, oj = rj - 2;
-  for (int t = threadIdx.x; t < 3 * kVcWR * kVcWR; t += kVcThreads) {
-    const int q = t / 3;
-    vc_copy_row(&st.rows[t], op, ri + q % kVcWR, rj + q / kVcWR, t - 3 * q);
-  }
-  for (int t = threadIdx.x; t < kVcWR * kVcWR; t += kVcThreads) {
-    const int i = ri + t % kVcWR, j = rj + t / kVcWR;
-    const bool ok = vc_inside(op, i, j);
-    cp_async_elem(&st.s[t], op.s + (ok ? (int64_t)i + (int64_t)j * op.nv : 0), op.s, ok);
-  }
-  for (int t = threadIdx.x; t < kVcW1 * kVcW1; t += kVcThreads) {
-    const int i = oi + t % kVcW1, j = oj + t / kVcW1;
-    vc_copy_vec(&st.r[t], r, op, B, col, i, j);
-    vc_copy_vec(&st.d[t], dinv, op, B, col, i, j);
-  }
+  vc_stage_rows<kVcWR, kVcWR>(st.rows, op, ri, rj);
+  vc_stage_vec<kVcWR, kVcWR>(st.s, op.s, 1, 0, op.nv, op.nh, ri, rj);
+  vc_stage_vec<kVcW1, kVcW1>(st.r, r, B, col, op.nv, op.nh, ri - 2, rj - 2);
+  vc_stage_vec<kVcW1, kVcW1>(st.d, dinv, B, col, op.nv, op.nh, ri - 2, rj - 2);
 }
 
 __device__ __forceinline__ void vc_stage_up(VcUpStage& st, const CoarseOpH& op, int B, int col,
@@ -85,26 +83,20 @@ __device__ __forceinline__ void vc_stage_up(VcUpStage& st, const CoarseOpH& op, 
                                             const float* __restrict__ ec, const float* __restrict__ zpre, int tx,
                                             int ty) {
   const int fi = kVcWF * tx, fj = kVcWF * ty;
-  for (int t = threadIdx.x; t < 3 * kVcWF * kVcWF; t += kVcThreads) {
-    const int q = t / 3;
-    vc_copy_row(&st.rows[t], op, fi + q % kVcWF, fj + q / kVcWF, t - 3 * q);
-  }
-  for (int t = threadIdx.x; t < kVcWF * kVcWF; t += kVcThreads) {
-    const int i = fi + t % kVcWF, j = fj + t / kVcWF;
-    const bool ok = vc_inside(op, i, j);
-    cp_async_elem(&st.s[t], op.s + (ok ? (int64_t)i + (int64_t)j * op.nv : 0), op.s, ok);
-    vc_copy_vec(&st.r[t], r, op, B, col, i, j);
-    vc_copy_vec(&st.d[t], dinv, op, B, col, i, j);
-  }
-  for (int t = threadIdx.x; t < kVcW0 * kVcW0; t += kVcThreads)
-    vc_copy_vec(&st.zp[t], zpre, op, B, col, fi - 2 + t % kVcW0, fj - 2 + t / kVcW0);
-  const int nvc = op.nv / 2, nhc = op.nh / 2;
-  const int ci = kVTile * tx - 2, cj = kVTile * ty - 2;
-  for (int t = threadIdx.x; t < kVcCW * kVcCW; t += kVcThreads) {
-    const int I = ci + t % kVcCW, J = cj + t / kVcCW;
-    const bool ok = I >= 0 && I < nvc && J >= 0 && J < nhc;
-    cp_async_elem(&st.ec[t], ec + (ok ? ((int64_t)I + (int64_t)J * nvc) * B + col : 0), ec, ok);
-  }
+  vc_stage_rows<kVcWF, kVcWF>(st.rows, op, fi, fj);
+  vc_stage_vec<kVcWF, kVcWF>(st.s, op.s, 1, 0, op.nv, op.nh, fi, fj);
+  vc_stage_vec<kVcWF, kVcWF>(st.r, r, B, col, op.nv, op.nh, fi, fj);
+  vc_stage_vec<kVcWF, kVcWF>(st.d, dinv, B, col, op.nv, op.nh, fi, fj);
+  vc_stage_vec<kVcW0, kVcW0>(st.zp, zpre, B, col, op.nv, op.nh, fi - 2, fj - 2);
+  vc_stage_vec<kVcCW, kVcCW>(st.ec, ec, B, col, op.nv / 2, op.nh / 2, kVTile * tx - 2, kVTile * ty - 2);
+}
+
+// pw1(a, I) for a = 2I - 1 .. 2I + 2 on a line of nc coarse points
+__device__ __forceinline__ void pw1_four(int I, int nc, float (&w)[4]) {
+  w[0] = 0.25f;
+  w[1] = I == 0 ? 1.f : 0.75f;
+  w[2] = I == nc - 1 ? 1.f : 0.75f;
+  w[3] = 0.25f;
 }
 
 template <class Stage>
@@ -121,6 +113,7 @@ __global__ void __launch_bounds__(kVcThreads)
   __shared__ float sres[kVcWR * kVcWR];
   const int col = blockIdx.y;
   const int nv = op.nv, nh = op.nh, nvc = nv / 2, nhc = nh / 2;
+  const float inv_sc = 1.0f / op.sc;  // a power of two
   int buf = 0;
   if ((int)blockIdx.x < ntiles) vc_stage_down(st[0], op, B, col, dinv, r, blockIdx.x % ntx, blockIdx.x / ntx);
   cp_async_commit();
@@ -137,19 +130,14 @@ __global__ void __launch_bounds__(kVcThreads)
     // z1 = D r on the window (zero outside the level)
     for (int t = threadIdx.x; t < kVcW1 * kVcW1; t += kVcThreads) sz1[t] = S.d[t] * S.r[t];
     __syncthreads();
-    // res = r - K z1 on the restriction window
+    // res = r - K z1 on the restriction window (zero outside the level)
     for (int t = threadIdx.x; t < kVcWR * kVcWR; t += kVcThreads) {
-      const int li = t % kVcWR, lj = t / kVcWR;
+      const int lj = t / kVcWR, li = t - lj * kVcWR;
       const int i = ri + li, j = rj + lj;
-      float v = 0.f;
-      if (i >= 0 && i < nv && j >= 0 && j < nh) {
-        float k[28];
-        op.decode(S.rows[3 * t], S.rows[3 * t + 1], S.rows[3 * t + 2], S.s[t], k);
-        const int q = (li + 2) + (lj + 2) * kVcW1;
-        auto vz = [&](int di, int dj) { return sz1[q + di + dj * kVcW1]; };
-        v = S.r[q] - op.apply_k(k, i, j, vz);
-      }
-      sres[t] = v;
+      const int q = (li + 2) + (lj + 2) * kVcW1;
+      auto vz = [&](int di, int dj) { return sz1[q + di + dj * kVcW1]; };
+      const float kz = op.apply_rows(S.rows[3 * t], S.rows[3 * t + 1], S.rows[3 * t + 2], S.s[t], inv_sc, vz);
+      sres[t] = (i >= 0 && i < nv && j >= 0 && j < nh) ? S.r[q] - kz : 0.f;
     }
     // the pre-smoothed z of the tile's own points
     for (int t = threadIdx.x; t < kVcWF * kVcWF; t += kVcThreads) {
@@ -158,21 +146,20 @@ __global__ void __launch_bounds__(kVcThreads)
       if (i < nv && j < nh) zpre[((int64_t)i + (int64_t)j * nv) * B + col] = sz1[(li + 3) + (lj + 3) * kVcW1];
     }
     __syncthreads();
-    // r_c = R res
+    // r_c = R res (the residual window is zero outside the level, so the
+    // terms k_vdown leaves out add nothing)
     for (int t = threadIdx.x; t < kVTile * kVTile; t += kVcThreads) {
       const int I = I0 + t % kVTile, J = J0 + t / kVTile;
       if (I >= nvc || J >= nhc) continue;
+      float wa[4], wb[4];
+      pw1_four(I, nvc, wa);
+      pw1_four(J, nhc, wb);
+      const float* rs = sres + (2 * I - 1 - ri) + (2 * J - 1 - rj) * kVcWR;
       float acc = 0.f;
 #pragma unroll
-      for (int b = 2 * J - 1; b <= 2 * J + 2; ++b) {
-        if (b < 0 || b >= nh) continue;
-        const float wb = pw1<float>(b, J, nhc);
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int a2 = 2 * I - 1; a2 <= 2 * I + 2; ++a2) {
-          if (a2 < 0 || a2 >= nv) continue;
-          acc += wb * pw1<float>(a2, I, nvc) * sres[(a2 - ri) + (b - rj) * kVcWR];
-        }
-      }
+        for (int m = 0; m < 4; ++m) acc += wb[u] * wa[m] * rs[m + u * kVcWR];
       rc[((int64_t)I + (int64_t)J * nvc) * B + col] = acc;
     }
     __syncthreads();  // sz1, sres and this stage are rewritten for the tile after next
@@ -189,6 +176,7 @@ __global__ void __launch_bounds__(kVcThreads)
   __shared__ double sred[kVcThreads / 32];
   const int col = blockIdx.y;
   const int nv = op.nv, nh = op.nh, nvc = nv / 2, nhc = nh / 2;
+  const float inv_sc = 1.0f / op.sc;  // a power of two
   double dacc = 0.0;  // the tiles' r.z, each summed as in k_vup
   int buf = 0;
   if ((int)blockIdx.x < ntiles)
@@ -238,11 +226,9 @@ __global__ void __launch_bounds__(kVcThreads)
       const int li = t % kVcWF, lj = t / kVcWF;
       const int i = fi + li, j = fj + lj;
       if (i >= nv || j >= nh) continue;
-      float k[28];
-      op.decode(S.rows[3 * t], S.rows[3 * t + 1], S.rows[3 * t + 2], S.s[t], k);
       const int q = (li + 2) + (lj + 2) * kVcW0;
       auto vz = [&](int di, int dj) { return s0[q + di + dj * kVcW0]; };
-      const float kz = op.apply_k(k, i, j, vz);
+      const float kz = op.apply_rows(S.rows[3 * t], S.rows[3 * t + 1], S.rows[3 * t + 2], S.s[t], inv_sc, vz);
       const float rv = S.r[t];
       const float zn = s0[q] + S.d[t] * (rv - kz);
       zout[((int64_t)i + (int64_t)j * nv) * B + col] = zn;
