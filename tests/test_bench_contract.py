@@ -16,6 +16,21 @@ def test_traffic_record_matches_the_current_kernel_source():
     assert 1.0e8 < bench.recorded_traffic() < 1.2e8
 
 
+def test_deblur2048_records_match_the_current_kernel_sources():
+    """The ncu DRAM records of the 2048^2 step's banded passes and V-cycle
+    are used only while the kernel sources hash to their fingerprints: a
+    kernel edit must come with a fresh capture (else traffic is null)."""
+    band = bench.recorded_float("k_band", "dram_bytes_per_apply")
+    cyc = bench.recorded_float("vcycle", "dram_bytes_per_cycle")
+    assert band is not None, bench.source_fingerprint("k_band")
+    assert cyc is not None, bench.source_fingerprint("vcycle")
+    n = 2048 * 2048
+    assert 4 * n * 4 < band < 7 * n * 4   # at least p, u, w_s, w_e once; at most the 7 * 4n of the algorithm
+    assert 10 * n < cyc < 100 * n
+    levels = bench.recorded("vcycle")
+    assert any(k.startswith("level_") for k in levels)
+
+
 def test_peak_is_measured_or_the_stated_fallback(tmp_path, monkeypatch):
     peak, kind = bench.measured_hbm_peak()
     path = os.path.join(bench.ROOT, "MEASURED_PEAKS.json")
