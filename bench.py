@@ -237,9 +237,115 @@ def run_oracle_concurrent(spec: dict, procs: int) -> list:
     return res
 
 
+def oracle_sample_small(spec: dict) -> dict:
+    """The oracle on the 32 x 32 CSR blur case (9 x 9 PSF sigma 1.5 as an
+    FP64 CSR matrix, lambda = 0.05, tol 1e-10, 3 levels): hierarchy and PCG
+    solve from zero, timed whole, repeated for about a second."""
+    import numpy as np
+    import scipy.sparse as sp
+    import problemgen as pg
+    from oracle import operators as ops, multigrid as mg, krylov
+    P = pg.make_problem("deblur32_csr")
+    F = ops.ForwardCSR(P.A.to_scipy())
+    Lg = ops.gradient(P.n_v, P.n_h)
+    d = np.ones(ops.n_edges(P.n_v, P.n_h))
+    lam = float(P.lambdas[0])
+    n, its, t0 = 0, 0, time.perf_counter()
+    while n < 3 or time.perf_counter() - t0 < 1.0:
+        H = mg.build_hierarchy(mg.weighted_laplacian(Lg, d), sp.diags(F.diag_AtA()), P.n_v, P.n_h, P.levels)
+        _, it, st, _ = krylov.pcg(lambda v: ops.normal_apply(F, Lg, d, lam, v), ops.rhs(F, P.b[:, 0]), None,
+                                  mg.VCycle(H, lam, nu=NU), tol=P.tol, maxit=20000)
+        n, its = n + 1, it
+    return dict(seconds_per_solve=(time.perf_counter() - t0) / n, iterations=int(its), solves=n,
+                threads=int(os.environ.get("OMP_NUM_THREADS", "1")))
+
+
+def oracle_sample_512(spec: dict) -> dict:
+    """The oracle's pieces on the 512 x 512 blur workload (19 x 19 PSF sigma 3,
+    6 levels): one K(lambda) application, the hierarchy, one V-cycle setup
+    and one V(1,1) cycle, with the weights of the right-hand-side leg."""
+    import numpy as np
+    import scipy.sparse as sp
+    import problemgen as pg
+    from oracle import operators as ops, multigrid as mg
+    P = pg.make_problem("deblur512")
+    F = ops.make_forward(P)
+    Lg = ops.gradient(P.n_v, P.n_h)
+    d = pg.random_weights(ops.n_edges(P.n_v, P.n_h), 52, d_min=0.05)
+    lam = float(spec.get("lam", 0.01))
+    x = pg.rng(5).standard_normal(P.n)
+    t0 = time.perf_counter()
+    ops.normal_apply(F, Lg, d, lam, x)
+    t_k = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    H = mg.build_hierarchy(mg.weighted_laplacian(Lg, d), sp.diags(F.diag_AtA()), P.n_v, P.n_h, P.levels)
+    t_h = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    V = mg.VCycle(H, lam, nu=NU)
+    t_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    V(x)
+    t_v = time.perf_counter() - t0
+    return dict(t_apply=t_k, t_hierarchy=t_h, t_vsetup=t_s, t_vcycle=t_v,
+                threads=int(os.environ.get("OMP_NUM_THREADS", "1")))
+
+
+def cpu_configs(device, rhs_leg):
+    """The oracle, one thread, on the 32^2 CSR case (timed whole) and on the
+    512^2 blur sweep of the right-hand-side leg (one right-hand side, the 32
+    lambdas of one outer iteration: extrapolated from its timed pieces with
+    the GPU one-column chain's iterations), beside the GPU's figures."""
+    import numpy as np
+    import problemgen as pg
+    from paper_2306_11067_gb300 import lcmg as L
+    out = {}
+    try:
+        o = run_oracle_subprocess({"kind": "small"})
+        P = pg.make_problem("deblur32_csr")
+        gpu = {}
+        for prec, nm in ((L.PREC_FP64, "fp64"), (L.PREC_MIXED, "mixed")):
+            sv = L.Solver(P.n_v, P.n_h, device=device, precision=prec, tol=P.tol, maxit=20000, levels=P.levels)
+            sv.set_forward_csr(P.A)
+            sv.solve(P.lambdas, P.b[:, 0])
+            t0, n = time.perf_counter(), 0
+            while n < 5 or time.perf_counter() - t0 < 0.5:
+                r = sv.solve(P.lambdas, P.b[:, 0])
+                n += 1
+            gpu[nm] = {"solves_per_s": n / (time.perf_counter() - t0), "iterations": int(r["iters"][0, 0])}
+            sv.close()
+        out["deblur32_csr"] = {"workload": "32x32 blur, 9x9 PSF sigma 1.5 as FP64 CSR, lambda 0.05, tol 1e-10, "
+                                           "3 levels, one solve from zero (hierarchy included)",
+                               "oracle_solves_per_s_1thread": 1.0 / o["seconds_per_solve"],
+                               "oracle_iterations": o["iterations"], "gpu": gpu}
+    except Exception as ex:  # reported, not fatal
+        out["deblur32_csr"] = {"failed": str(ex)}
+    try:
+        if rhs_leg and "one_column_chains" in rhs_leg:
+            o = run_oracle_subprocess({"kind": "512"})
+            its = float(np.mean(rhs_leg["iterations_per_rhs_one_column"]))
+            t = its * (o["t_apply"] + o["t_vcycle"]) + 32 * o["t_vsetup"] + o["t_hierarchy"]
+            out["deblur512_sweep"] = {
+                "workload": "512x512 blur (19x19 PSF sigma 3), one right-hand side, the 32 lambdas of one outer "
+                            "iteration in the chain",
+                "oracle_lambda_solves_per_s_1thread": 32.0 / t, "kind": "extrapolation",
+                "how": "oracle time per PCG iteration (one K application + one V-cycle) x the GPU one-column "
+                       "chain's mean iterations per right-hand side (%.0f) + 32 V-cycle setups + one hierarchy"
+                       % its,
+                "timings_s": o,
+                "gpu_one_column_lambda_solves_per_s": rhs_leg["one_column_chains"]["value"],
+                "gpu_batched_lambda_solves_per_s": rhs_leg["batched"]["value"]}
+    except Exception as ex:  # reported, not fatal
+        out["deblur512_sweep"] = {"failed": str(ex)}
+    return out
+
+
 def oracle_dispatch(spec: dict) -> dict:
     if spec["kind"] == "deblur2048":
         return oracle_sample_2048(spec)
+    if spec["kind"] == "small":
+        return oracle_sample_small(spec)
+    if spec["kind"] == "512":
+        return oracle_sample_512(spec)
     return oracle_sample_ct256(float(spec.get("budget", 8.0)), int(spec.get("solves", 1)))
 
 
@@ -892,6 +998,9 @@ def main_deblur(args, world, rank, local):
             rhs_batched = rhs_batched_leg(local)
         except Exception as ex:  # reported, not fatal
             rhs_batched = {"failed": str(ex)}
+    cpu_cfg = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu_cfg = cpu_configs(local, rhs_batched)
 
     if rank == 0:
         line = {
@@ -922,6 +1031,7 @@ def main_deblur(args, world, rank, local):
             "fma_peaks": fp64_peak(local) if rank == 0 else None,
             "serving": serving,
             "rhs_batched_512": rhs_batched,
+            "cpu_baseline_configs": cpu_cfg,
             "clocks": clocks,
         }
         print(json.dumps(line))
