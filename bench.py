@@ -1268,8 +1268,9 @@ def main_ct256(args, world, rank, local):
 
 
 # measured on GB300 by this benchmark (its config.pcg_iterations_per_step /
-# lambda_solves_per_step): the reference arm's extrapolation to lambda-solves
-REF_ITS_PER_SOLVE = 500.0
+# lambda_solves_per_step: 1,184 / 10): the reference arm's extrapolation to
+# lambda-solves
+REF_ITS_PER_SOLVE = 118.4
 
 
 def oracle_steps_2048(spec: dict) -> dict:
