@@ -634,8 +634,10 @@ struct Batch {
       const bool fine1 = fine_v11();
       // FP16 coarse levels of at most kTailPoints points and the coarsest
       // solve: one single-block kernel (vtail.cuh)
+      // (only while the coarsest level is small: its dense FP64 solve then runs
+      // on one SM, which at 256 points costs more than the launches saved)
       int t0 = nlev - 1;
-      if (std::is_same<T, float>::value && c.h16_on && nu == 1)
+      if (std::is_same<T, float>::value && c.h16_on && nu == 1 && c.lev[nlev - 1].n <= kTailCoarsest)
         while (t0 - 1 >= 1 && c.lev[t0 - 1].n <= kTailPoints) --t0;
       if (!vtail_fits(nlev - t0)) t0 = nlev - 1;
       for (int k = 0; k < t0; ++k) {

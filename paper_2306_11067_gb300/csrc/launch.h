@@ -81,6 +81,7 @@ void launch_coarse_solve(int nc, int B, const double* kinv, const T* rc, T* ec, 
 // last entry the coarsest level; only levels[0].rhs is read and
 // levels[0].z written.  See vtail.cuh.
 constexpr int64_t kTailPoints = 1024;  // levels of at most this many points run in the tail kernel
+constexpr int64_t kTailCoarsest = 64;  // ... when the coarsest level has at most this many
 struct TailLevelIn {
   CoarseOpH op;
   const float* dinv;

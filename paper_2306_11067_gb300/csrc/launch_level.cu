@@ -245,17 +245,36 @@ static int fused_update_grid(int64_t n, int max_blocks) {
   return std::min(grid_for(n, 1, max_blocks), std::max(1, 4 * sms));
 }
 
+// Rows per strip of the row-streaming kernels: at most `most`, and few
+// enough that the strips number about four warps per SM slot of a wave
+// (one warp walks a strip in sequence, so on a small grid long strips leave
+// most of the GPU idle), but at least `least` (the strip's halo rows are
+// computed twice).
+static int strip_rows(int nsi, int len, int most, int least) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    LCMG_CUDA(cudaGetDevice(&dev));
+    LCMG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int64_t want = (int64_t)sms * 32;  // warps resident at 4 blocks of 8 warps per SM
+  const int64_t per_col = std::max<int64_t>(1, (want + nsi - 1) / nsi);  // strips wanted along the rows
+  const int rows = (int)((len + per_col - 1) / per_col);
+  return std::max(least, std::min(most, rows));
+}
+
 int launch_vfine_down(const LevelView<float>& L, int B, const float* lam2, int smoother, double omega,
                       const float* r, float* rc, cudaStream_t s) {
   const int nt = ((L.nv + kFineTI - 1) / kFineTI) * ((L.nh + kFineTJ - 1) / kFineTJ);
   int g;
   if (L.h16 && L.nv % 2 == 0 && L.nh % 2 == 0 && (int64_t)L.nv * L.nh * B < (int64_t(1) << 31)) {  // row streaming
     const int nsi = (L.nv / 2 + kDownCols - 1) / kDownCols;
-    const int nst = nsi * ((L.nh / 2 + kStripCoarse - 1) / kStripCoarse);
+    const int crows = strip_rows(nsi, L.nh / 2, kStripCoarse, 2);
+    const int nst = nsi * ((L.nh / 2 + crows - 1) / crows);
     auto k = B == 1 ? k_vfine_down_s<true> : k_vfine_down_s<false>;
     g = tile_grid(k, kFineThreads, (nst + kFineThreads / 32 - 1) / (kFineThreads / 32));
     klaunch(k, dim3((unsigned)g, (unsigned)B), dim3(kFineThreads), 0, s, L.fh, B, lam2, smoother, (float)omega, r,
-            rc, nsi, nst);
+            rc, nsi, nst, crows);
   } else if (L.h16) {
     g = tile_grid(k_vfine_down<FineOpH>, kFineThreads, nt);
     klaunch(k_vfine_down<FineOpH>, dim3((unsigned)g, (unsigned)B), dim3(kFineThreads), 0, s, L.fh, B, lam2, smoother,
@@ -275,11 +294,12 @@ int launch_vfine_up(const LevelView<float>& L, int B, const float* lam2, int smo
   int g;
   if (L.h16 && L.nv % 2 == 0 && L.nh % 2 == 0 && (int64_t)L.nv * L.nh * B < (int64_t(1) << 31)) {  // row streaming
     const int nsi = (L.nv + kUpCols - 1) / kUpCols;
-    const int nst = nsi * ((L.nh + kStripRows - 1) / kStripRows);
+    const int rows = strip_rows(nsi, L.nh, kStripRows, 4);
+    const int nst = nsi * ((L.nh + rows - 1) / rows);
     auto k = B == 1 ? k_vfine_up_s<true> : k_vfine_up_s<false>;
     g = tile_grid(k, kFineThreads, (nst + kFineThreads / 32 - 1) / (kFineThreads / 32));
     klaunch(k, dim3((unsigned)g, (unsigned)B), dim3(kFineThreads), 0, s, L.fh, B, lam2, smoother, (float)omega, r,
-            ec, zout, nsi, nst, part);
+            ec, zout, nsi, nst, rows, part);
   } else if (L.h16) {
     g = tile_grid(k_vfine_up<FineOpH>, kFineThreads, nt);
     klaunch(k_vfine_up<FineOpH>, dim3((unsigned)g, (unsigned)B), dim3(kFineThreads), 0, s, L.fh, B, lam2, smoother,

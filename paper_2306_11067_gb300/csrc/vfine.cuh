@@ -216,7 +216,9 @@ __global__ void __launch_bounds__(kFineThreads)
 // along i are the neighbouring lanes' values (warp shuffles).  The two edge
 // lanes of a warp compute only what their neighbours need (the halo), so a
 // warp produces 30 points of z (k_vfine_up_s) or 14 coarse points of r_c
-// (k_vfine_down_s) per row.  No shared memory, no barrier; a row's loads
+// (k_vfine_down_s) per row; a strip is at most kStripRows rows (kStripCoarse
+// coarse rows), fewer on small grids, so that the strips fill the GPU.  No
+// shared memory, no barrier; a row's loads
 // are issued one row ahead of their use, from addresses clamped into the
 // arrays, and every per-point step is branch-free (selects), so that a
 // lane's work per row is its arithmetic and little else.
@@ -229,8 +231,8 @@ __global__ void __launch_bounds__(kFineThreads)
 // along j.  32-bit indices: the launcher takes this path while
 // n_v n_h B < 2^31.
 // ---------------------------------------------------------------------------
-constexpr int kStripRows = 32;    // fine rows of z per k_vfine_up_s strip
-constexpr int kStripCoarse = 16;  // coarse rows of r_c per k_vfine_down_s strip
+constexpr int kStripRows = 32;    // most fine rows of z per k_vfine_up_s strip
+constexpr int kStripCoarse = 16;  // most coarse rows of r_c per k_vfine_down_s strip
 constexpr int kUpCols = 30;       // z columns per warp
 constexpr int kDownCols = 14;     // r_c columns per warp
 
@@ -308,7 +310,7 @@ template <bool kUnit>
 __global__ void __launch_bounds__(kFineThreads)
     k_vfine_up_s(FineOpH op, int B, const float* __restrict__ lam2, int smoother, float omega,
                  const float* __restrict__ r, const float* __restrict__ ec, float* __restrict__ zout, int nsi,
-                 int nstrips, double* __restrict__ part) {
+                 int nstrips, int rows, double* __restrict__ part) {
   __shared__ double sred[kFineThreads / 32];
   const unsigned FULL = 0xffffffffu;
   const int S = kUnit ? 1 : B;
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(kFineThreads)
   Dot2 dot;
   for (int st = blockIdx.x * (kFineThreads / 32) + warp; st < nstrips; st += gridDim.x * (kFineThreads / 32)) {
     const int i = (st % nsi) * kUpCols - 1 + lane;
-    const int j0 = (st / nsi) * kStripRows, j1 = min(j0 + kStripRows, nh);
+    const int j0 = (st / nsi) * rows, j1 = min(j0 + rows, nh);
     const bool in_i = i >= 0 && i < nv, has_s = i + 1 < nv, has_n = i > 0;
     const bool out = lane >= 1 && lane <= kUpCols && i < nv;
     // interpolation along i (fixed for the lane): coarse columns Ia, Ib
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(kFineThreads)
 template <bool kUnit>
 __global__ void __launch_bounds__(kFineThreads)
     k_vfine_down_s(FineOpH op, int B, const float* __restrict__ lam2, int smoother, float omega,
-                   const float* __restrict__ r, float* __restrict__ rc, int nsi, int nstrips) {
+                   const float* __restrict__ r, float* __restrict__ rc, int nsi, int nstrips, int crows) {
   const unsigned FULL = 0xffffffffu;
   const int S = kUnit ? 1 : B;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(kFineThreads)
   const float sw = op.sw, sg = op.sg;
   const float l2 = lam2[col];
   for (int st = blockIdx.x * (kFineThreads / 32) + warp; st < nstrips; st += gridDim.x * (kFineThreads / 32)) {
-    const int I0 = (st % nsi) * kDownCols, J0 = (st / nsi) * kStripCoarse;
+    const int I0 = (st % nsi) * kDownCols, J0 = (st / nsi) * crows;
     const int i = 2 * I0 - 2 + lane;  // z1 at every lane, res at lanes 1..30
     const bool in_i = i >= 0 && i < nv, has_s = i + 1 < nv, has_n = i > 0;
     // restriction along i: coarse column I = I0 + lane (lanes < 14) from the
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(kFineThreads)
       const int a2 = 2 * I - 1 + m;
       wa[m] = (a2 >= 0 && a2 < nv && I < nvc) ? pw1<float>(a2, I, nvc) : 0.f;
     }
-    const int jb0 = 2 * J0 - 1, jb1 = min(2 * (J0 + kStripCoarse), nh);  // residual rows [jb0, jb1]
+    const int jb0 = 2 * J0 - 1, jb1 = min(2 * (J0 + crows), nh);  // residual rows [jb0, jb1]
     int p = i + (jb0 - 1) * nv;  // the lane's point in row jb0 - 1
     float we_prev = 0.f;
     if (jb0 - 2 >= 0 && in_i && jb0 - 1 < nh) we_prev = __half2float(we[p - nv]) * sw;

@@ -19,9 +19,9 @@ GPU tests compare with the library at those sizes.
                      with seeded weights; sampled entries, norms, rho, eta
   ct128_alg2.txt     Algorithm 2 on the 128 x 128 CT recipe at tol 1e-9:
                      the selected lambda indices
-  deblur128_alg2.txt Algorithm 2 on the 512 x 512 blur recipe's 128 x 128
-                     form (19 x 19 PSF, 32 lambdas, at most 5 outer
-                     iterations) at tol 1e-9, right-hand sides 0 and 1
+  deblur64_alg2.txt  Algorithm 2 on the 512 x 512 blur recipe's 64 x 64
+                     form (19 x 19 PSF, its 24 lambdas >= 1e-4, at most 5
+                     outer iterations) at tol 1e-9, right-hand sides 0, 1
   deblur512_solve.txt  512 x 512, 19 x 19 Gaussian sigma 3, 4 right-hand
                      sides, lambda = 0.05, 0.5, tol 1e-12, 6 levels
   deblur2048_ops.txt   2048 x 2048, 31 x 31 Gaussian sigma 5: K(lambda) p
@@ -86,20 +86,24 @@ def ct256_full():
     return lines
 
 
-def deblur128_alg2():
-    P = pg.make_problem("deblur512", size=128)
+def deblur64_alg2():
+    P = pg.make_problem("deblur512", size=64)
+    lams = P.lambdas[8:]
     prm = outer.Params(nu=1, tol=1e-9, maxit=50000, levels=P.levels)
-    lines = ["# Algorithm 2 on the deblur512 recipe at 128 x 128 (19 x 19 Gaussian sigma 3, zero boundary,",
-             "# %d lambdas logspace(-5, 0), %d levels), V(1,1), tol 1e-9, three-equal stop, at most %d outer" % (
-                 len(P.lambdas), P.levels, P.meta["max_outer"]),
+    lines = ["# Algorithm 2 on the deblur512 recipe at 64 x 64 (19 x 19 Gaussian sigma 3, zero boundary, %d" % P.levels,
+             "# levels), the recipe's lambdas from the 9th on (%d lambdas, %.3g .. 1: the smaller ones do not reach" % (
+                 len(lams), lams[0]),
+             "# tol 1e-9 within 50,000 PCG iterations), V(1,1), tol 1e-9, three-equal stop, at most %d outer" % (
+                 P.meta["max_outer"]),
              "# iterations, right-hand sides 0 and 1: the selected 1-based lambda indices per right-hand side."]
     for r in (0, 1):
-        res = outer.lcurve_run(P, prm, rhs_index=r, max_outer=P.meta["max_outer"])
+        res = outer.lcurve_run(P, prm, rhs_index=r, max_outer=P.meta["max_outer"], lambdas=lams)
         lines.append("history %d " % r + " ".join(str(h) for h in res.history))
         for rec in res.records:
             kap = np.sort(lcurve.menger_curvature(rec.rho, rec.eta))[::-1]
             lines.append("kappa_top2 %d %.6g %.6g" % (r, kap[0], kap[1]))
-        print("deblur128 history", r, res.history, flush=True)
+            lines.append("iterations %d %s status %s" % (r, " ".join(str(int(v)) for v in rec.iters), " ".join(str(int(v)) for v in rec.status)))
+        print("deblur64 history", r, res.history, flush=True)
     return lines
 
 
@@ -248,7 +252,7 @@ def deblur2048_vcycle16():
     return lines
 
 
-FULL = {"ct256_full.txt": ct256_full, "ct128_alg2.txt": ct128_alg2, "deblur128_alg2.txt": deblur128_alg2,
+FULL = {"ct256_full.txt": ct256_full, "ct128_alg2.txt": ct128_alg2, "deblur64_alg2.txt": deblur64_alg2,
         "deblur512_solve.txt": deblur512_solve,
         "deblur2048_ops.txt": deblur2048_ops, "ct256_vcycle16.txt": ct256_vcycle16,
         "deblur2048_vcycle16.txt": deblur2048_vcycle16}

@@ -184,21 +184,24 @@ def test_ct128_algorithm2_history(precision):
 
 @pytest.mark.parametrize("precision", [L.PREC_FP64, L.PREC_MIXED])
 @pytest.mark.parametrize("rhs", [0, 1])
-def test_deblur128_algorithm2_history(precision, rhs):
-    """Algorithm 2 on the 512^2 blur recipe's 128^2 form (the separable
-    operator, 19 x 19 PSF, 32 lambdas, at most 5 outer iterations) selects
-    the oracle's lambdas at tol 1e-9, in the paper's chain."""
-    _need("deblur128_alg2.txt")
+def test_deblur64_algorithm2_history(precision, rhs):
+    """Algorithm 2 on the 512^2 blur recipe's 64^2 form (the separable
+    operator, 19 x 19 PSF, the recipe's 24 lambdas >= 1e-4, at most 5 outer
+    iterations) selects the oracle's lambdas at tol 1e-9, in the paper's
+    chain.  (At tol 1e-9 the recipe's smaller lambdas do not converge within
+    50,000 iterations, on the GPU or in the oracle, so their iterates, and a
+    history through them, would be decided by rounding.)"""
+    _need("deblur64_alg2.txt")
     hist = None
-    for line in open(os.path.join(GOLD, "deblur128_alg2.txt")):
+    for line in open(os.path.join(GOLD, "deblur64_alg2.txt")):
         if line.startswith("history %d " % rhs):
             hist = [int(v) for v in line.split()[2:]]
     assert hist is not None
-    P = pg.make_problem("deblur512", size=128)
-    s = Solver(128, 128, levels=P.levels, precision=precision, tol=1e-9, maxit=50000)
+    P = pg.make_problem("deblur512", size=64)
+    s = Solver(64, 64, levels=P.levels, precision=precision, tol=1e-9, maxit=50000)
     s.set_forward_stencil(P.psf)
     assert s.forward_form() == L.FORM_SEPARABLE
-    r = s.lcurve_run(P.lambdas, P.b[:, rhs], max_outer=P.meta["max_outer"])
+    r = s.lcurve_run(P.lambdas[8:], P.b[:, rhs], max_outer=P.meta["max_outer"])
     s.close()
     assert [int(h) for h in r["history"]] == hist
 
