@@ -476,7 +476,7 @@ def recorded_traffic():
     except (KeyError, ValueError):
         return None
 
-
+# Served mix (the mixed blur and CT request stream, in the sizes that generate in
 
 # Served mix (configs[3]'s request stream in the sizes that generate in
 # seconds): 60% deblurring at 128^2, 256^2, 512^2, 1024^2 (PSF 9 x 9, sigma
