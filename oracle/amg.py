@@ -23,7 +23,7 @@ for a matrix K:
     F_i^s its strong F connections and F_i^w the rest of its neighbours;
   * coarse operators K_{k+1} = P_k^T K_k P_k (Galerkin).
 
-Readings of this build (the paper names the steps, not these details):
+Readings taken where the paper names the steps, not these details:
   * "strong connections of i" are the j in S_i = {j : -k_ij > theta max};
     "its strong neighbours" of a new C point i are the unsorted points that
     depend strongly on i (i in S_j), as Ruge and Stueben define the

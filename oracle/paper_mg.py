@@ -18,7 +18,7 @@ and one after the coarse-grid correction (the paper's V(2,1)).  The
 coarsest level is solved exactly.  Because CG relaxation makes the cycle a
 nonlinear operator, the outer solver is flexible GMRES (Sec. 3.3).
 
-Readings of this build:
+Readings taken where the paper is silent:
   * P_k is either the cell-centred bilinear interpolation of the geometric
     hierarchy (oracle.multigrid.prolongation) or the paper's classical AMG
     interpolation of G_L = L^T D^2 L (oracle.amg, Sec. 3.1), which depends
